@@ -1,0 +1,207 @@
+"""FP64 reference oracle for the BSS-MPPI solve (ctypes wrapper around bssmppi_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg use it to check and to time against; the product path never imports it. It shares no code
+with the CUDA library: the two receive the same seeded inputs from ``workload`` and nothing else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_DIR = os.path.join(_HERE, "_lib")
+_LIB_PATH = os.path.join(_LIB_DIR, "liboracle.so")
+_SRC = os.path.join(_HERE, "bssmppi_oracle.c")
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class OrcProblem(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int), ("M", ctypes.c_int), ("T", ctypes.c_int), ("n_sub", ctypes.c_int),
+        ("model", ctypes.c_int),
+        ("dt", ctypes.c_double), ("mass", ctypes.c_double), ("Iz", ctypes.c_double),
+        ("lf", ctypes.c_double), ("lr", ctypes.c_double), ("tire_B", ctypes.c_double),
+        ("tire_C", ctypes.c_double), ("mu", ctypes.c_double), ("g", ctypes.c_double),
+        ("vx_floor", ctypes.c_double),
+        ("u_min", ctypes.c_double * 2), ("u_max", ctypes.c_double * 2),
+        ("Sigma_eps", ctypes.c_double * 4), ("Sigma_w", ctypes.c_double * 36),
+        ("lam", ctypes.c_double), ("delta", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("ctrl_w", ctypes.c_double), ("C_safe", ctypes.c_double), ("C_obs", ctypes.c_double),
+        ("w_T", ctypes.c_double),
+        ("x_goal", ctypes.c_double * 6), ("Q", ctypes.c_double * 6), ("Qf", ctypes.c_double * 6),
+        ("ey_index", ctypes.c_int),
+        ("kappa", _dp), ("n_track", ctypes.c_int), ("track_len", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("crn_disturbance", ctypes.c_int),
+    ]
+
+
+class OrcOutputs(ctypes.Structure):
+    _fields_ = [(n, _dp) for n in ("S", "u", "w", "v_plus", "mean", "cov", "margin", "h", "diag")]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (strict IEEE double: no contraction, no fast-math)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+               "-o", _LIB_PATH, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_gaussian_pair.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _dp]
+        L.orc_backoff_gaussian.restype = ctypes.c_double
+        L.orc_backoff_gaussian.argtypes = [ctypes.c_double]
+        L.orc_backoff_cantelli.restype = ctypes.c_double
+        L.orc_backoff_cantelli.argtypes = [ctypes.c_double]
+        L.orc_track_kappa.restype = ctypes.c_double
+        L.orc_track_kappa.argtypes = [ctypes.POINTER(OrcProblem), ctypes.c_double]
+        L.orc_model_step.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, _dp]
+        L.orc_rollout.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, _dp, ctypes.c_uint32,
+                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrcOutputs)]
+        L.orc_optimal_control.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                          _dp, _dp, _dp]
+        L.orc_solve.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, _dp, ctypes.c_uint32,
+                                ctypes.POINTER(OrcOutputs)]
+        L.orc_repair_objective.restype = ctypes.c_double
+        L.orc_repair_objective.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, ctypes.c_uint32, _dp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _f32(x):
+    """Inputs are handed to the CUDA path as float32; the oracle takes the same rounded values."""
+    return float(np.float32(x))
+
+
+class Oracle:
+    """Holds one problem in the oracle's own struct (keeps the arrays it points to alive)."""
+
+    def __init__(self, prob):
+        self.prob = prob
+        p = OrcProblem()
+        for name in ("K", "M", "T", "n_sub", "model", "ey_index", "crn_disturbance"):
+            setattr(p, name, int(getattr(prob, name)))
+        for name in ("dt", "mass", "Iz", "lf", "lr", "tire_B", "tire_C", "mu", "g", "vx_floor",
+                     "delta", "gamma", "ctrl_w", "C_safe", "C_obs", "w_T"):
+            setattr(p, name, _f32(getattr(prob, name)))
+        p.lam = _f32(prob.lam)
+        for i in range(2):
+            p.u_min[i] = _f32(prob.u_min[i])
+            p.u_max[i] = _f32(prob.u_max[i])
+        se = np.asarray(prob.Sigma_eps, dtype=np.float64).reshape(2, 2)
+        for i in range(4):
+            p.Sigma_eps[i] = se.flat[i]
+        nx = prob.nx
+        sw = np.asarray(prob.Sigma_w, dtype=np.float64).reshape(nx, nx)
+        for i in range(nx * nx):
+            p.Sigma_w[i] = sw.flat[i]
+        for i in range(6):
+            p.x_goal[i] = _f32(prob.x_goal[i])
+            p.Q[i] = _f32(prob.Q[i])
+            p.Qf[i] = _f32(prob.Qf[i])
+        self._kappa = np.ascontiguousarray(np.asarray(prob.kappa, dtype=np.float32), dtype=np.float64)
+        p.kappa = _ptr(self._kappa)
+        p.n_track = int(self._kappa.size)
+        p.track_len = _f32(prob.track_len)
+        p.seed = int(prob.seed) & 0xFFFFFFFFFFFFFFFF
+        self.p = p
+        self.nx = nx
+
+    def solve(self, x0, v, ctr, Sigma0=None, want_cov=False, k_range=None):
+        """Full solve (or rollout of samples k_range=(k0, k1) only). Returns a dict of arrays."""
+        K, T, nx = self.prob.K, self.prob.T, self.nx
+        x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float32), dtype=np.float64)
+        v = np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(T, 2), dtype=np.float64)
+        S0 = None
+        if Sigma0 is not None:
+            S0 = np.ascontiguousarray(np.asarray(Sigma0, dtype=np.float32).reshape(nx, nx), dtype=np.float64)
+        r = {
+            "S": np.zeros(K), "u": np.zeros((K, T, 2)), "w": np.zeros(K), "v_plus": np.zeros((T, 2)),
+            "mean": np.zeros((K, T + 1, nx)), "margin": np.zeros(K), "h": np.zeros((K, T + 1)),
+            "diag": np.zeros(4),
+        }
+        if want_cov:
+            r["cov"] = np.zeros((K, T + 1, nx, nx))
+        o = OrcOutputs(*[_ptr(r.get(name)) for name, _ in OrcOutputs._fields_])
+        if k_range is None:
+            rc = lib().orc_solve(ctypes.byref(self.p), _ptr(x0), _ptr(S0), _ptr(v), ctypes.c_uint32(ctr),
+                                 ctypes.byref(o))
+        else:
+            rc = lib().orc_rollout(ctypes.byref(self.p), _ptr(x0), _ptr(S0), _ptr(v), ctypes.c_uint32(ctr),
+                                   int(k_range[0]), int(k_range[1]), ctypes.byref(o))
+        if rc != 0:
+            raise ValueError("oracle rejected the problem")
+        r["eps"] = r["u"] - v[None]
+        return r
+
+    def model_step(self, x, u):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros(self.nx)
+        lib().orc_model_step(ctypes.byref(self.p), _ptr(x), _ptr(u), _ptr(out))
+        return out
+
+    def kappa_at(self, s):
+        return lib().orc_track_kappa(ctypes.byref(self.p), float(s))
+
+    def repair_objective(self, x0, v, ctr, grad=True):
+        T = self.prob.T
+        x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
+        v = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(T, 2))
+        g = np.zeros((T, 2)) if grad else None
+        J = lib().orc_repair_objective(ctypes.byref(self.p), _ptr(x0), _ptr(v), ctypes.c_uint32(ctr), _ptr(g))
+        return (J, g) if grad else J
+
+
+def optimal_control(S, u, lam):
+    """Weights and update from given costs S[K] and clamped samples u[K, T, 2]."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    K, T = u.shape[0], u.shape[1]
+    w = np.zeros(K)
+    vp = np.zeros((T, 2))
+    diag = np.zeros(4)
+    lib().orc_optimal_control(K, T, float(lam), _ptr(S), _ptr(u), _ptr(w), _ptr(vp), _ptr(diag))
+    return w, vp, diag
+
+
+def philox(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    out = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, out)
+    return np.array(list(out), dtype=np.uint32)
+
+
+def gaussian_pair(a, b):
+    z = np.zeros(2)
+    lib().orc_gaussian_pair(ctypes.c_uint32(a), ctypes.c_uint32(b), _ptr(z))
+    return z
+
+
+def backoff_gaussian(p):
+    return lib().orc_backoff_gaussian(float(p))
+
+
+def backoff_cantelli(p):
+    return lib().orc_backoff_cantelli(float(p))
