@@ -21,12 +21,20 @@ def _di_mats(dt):
     return A, B
 
 
-@pytest.mark.parametrize("with_sigma0", [False, True])
-def test_linear_gaussian_moments_match_closed_form(with_sigma0):
+CORRELATED_W = np.array([[0.010, 0.004, 0.002, 0.000],
+                         [0.004, 0.020, 0.000, -0.003],
+                         [0.002, 0.000, 0.015, 0.005],
+                         [0.000, -0.003, 0.005, 0.012]])
+
+
+@pytest.mark.parametrize("with_sigma0,correlated", [(False, False), (True, False), (False, True)])
+def test_linear_gaussian_moments_match_closed_form(with_sigma0, correlated):
     """Linear dynamics with additive Gaussian noise: mean_{k+1} = A mean_k + B u_k and
-    Cov_{k+1} = A Cov_k A^T + q I (the analytic belief dynamics mentioned in Sec. IV-C).
+    Cov_{k+1} = A Cov_k A^T + Sigma_w (the analytic belief dynamics mentioned in Sec. IV-C).
     Monte-Carlo moments must sit within a few standard errors of them."""
     p = workload.double_integrator_problem(K=2, M=40000, T=8, q_w=0.01)
+    if correlated:
+        p.Sigma_w = CORRELATED_W
     o = oracle.Oracle(p)
     x0 = np.array([0.5, -1.0, 1.0, 0.2], np.float32)
     v = workload.random_nominal(p, 3, scale=(1.0, 1.0))
@@ -44,7 +52,7 @@ def test_linear_gaussian_moments_match_closed_form(with_sigma0):
         cov = np.zeros((4, 4)) if Sig0 is None else Sig0.astype(float)
         for t in range(p.T):
             mean = A @ mean + B @ r["u"][k, t]
-            cov = A @ cov @ A.T + 0.01 * np.eye(4)
+            cov = A @ cov @ A.T + np.asarray(p.Sigma_w)
             mc_mean, mc_cov = r["mean"][k, t + 1], r["cov"][k, t + 1]
             sd_mean = np.sqrt(np.diag(cov) / M)
             zmax = max(zmax, np.max(np.abs(mc_mean - mean) / sd_mean))
@@ -178,6 +186,7 @@ def test_oracle_matches_literal_brute_force(case):
             x0[3] = 0.1
     else:
         p = workload.double_integrator_problem(K=4, M=4, T=3)
+        p.Sigma_w = CORRELATED_W
         x0 = workload.random_state(p, 9)
     v = workload.random_nominal(p, 10)
     r = oracle.Oracle(p).solve(x0, v, ctr=77, want_cov=True)
