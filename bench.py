@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""Benchmark of the BSS-MPPI hot path: particle-steps/s of one controller's solve step.
+
+A step is one pass of the whole path on the racing workload K=4096 control samples, M=64
+particles, T=40 steps (6-state dynamic bicycle, 5 Euler substeps): control noise, clamp,
+disturbance draws, particle rollout, per-step belief moments, barrier and cost (rollout kernel),
+weights and update (update kernel), then the warm-start shift. Inputs are resident on the device;
+the L2 cache is flushed (a 256 MiB write) before every timed step, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line. Under torchrun (N > 1) every rank solves its own controller (replicas on
+independent tracks; no collective on the data path) and rank 0 prints the whole-job throughput
+from the slowest rank's time. `--impl reference` times the FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workload  # noqa: E402
+
+METRIC = "particle-steps/s (K*M*T per solve)"
+# Device facts used for the ALU roofline (GB300: 152 SMs, 128 FP32 lanes per SM, max SM clock).
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def algorithmic_flops_per_particle_step(prob) -> float:
+    """FP32-equivalent operations the method needs per particle-step (one particle, one dt).
+
+    Counting convention: add, sub, mul, min, max, compare, floor and each integer Philox operation
+    = 1; fma = 2; division, reciprocal, square root = 4; each of exp, log, sin, cos, atan = 8
+    (sincos = 16). Counted from the method's formulas (model, noise, moments), not from any kernel.
+    """
+    if prob.model == workload.MODEL_BICYCLE6:
+        # per Euler substep: floor on v_x 1, 1/v_x 4, front/rear slip 2x(2 + 1 + 8 + 1),
+        # two tyre forces 2x(1 + 8 + 1 + 8 + 1), curvature lookup 7, sincos(e_psi) 16,
+        # s' 9, v_x' 5, v_y' 5, r' 5, e_psi' 2, e_y' 3, six Euler fmas 12
+        substep = 1 + 4 + 2 * 12 + 2 * 19 + 7 + 16 + 9 + 5 + 5 + 5 + 2 + 3 + 12
+        model = prob.n_sub * substep
+        nx = 6
+    else:
+        model = 4 * 2 + 2 * 2  # exact ZOH step: 4 + 2 fmas
+        nx = 4
+    pairs = (nx + 1) // 2
+    philox_calls = (pairs + 1) // 2
+    philox = philox_calls * 10 * 10       # 10 rounds x (2 wide multiplies = 4, 2 three-way xors = 4, 2 key adds)
+    box_muller = pairs * (2 + 8 + 1 + 4 + 16 + 2)
+    disturbance = nx * (nx + 1) // 2 * 2 + nx  # L_w z (fmas) and x += w
+    moments = 2 * nx + 3                   # mean sums and the e_y second moment
+    return float(model + philox + box_muller + disturbance + moments)
+
+
+# ------------------------------------------------------------------------------------------------
+def _problem(name: str, rank: int = 0):
+    if name == "racing_K4096_M64_T40":
+        p = workload.config1()
+    elif name == "racing_K256_M16_T20":
+        p = workload.config0()
+    elif name == "racing_K16384_M128_T60":
+        p = workload.config3(1.0)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    p.seed = int(p.seed) + 1000 * rank  # replicas: independent random streams per rank
+    return p
+
+
+def _workload_desc(p, name):
+    return {"workload": name, "K": p.K, "M": p.M, "T": p.T, "model": "dynamic bicycle (6 states)",
+            "n_sub": p.n_sub, "track": "seeded Fourier-perturbed circle, R=60 m, half-width 3 m",
+            "l2": "flushed before every timed step (256 MiB device write, outside the timed events)"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+def run_cpu_baseline(p, budget_s: float = 12.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the same solve."""
+    import oracle
+
+    o = oracle.Oracle(p)
+    x0 = workload.racing_x0(p)
+    v = np.zeros((p.T, 2), np.float32)
+    k = 8
+    t0 = time.perf_counter()
+    o.solve(x0, v, 0, k_range=(0, k))
+    dt = time.perf_counter() - t0
+    k = int(min(p.K, max(8, k * budget_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    o.solve(x0, v, 0, k_range=(0, k))
+    dt = time.perf_counter() - t0
+    return {"value": k * p.M * p.T / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"rollout and cost of the first {k} of the {p.K} control samples of one solve "
+                      f"({k * p.M * p.T} particle-steps, {dt:.1f} s, FP64, 1 thread)"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, a bounded sample of the workload per step."""
+    import oracle
+
+    p = _problem(args.workload)
+    o = oracle.Oracle(p)
+    x0 = workload.racing_x0(p)
+    v = np.zeros((p.T, 2), np.float32)
+    k_step = max(1, min(p.K, args.ref_samples))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = o.solve(x0, v, i, k_range=(0, k_step))
+        oracle.optimal_control(r["S"][:k_step], r["u"][:k_step], float(p.lam))
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    mean_s = statistics.fmean(times)
+    value = k_step * p.M * p.T / mean_s
+    sample = (f"each step: rollout, cost, weights and update of the first {k_step} of the {p.K} control "
+              f"samples of one solve ({k_step * p.M * p.T} particle-steps), FP64, 1 thread")
+    return {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": _workload_desc(p, args.workload),
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2408_00494_gb300 import bssmppi
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    p = _problem(args.workload, rank)
+    ctl = bssmppi.Controller(p, stream=stream)
+    h = ctl.h
+    x0 = torch.as_tensor(workload.racing_x0(p), device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+
+    def step():
+        bssmppi.solve(h, x0)       # resident nominal in, v+ resident out
+        bssmppi.shift(h, None, 1)  # warm start for the next solve
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    bssmppi.timing(h, args.steps)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    roll_ms, upd_ms = bssmppi.timing_read(h, args.steps)
+    bssmppi.timing(h, 0)
+
+    # end to end through the C ABI with host buffers (H2D of the state and nominal, D2H of v+ and u0)
+    x0_h = workload.racing_x0(p)
+    v_h = np.zeros((p.T, 2), np.float32)
+    u0_h = np.zeros(2, np.float32)
+    e2e_s = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bssmppi.solve_host(h, x0_h, None, v_h, u0_h)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_s.append(dt)
+    ctl.close()
+
+    mean_ms = statistics.fmean(step_ms)
+    mean_roll = statistics.fmean(roll_ms)
+    mean_e2e = statistics.fmean(e2e_s)
+    stats = torch.tensor([mean_ms, mean_roll, mean_e2e * 1e3, t_wall], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(stats, op=torch.distributed.ReduceOp.MAX)
+    mean_ms, mean_roll, mean_e2e_ms, t_wall = stats.tolist()
+    units = p.K * p.M * p.T
+    value = world * units / (mean_ms * 1e-3)
+    flops = algorithmic_flops_per_particle_step(p) * units
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (mean_roll * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _workload_desc(p, args.workload),
+        "solves_per_s": world * 1e3 / mean_ms,
+        "phases_ms": {"rollout": mean_roll, "weights_update": statistics.fmean(upd_ms)},
+        "roofline": {"bound": "alu", "kernel": "rollout_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 (fma) x 2070 MHz max SM clock",
+                     "flops_per_particle_step": algorithmic_flops_per_particle_step(p)},
+        "e2e": {"value": world * units / (mean_e2e_ms * 1e-3), "unit": "particle-steps/s",
+                "h2d_bytes_per_step": 4 * (p.nx + 2 * p.T), "d2h_bytes_per_step": 4 * (2 * p.T + 2)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = run_cpu_baseline(p, args.cpu_budget)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="racing_K4096_M64_T40")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-samples", type=int, default=128)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    try:
+        line = run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

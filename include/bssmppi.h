@@ -1,0 +1,209 @@
+/*
+ * bssmppi.h - C ABI of the GB300 (sm_103a) BSS-MPPI library.
+ *
+ * BSS-MPPI (Yin, Tsiotras, Berntorp, "Chance-Constrained Information-Theoretic Stochastic Model
+ * Predictive Control with Safety Shielding") solves, at every control step, the chance-constrained
+ * stochastic optimal control problem of Sec. III (problem "BSSMPPIProblemformulation"): minimise the
+ * expected trajectory cost over the nominal control sequence v subject to disturbed dynamics
+ * x_{k+1} = f(x_k, u_k, w_k) and per-step chance constraints Pr(x_k in F) > 1 - P_fail. One solve
+ * is Algorithm 1's body: K perturbed control sequences are each rolled out over M disturbance
+ * particles for T steps (Algorithm 2 gives the particle mean and covariance of every step), the
+ * belief barrier of Eq. "DCBF" and the penalty of Eq. "cbfpenalty" enter the cost, and the costs
+ * give the weights of Eq. "Weights" and the update of Eq. "MPPI update law".
+ *
+ * Notation bridge to the paper: K here = the paper's M (control samples), M here = the paper's N
+ * (particles per sample), T here = the paper's K (horizon), gamma here = the paper's beta (DCBF
+ * decay rate, factor (1 - gamma)), ctrl_w = the paper's gamma (control-cost weight of Eq.
+ * "TrajectoryCost"), delta = the per-boundary chance level epsilon of Eq. "track chance constraint".
+ *
+ * Conventions (all entry points):
+ *  - Pointers named d_* are device pointers (global memory of the current CUDA device); h_* are host
+ *    pointers. All arrays are dense, row-major, float32 unless stated. The caller owns every pointer
+ *    it passes; the library never frees or keeps them beyond the call (except where stated).
+ *  - A handle owns its device buffers and runs all work on the CUDA stream given at create time.
+ *    Calls taking d_* pointers only enqueue work (stream-ordered, asynchronous) unless stated.
+ *  - Return value: BSSMPPI_OK (0) or a negative bssmppi_status. Arguments are validated on the host
+ *    before any launch; on error nothing is enqueued and bssmppi_last_error() explains why.
+ *  - There is no CPU fallback: without a usable CUDA device every compute call fails with
+ *    BSSMPPI_ECUDA.
+ */
+#ifndef BSSMPPI_H
+#define BSSMPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSSMPPI_ABI_VERSION 1u
+#define BSSMPPI_NU 2          /* controls: [steer delta (rad), acceleration (m/s^2)] */
+#define BSSMPPI_NX_MAX 6
+#define BSSMPPI_K_MAX (1 << 20)
+#define BSSMPPI_M_MAX 256
+#define BSSMPPI_T_MAX 256
+#define BSSMPPI_NTRACK_MAX 16384
+#define BSSMPPI_NDIAG 4       /* diagnostics: {beta = min S, eta = sum of omega, ESS = eta^2 / sum omega^2,
+                                 free energy beta - lambda ln(eta / K)} */
+
+typedef enum bssmppi_status {
+    BSSMPPI_OK = 0,
+    BSSMPPI_EINVAL = -1,   /* invalid argument or parameter */
+    BSSMPPI_ENOMEM = -2,   /* device or pinned-host allocation failed */
+    BSSMPPI_ECUDA = -3,    /* a CUDA runtime call failed (no device, launch error, ...) */
+    BSSMPPI_ETIMEOUT = -4, /* a bounded device wait gave up */
+    BSSMPPI_EBUSY = -5,    /* resource temporarily exhausted */
+    BSSMPPI_ENOTSUP = -6   /* valid but unsupported combination */
+} bssmppi_status;
+
+typedef enum bssmppi_model {
+    BSSMPPI_MODEL_BICYCLE6 = 0,  /* dynamic single-track vehicle, x = [v_x, v_y, r, e_psi, e_y, s] */
+    BSSMPPI_MODEL_DOUBLE_INT4 = 1 /* planar double integrator, x = [p_x, p_y, v_x, v_y] (test model) */
+} bssmppi_model;
+
+/* Which internal buffer of the last solve bssmppi_read() copies. */
+typedef enum bssmppi_buffer {
+    BSSMPPI_BUF_S = 0,     /* K trajectory costs S_k (Eq. "TrajectoryCost" with the augmented costs) */
+    BSSMPPI_BUF_W = 1,     /* K normalised weights omega_k / sum omega (Eq. "Weights") */
+    BSSMPPI_BUF_EPS = 2,   /* K*T*2 effective perturbations u_{k,t} - v_t (u clamped to the bounds) */
+    BSSMPPI_BUF_MEAN = 3,  /* K*(T+1)*nx particle means per step (record_moments=1 only) */
+    BSSMPPI_BUF_VAR = 4,   /* K*(T+1)*nx unbiased particle variances per step (record_moments=1 only) */
+    BSSMPPI_BUF_DIAG = 5,  /* BSSMPPI_NDIAG floats */
+    BSSMPPI_BUF_V = 6      /* T*2 resident nominal control sequence */
+} bssmppi_buffer;
+
+/*
+ * Problem parameters, copied at create. Sec. III states the problem: initial state x_0 (and its
+ * covariance Sigma_{x_0}, Algorithm 1), control noise covariance Sigma_eps (Sec. II), disturbance
+ * law w ~ N(0, Sigma_w) (Sec. V-A), chance level delta (Eq. "track chance constraint"), DCBF decay
+ * rate gamma (Eq. "DCBF_constraint2") and temperature lambda (Eq. "Weights").
+ */
+typedef struct bssmppi_params {
+    int32_t K, M, T;      /* samples (1..BSSMPPI_K_MAX), particles (2..BSSMPPI_M_MAX), horizon (1..BSSMPPI_T_MAX) */
+    int32_t n_sub;        /* explicit-Euler substeps per dt (bicycle model), 1..64 */
+    int32_t model;        /* bssmppi_model */
+    int32_t ey_index;     /* state component bounded by |x_i| <= w_T (4 = e_y for the bicycle) */
+    float dt, mass, Iz, lf, lr, tire_B, tire_C, mu, g, vx_floor; /* model constants (SI units) */
+    float u_min[2], u_max[2];  /* control bounds; sampled controls are clamped to them */
+    float lambda;         /* temperature, > 0 */
+    float delta;          /* per-boundary chance level, 0 < delta < 0.5; nu = sqrt(2) erfinv(1 - 2 delta) */
+    float gamma;          /* DCBF decay rate, 0 < gamma < 1 */
+    float ctrl_w;         /* weight of v_t^T Sigma_eps^-1 u_t in S */
+    float C_safe;         /* weight C of the safe-condition violation cost */
+    float C_obs;          /* collision penalty added when |mean e_y| > w_T */
+    float w_T;            /* track half-width */
+    float x_goal[6], Q[6], Qf[6]; /* quadratic running and terminal cost (diagonal weights) */
+    float track_len;      /* length of the closed centre line (m), > 0 */
+    int32_t n_track;      /* curvature table size, a power of two in 2..BSSMPPI_NTRACK_MAX */
+    const float* track_kappa; /* host pointer to n_track curvature samples kappa(i * track_len / n_track); copied */
+    double Sigma_eps[4];  /* 2x2 SPD control-noise covariance */
+    double Sigma_w[36];   /* nx x nx PSD disturbance covariance (leading dimension nx) */
+    uint64_t seed;        /* Philox key */
+    int32_t crn_disturbance; /* 1: disturbance draws shared by all K samples (common random numbers) */
+    int32_t compensated;  /* 1: Welford/Chan moments and Kahan sums; 0: naive sums (precision study) */
+    int32_t record_moments; /* 1: keep per-step particle means and variances (BSSMPPI_BUF_MEAN/VAR) */
+    int32_t reserved;     /* must be 0 */
+} bssmppi_params;
+
+typedef struct bssmppi_ctx* bssmppi_t;
+
+/* Library identification. bssmppi_params_size() lets bindings check their struct layout. */
+uint32_t bssmppi_abi_version(void);
+size_t bssmppi_params_size(void);
+
+/*
+ * Create a controller handle for one problem (Sec. III). `cuda_stream` is a cudaStream_t (NULL = the
+ * legacy default stream) on the current device; all of the handle's work runs on it. Allocates the
+ * handle's device buffers (sample costs, weights, perturbations, the resident nominal sequence v
+ * (zero-initialised), the device-resident solve counter (0) and the reduction scratch) and copies
+ * the curvature table. Synchronous. Returns EINVAL for out-of-range parameters, ENOMEM or ECUDA.
+ * On success *out is a new handle; on failure *out is NULL and bssmppi_last_error(NULL) says why.
+ */
+int bssmppi_create(const bssmppi_params* params, void* cuda_stream, bssmppi_t* out);
+
+/*
+ * One BSS-MPPI solve (Algorithm 1, one iteration of its outer loop, lines from the state estimate
+ * to OptimalControl, with Algorithm 2 for the mean and covariance propagation):
+ *   d_x0     [nx]      state estimate x_bar_0 (device).
+ *   d_Sigma0 [nx*nx]   covariance Sigma_{x_0} of the estimate, or NULL for a known state. When given,
+ *                      the particles start at x_bar_0 + L_0 xi with L_0 its Cholesky factor.
+ *   d_v      [T*2]     in: nominal sequence v; out: updated sequence v+ (Eq. "MPPI update law").
+ *                      NULL: use and update the handle's resident nominal sequence instead.
+ *   d_u0     [2]       out: first control v+_0 to execute, or NULL.
+ * The handle's resident sequence always ends equal to v+. The solve uses the device-resident
+ * counter for its random numbers and then increments it on the device. Asynchronous.
+ */
+int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* d_v, float* d_u0);
+
+/*
+ * The same solve with host buffers: copies h_x0 (and h_Sigma0 if non-NULL) and h_v (NULL = resident)
+ * to the device, solves, copies v+ back into h_v (if non-NULL) and the first control into h_u0 (if
+ * non-NULL), and waits for the stream. Synchronous; the host pointers may be pageable.
+ */
+int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, float* h_v, float* h_u0);
+
+/*
+ * Warm start (Algorithm 1, "v <- v_safe", followed by the usual receding-horizon shift): shift the
+ * sequence left by n steps, repeating its last element: v[t] <- v[min(t + n, T - 1)].
+ * d_v [T*2] device sequence, or NULL for the resident one. 0 <= n <= T. Asynchronous.
+ */
+int bssmppi_shift(bssmppi_t h, float* d_v, int32_t n);
+
+/* Free the handle and its device buffers after waiting for its stream. NULL is accepted. */
+int bssmppi_destroy(bssmppi_t h);
+
+/* Human-readable reason for the last failure on this handle (h = NULL: the last failed create on
+ * this thread). The string stays valid until the next call on the same handle / thread. */
+const char* bssmppi_last_error(bssmppi_t h);
+
+/* Solve counter (the Philox counter word that distinguishes solves). set: stream-ordered write;
+ * get: waits for the stream, then reads. */
+int bssmppi_set_counter(bssmppi_t h, uint32_t counter);
+int bssmppi_get_counter(bssmppi_t h, uint32_t* counter);
+
+/* Overwrite the resident nominal sequence from d_v [T*2] (device). Asynchronous. */
+int bssmppi_set_nominal(bssmppi_t h, const float* d_v);
+
+/*
+ * Copy an internal buffer of the last solve (bssmppi_buffer `which`) into the device array d_dst of
+ * `bytes` bytes (must be at least the buffer's size; see bssmppi_buffer). Asynchronous. MEAN and VAR
+ * need record_moments = 1 (else ENOTSUP).
+ */
+int bssmppi_read(bssmppi_t h, int32_t which, void* d_dst, size_t bytes);
+
+/*
+ * Per-phase timing with CUDA events recorded on the handle's stream around the rollout kernel and
+ * around the weights/update kernel of every solve. bssmppi_timing(h, n) with n > 0 starts recording
+ * the next n solves (older records are dropped; n <= 4096), n = 0 stops. bssmppi_timing_read waits
+ * for the recorded events and writes up to `max` durations in milliseconds (rollout_ms[i],
+ * update_ms[i], either may be NULL) for the solves recorded so far; *count receives how many.
+ */
+int bssmppi_timing(bssmppi_t h, int32_t n);
+int bssmppi_timing_read(bssmppi_t h, float* h_rollout_ms, float* h_update_ms, int32_t max, int32_t* count);
+
+/*
+ * Deterministic model step x_{k+1} = f(x_k, u_k) (Eq. "DeterministicNonlinearSystem"; n_sub Euler
+ * substeps of the handle's model, no disturbance) for n independent states: d_x [n*nx], d_u [n*2],
+ * d_x_next [n*nx], device. Used to check the model on its own. Asynchronous.
+ */
+int bssmppi_model_step(bssmppi_t h, const float* d_x, const float* d_u, float* d_x_next, int64_t n);
+
+/*
+ * Philox4x32-10 (Salmon et al., SC'11), the counter-based generator of every random number the solve
+ * draws: d_out[4i..4i+3] = Philox(counter d_ctr[4i..4i+3], key (seed & 0xffffffff, seed >> 32)) for
+ * i < n. Device arrays of 4n uint32. Runs on `cuda_stream` (cudaStream_t, NULL = default).
+ */
+int bssmppi_philox4x32_10(const uint32_t* d_ctr, uint64_t seed, uint32_t* d_out, int64_t n, void* cuda_stream);
+
+/*
+ * Box-Muller Gaussians as the solve draws them: for each word pair (a, b) = d_words[2i], d_words[2i+1],
+ * u1 = ((a >> 8) + 1) 2^-24, u2 = (b >> 8) 2^-24, d_z[2i] = sqrt(-2 ln u1) cos(2 pi u2),
+ * d_z[2i+1] = sqrt(-2 ln u1) sin(2 pi u2). n pairs; device arrays.
+ */
+int bssmppi_box_muller(const uint32_t* d_words, float* d_z, int64_t n, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSSMPPI_H */

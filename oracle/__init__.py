@@ -64,6 +64,7 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         u32p = ctypes.POINTER(ctypes.c_uint32)
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_philox4x32_10_batch.argtypes = [ctypes.c_int64, u32p, u32p, u32p]
         L.orc_gaussian_pair.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _dp]
         L.orc_backoff_gaussian.restype = ctypes.c_double
         L.orc_backoff_gaussian.argtypes = [ctypes.c_double]
@@ -191,6 +192,16 @@ def philox(ctr, key):
     out = (ctypes.c_uint32 * 4)()
     lib().orc_philox4x32_10(c, k, out)
     return np.array(list(out), dtype=np.uint32)
+
+
+def philox_batch(ctr, key):
+    """Philox of n counters (uint32 array of shape (n, 4))."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32)
+    out = np.zeros_like(ctr)
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib().orc_philox4x32_10_batch(ctr.shape[0], ctr.ctypes.data_as(u32p), k, out.ctypes.data_as(u32p))
+    return out
 
 
 def gaussian_pair(a, b):

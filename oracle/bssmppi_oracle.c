@@ -48,6 +48,11 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+void orc_philox4x32_10_batch(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out)
+{
+    for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
 void orc_gaussian_pair(uint32_t a, uint32_t b, double z[2])
 {
     const double two_m24 = 1.0 / 16777216.0;
@@ -421,7 +426,7 @@ void orc_optimal_control(int K, int T, double lambda, const double* S, const dou
         if (w) w[m] = wh;
         sq += wh * wh;
     }
-    if (diag) { diag[0] = beta; diag[1] = eta; diag[2] = 1.0 / sq; diag[3] = 0.0; }
+    if (diag) { diag[0] = beta; diag[1] = eta; diag[2] = 1.0 / sq; diag[3] = beta - lambda * log(eta / K); }
     free(om);
 }
 

@@ -46,12 +46,14 @@ typedef struct orc_problem {
 
 /* Per-solve outputs; any pointer may be NULL. Sizes: S[K], u[K*T*2] (clamped samples), w[K]
  * (normalised weights), v_plus[T*2], mean[K*(T+1)*nx], cov[K*(T+1)*nx*nx], margin[K]
- * (min over steps of ||mean e_y| - w_T|), h[K*(T+1)], diag[4] = {beta, eta, ESS, 0}. */
+ * (min over steps of ||mean e_y| - w_T|), h[K*(T+1)], diag[4] = {beta, eta, ESS, free energy
+ * beta - lambda ln(eta / K)}. */
 typedef struct orc_outputs {
     double *S, *u, *w, *v_plus, *mean, *cov, *margin, *h, *diag;
 } orc_outputs;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_philox4x32_10_batch(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out);
 void orc_gaussian_pair(uint32_t a, uint32_t b, double z[2]);
 double orc_backoff_gaussian(double p);  /* sqrt(2) erfinv(1 - 2p) */
 double orc_backoff_cantelli(double p);  /* sqrt((1 - p) / p) */

@@ -1,0 +1,272 @@
+"""Thin Python binding of the C ABI in include/bssmppi.h (argument marshalling only).
+
+Every function has the C entry point's name without the ``bssmppi_`` prefix and takes torch CUDA
+tensors where the C function takes device pointers (the tensor's storage is passed as is) and
+numpy arrays where it takes host pointers. All compute happens in libbssmppi.so; if the library is
+missing or cannot be loaded, every call raises. There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+NU = 2
+NDIAG = 4
+BUF_S, BUF_W, BUF_EPS, BUF_MEAN, BUF_VAR, BUF_DIAG, BUF_V = range(7)
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUSY", -6: "ENOTSUP"}
+
+
+class BssmppiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """Mirror of struct bssmppi_params (layout checked against bssmppi_params_size())."""
+
+    _fields_ = [
+        ("K", ctypes.c_int32), ("M", ctypes.c_int32), ("T", ctypes.c_int32), ("n_sub", ctypes.c_int32),
+        ("model", ctypes.c_int32), ("ey_index", ctypes.c_int32),
+        ("dt", ctypes.c_float), ("mass", ctypes.c_float), ("Iz", ctypes.c_float), ("lf", ctypes.c_float),
+        ("lr", ctypes.c_float), ("tire_B", ctypes.c_float), ("tire_C", ctypes.c_float), ("mu", ctypes.c_float),
+        ("g", ctypes.c_float), ("vx_floor", ctypes.c_float),
+        ("u_min", ctypes.c_float * 2), ("u_max", ctypes.c_float * 2),
+        ("lam", ctypes.c_float), ("delta", ctypes.c_float), ("gamma", ctypes.c_float), ("ctrl_w", ctypes.c_float),
+        ("C_safe", ctypes.c_float), ("C_obs", ctypes.c_float), ("w_T", ctypes.c_float),
+        ("x_goal", ctypes.c_float * 6), ("Q", ctypes.c_float * 6), ("Qf", ctypes.c_float * 6),
+        ("track_len", ctypes.c_float), ("n_track", ctypes.c_int32),
+        ("track_kappa", ctypes.POINTER(ctypes.c_float)),
+        ("Sigma_eps", ctypes.c_double * 4), ("Sigma_w", ctypes.c_double * 36),
+        ("seed", ctypes.c_uint64),
+        ("crn_disturbance", ctypes.c_int32), ("compensated", ctypes.c_int32),
+        ("record_moments", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libbssmppi.so from the package's _lib/ directory (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u32, u64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                  ctypes.c_uint64, ctypes.c_size_t)
+    sig = {
+        "bssmppi_abi_version": (u32, []),
+        "bssmppi_params_size": (sz, []),
+        "bssmppi_create": (ctypes.c_int, [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
+        "bssmppi_solve": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "bssmppi_solve_host": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "bssmppi_shift": (ctypes.c_int, [vp, vp, i32]),
+        "bssmppi_destroy": (ctypes.c_int, [vp]),
+        "bssmppi_last_error": (ctypes.c_char_p, [vp]),
+        "bssmppi_set_counter": (ctypes.c_int, [vp, u32]),
+        "bssmppi_get_counter": (ctypes.c_int, [vp, ctypes.POINTER(u32)]),
+        "bssmppi_set_nominal": (ctypes.c_int, [vp, vp]),
+        "bssmppi_read": (ctypes.c_int, [vp, i32, vp, sz]),
+        "bssmppi_timing": (ctypes.c_int, [vp, i32]),
+        "bssmppi_timing_read": (ctypes.c_int, [vp, vp, vp, i32, ctypes.POINTER(i32)]),
+        "bssmppi_model_step": (ctypes.c_int, [vp, vp, vp, vp, i64]),
+        "bssmppi_philox4x32_10": (ctypes.c_int, [vp, u64, vp, i64, vp]),
+        "bssmppi_box_muller": (ctypes.c_int, [vp, vp, i64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    if L.bssmppi_params_size() != ctypes.sizeof(Params):
+        raise RuntimeError("bssmppi_params layout mismatch between the binding and the library")
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    """Device pointer of a contiguous torch CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+        raise ValueError("expected a contiguous float32 numpy array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(rc, h=None):
+    if rc != 0:
+        msg = load().bssmppi_last_error(h)
+        raise BssmppiError(rc, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_params(prob, record_moments: bool = False, compensated: bool | None = None) -> Params:
+    """Fill the C struct from a problem description (workload.Problem or any object with its fields)."""
+    p = Params()
+    for name in ("K", "M", "T", "n_sub", "model", "ey_index"):
+        setattr(p, name, int(getattr(prob, name)))
+    for name in ("dt", "mass", "Iz", "lf", "lr", "tire_B", "tire_C", "mu", "g", "vx_floor", "delta", "gamma",
+                 "ctrl_w", "C_safe", "C_obs", "w_T"):
+        setattr(p, name, float(getattr(prob, name)))
+    p.lam = float(prob.lam)
+    for i in range(2):
+        p.u_min[i] = float(prob.u_min[i])
+        p.u_max[i] = float(prob.u_max[i])
+    for i in range(6):
+        p.x_goal[i] = float(prob.x_goal[i])
+        p.Q[i] = float(prob.Q[i])
+        p.Qf[i] = float(prob.Qf[i])
+    kappa = np.ascontiguousarray(np.asarray(prob.kappa, dtype=np.float32))
+    p._kappa_keepalive = kappa
+    p.track_kappa = kappa.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    p.n_track = int(kappa.size)
+    p.track_len = float(prob.track_len)
+    se = np.asarray(prob.Sigma_eps, dtype=np.float64).reshape(-1)
+    for i in range(4):
+        p.Sigma_eps[i] = float(se[i])
+    sw = np.asarray(prob.Sigma_w, dtype=np.float64).reshape(-1)
+    for i in range(sw.size):
+        p.Sigma_w[i] = float(sw[i])
+    p.seed = int(prob.seed) & 0xFFFFFFFFFFFFFFFF
+    p.crn_disturbance = int(prob.crn_disturbance)
+    p.compensated = int(prob.compensated if compensated is None else compensated)
+    p.record_moments = int(record_moments)
+    p.reserved = 0
+    return p
+
+
+# ---- the C entry points, one Python function each ---------------------------------------------
+
+def abi_version() -> int:
+    return load().bssmppi_abi_version()
+
+
+def params_size() -> int:
+    return load().bssmppi_params_size()
+
+
+def create(params: Params, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().bssmppi_create(ctypes.byref(params), _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def solve(h, x0, Sigma0=None, v=None, u0=None):
+    _check(load().bssmppi_solve(h, _ptr(x0), _ptr(Sigma0), _ptr(v), _ptr(u0)), h)
+
+
+def solve_host(h, x0, Sigma0=None, v=None, u0=None):
+    _check(load().bssmppi_solve_host(h, _hptr(x0), _hptr(Sigma0), _hptr(v), _hptr(u0)), h)
+
+
+def shift(h, v=None, n: int = 1):
+    _check(load().bssmppi_shift(h, _ptr(v), int(n)), h)
+
+
+def destroy(h):
+    _check(load().bssmppi_destroy(h))
+
+
+def last_error(h=None) -> str:
+    msg = load().bssmppi_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def set_counter(h, counter: int):
+    _check(load().bssmppi_set_counter(h, ctypes.c_uint32(counter)), h)
+
+
+def get_counter(h) -> int:
+    c = ctypes.c_uint32()
+    _check(load().bssmppi_get_counter(h, ctypes.byref(c)), h)
+    return c.value
+
+
+def set_nominal(h, v):
+    _check(load().bssmppi_set_nominal(h, _ptr(v)), h)
+
+
+def read(h, which: int, dst):
+    _check(load().bssmppi_read(h, int(which), _ptr(dst), dst.numel() * dst.element_size()), h)
+
+
+def timing(h, n: int):
+    _check(load().bssmppi_timing(h, int(n)), h)
+
+
+def timing_read(h, max_n: int = 4096):
+    """Per-phase durations (ms) of the solves recorded since timing(h, n): (rollout, update) arrays."""
+    roll = np.zeros(max_n, np.float32)
+    upd = np.zeros(max_n, np.float32)
+    n = ctypes.c_int32()
+    _check(load().bssmppi_timing_read(h, ctypes.c_void_p(roll.ctypes.data), ctypes.c_void_p(upd.ctypes.data),
+                                      int(max_n), ctypes.byref(n)), h)
+    return roll[: n.value].copy(), upd[: n.value].copy()
+
+
+def model_step(h, x, u, x_next):
+    _check(load().bssmppi_model_step(h, _ptr(x), _ptr(u), _ptr(x_next), x.shape[0]), h)
+
+
+def philox4x32_10(ctr, seed: int, out, stream=None):
+    _check(load().bssmppi_philox4x32_10(_ptr(ctr), ctypes.c_uint64(seed), _ptr(out), ctr.numel() // 4,
+                                        _stream_handle(stream)))
+
+
+def box_muller(words, z, stream=None):
+    _check(load().bssmppi_box_muller(_ptr(words), _ptr(z), words.numel() // 2, _stream_handle(stream)))
+
+
+class Controller:
+    """Owns one handle: the problem, its device buffers and its stream (convenience wrapper)."""
+
+    def __init__(self, prob, record_moments=False, compensated=None, stream=None):
+        import torch
+        self.prob = prob
+        self.params = make_params(prob, record_moments=record_moments, compensated=compensated)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = create(self.params, self.stream)
+        self.nx = prob.nx
+
+    def close(self):
+        if self.h is not None:
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def buffer(self, which):
+        import torch
+        K, T, nx = self.prob.K, self.prob.T, self.nx
+        shape = {BUF_S: (K,), BUF_W: (K,), BUF_EPS: (K, T, 2), BUF_MEAN: (K, T + 1, nx),
+                 BUF_VAR: (K, T + 1, nx), BUF_DIAG: (NDIAG,), BUF_V: (T, 2)}[which]
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+        read(self.h, which, out)
+        return out

@@ -1,0 +1,220 @@
+// Device building blocks of the BSS-MPPI hot path (sm_103a): the counter-based random numbers,
+// the vehicle model, and the particle-moment merges. FP32 throughout; no FP64 on the device.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bss {
+
+constexpr int kWarp = 32;
+constexpr int kNxMax = 6;
+
+// Everything a solve's kernels need, derived on the host at create time and passed by value
+// (kernel parameter space), so several controllers can run concurrently without global state.
+struct DevParams {
+    int K, M, T, n_sub, nx;
+    int seg;          // lanes per control sample (power of two <= 32)
+    int spw;          // control samples per warp (32 / seg)
+    int uniform;      // 1: every lane of a segment holds exactly P valid particles
+    int ey, crn, record, n_track_mask;
+    uint32_t key0, key1;
+    float dt, h, inv_m, inv_Iz, lf, lr, tB, tC, Df, Dr, vx_floor;
+    float umin0, umin1, umax0, umax1;
+    float Le00, Le10, Le11;          // Cholesky factor of Sigma_eps
+    float Si00, Si01, Si10, Si11;    // Sigma_eps^-1
+    float Lw[21];                    // Cholesky factor of Sigma_w, packed lower triangle by rows
+    float inv_lambda, nu, one_m_gamma, ctrl_w, Csafe, Cobs, wT;
+    float xg[6], Q[6], Qf[6];
+    float track_scale;               // n_track / track_len
+    float Mf, invM, invM1;           // M, 1/M, 1/(M-1)
+    const float* kappa;              // device curvature table, n_track + 1 entries (last = first)
+};
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC'11): ten rounds of the 4x32 S-box (two 32x32->64 multiplies by 0xD2511F53 and 0xCD9E8D57,
+// xors with the other words and the round key), the key advanced by the Weyl increments
+// 0x9E3779B9 and 0xBB67AE85 between rounds. Kept entirely in registers.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Counter layout of the solve's streams: word 0 = step | (call << 16), word 1 = particle,
+// word 2 = sample, word 3 = (stream << 28) | (solve counter & 0x0fffffff).
+enum : uint32_t { kStreamControl = 0u, kStreamDisturbance = 1u, kStreamInitial = 3u };
+
+__device__ __forceinline__ uint4 draw_words(const DevParams& P, uint32_t step, uint32_t call, uint32_t particle,
+                                            uint32_t sample, uint32_t stream, uint32_t ctr)
+{
+    return philox4x32_10(make_uint4(step | (call << 16), particle, sample, (stream << 28) | (ctr & 0x0fffffffu)),
+                         P.key0, P.key1);
+}
+
+// Box-Muller from two 32-bit words: u1 in (0, 1], u2 in [0, 1) from their top 24 bits (exact in
+// FP32), z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
+{
+    const float two_m24 = 5.9604644775390625e-08f;
+    const float u1 = (float)((a >> 8) + 1u) * two_m24;
+    const float u2 = (float)(b >> 8) * two_m24;
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    return make_float2(rad * cs, rad * sn);
+}
+
+// Standard normals of one draw (Gaussian pair i from call i/2, words 2(i%2), 2(i%2)+1).
+template <int NX>
+__device__ __forceinline__ void draw_normals(const DevParams& P, uint32_t step, uint32_t particle, uint32_t sample,
+                                             uint32_t stream, uint32_t ctr, float (&z)[NX])
+{
+    const uint4 w0 = draw_words(P, step, 0u, particle, sample, stream, ctr);
+    const float2 g0 = box_muller(w0.x, w0.y);
+    const float2 g1 = box_muller(w0.z, w0.w);
+    z[0] = g0.x; z[1] = g0.y; z[2] = g1.x; z[3] = g1.y;
+    if constexpr (NX > 4) {
+        const uint4 w1 = draw_words(P, step, 1u, particle, sample, stream, ctr);
+        const float2 g2 = box_muller(w1.x, w1.y);
+        z[4] = g2.x; z[5] = g2.y;
+    }
+}
+
+// x += L z with L packed lower-triangular by rows.
+template <int NX>
+__device__ __forceinline__ void add_correlated(const float* L, const float (&z)[NX], float (&x)[NX])
+{
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+        float w = 0.0f;
+#pragma unroll
+        for (int j = 0; j <= i; ++j) w = fmaf(L[i * (i + 1) / 2 + j], z[j], w);
+        x[i] += w;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dynamic single-track vehicle in the road-aligned frame. State [v_x, v_y, r, e_psi, e_y, ds]
+// where ds = s - s0 is the progress since the start of the rollout (kept relative so that FP32
+// rounding of the progress does not grow with the lap position). Lateral tyre forces follow the
+// simplified Pacejka law F_y = D sin(C atan(B alpha)), D = mu F_z with static axle loads.
+// ---------------------------------------------------------------------------------------------
+struct Control {
+    float steer, accel, sin_steer, cos_steer;
+};
+
+__device__ __forceinline__ float track_curvature(const DevParams& P, const float* __restrict__ kap, float s)
+{
+    const float x = s * P.track_scale;
+    const float fl = floorf(x);
+    const float f = x - fl;
+    const int i = ((int)fl) & P.n_track_mask;
+    const float k0 = kap[i], k1 = kap[i + 1];
+    return fmaf(f, k1 - k0, k0);
+}
+
+__device__ __forceinline__ void bicycle_substep(const DevParams& P, const float* __restrict__ kap, float s0,
+                                                const Control& u, float (&x)[6])
+{
+    const float vx = x[0], vy = x[1], r = x[2], ep = x[3], ey = x[4];
+    const float inv_vx = 1.0f / fmaxf(vx, P.vx_floor);
+    const float alpha_f = u.steer - atanf((vy + P.lf * r) * inv_vx);
+    const float alpha_r = -atanf((vy - P.lr * r) * inv_vx);
+    const float Ff = P.Df * sinf(P.tC * atanf(P.tB * alpha_f));
+    const float Fr = P.Dr * sinf(P.tC * atanf(P.tB * alpha_r));
+    const float kap_s = track_curvature(P, kap, s0 + x[5]);
+    float sp, cp;
+    sincosf(ep, &sp, &cp);
+    const float sdot = (vx * cp - vy * sp) / (1.0f - kap_s * ey);
+    const float dvx = u.accel - Ff * u.sin_steer * P.inv_m + vy * r;
+    const float dvy = (Ff * u.cos_steer + Fr) * P.inv_m - vx * r;
+    const float dr = (P.lf * Ff * u.cos_steer - P.lr * Fr) * P.inv_Iz;
+    const float dep = r - kap_s * sdot;
+    const float dey = vx * sp + vy * cp;
+    x[0] = fmaf(P.h, dvx, vx);
+    x[1] = fmaf(P.h, dvy, vy);
+    x[2] = fmaf(P.h, dr, r);
+    x[3] = fmaf(P.h, dep, ep);
+    x[4] = fmaf(P.h, dey, ey);
+    x[5] = fmaf(P.h, sdot, x[5]);
+}
+
+// Planar double integrator, exact zero-order-hold step.
+__device__ __forceinline__ void double_integrator_step(const DevParams& P, const Control& u, float (&x)[4])
+{
+    const float dt = P.dt, hdt2 = 0.5f * P.dt * P.dt;
+    x[0] = fmaf(hdt2, u.steer, fmaf(dt, x[2], x[0]));
+    x[1] = fmaf(hdt2, u.accel, fmaf(dt, x[3], x[1]));
+    x[2] = fmaf(dt, u.steer, x[2]);
+    x[3] = fmaf(dt, u.accel, x[3]);
+}
+
+// One full model step f(x, u) (n_sub substeps for the bicycle).
+template <int MODEL, int NX>
+__device__ __forceinline__ void model_step(const DevParams& P, const float* __restrict__ kap, float s0,
+                                           const Control& u, float (&x)[NX])
+{
+    if constexpr (MODEL == 0) {
+        for (int j = 0; j < P.n_sub; ++j) bicycle_substep(P, kap, s0, u, x);
+    } else {
+        double_integrator_step(P, u, x);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Running / terminal cost on the belief mean: (m - x_g)^T W (m - x_g) + C_obs 1[|m_ey| > w_T].
+// ---------------------------------------------------------------------------------------------
+template <int NX>
+__device__ __forceinline__ float state_cost(const DevParams& P, const float* W, const float (&m)[NX])
+{
+    float c = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+        const float d = m[i] - P.xg[i];
+        c = fmaf(W[i] * d, d, c);
+    }
+    return c + (fabsf(m[P.ey]) > P.wT ? P.Cobs : 0.0f);
+}
+
+// Belief barrier h = (w_T - nu sigma)^2 - m_ey^2.
+__device__ __forceinline__ float belief_barrier(const DevParams& P, float mean_ey, float var_ey)
+{
+    const float b = P.wT - P.nu * sqrtf(fmaxf(var_ey, 0.0f));
+    return b * b - mean_ey * mean_ey;
+}
+
+// Neumaier-compensated accumulation: sum + c carries the sum to about twice the working precision.
+struct CompSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = s + x;
+        c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+};
+
+// Error-free sum of two compensated accumulators (TwoSum of the leading parts).
+__device__ __forceinline__ void comp_merge(float& s, float& c, float s2, float c2)
+{
+    const float t = s + s2;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    c = c + c2 + err;
+}
+
+}  // namespace bss

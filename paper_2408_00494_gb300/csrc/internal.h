@@ -1,0 +1,42 @@
+// Host-side declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bss {
+
+struct DevParams;
+
+constexpr int kRollWarps = 4;       // warps per rollout block
+constexpr int kUpdThreads = 512;    // threads per weights/update block
+constexpr int kUpdMaxBlocks = 148;  // upper bound on weights/update blocks (scratch is sized by it)
+
+size_t rollout_smem_bytes(const DevParams& dp);
+cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp);
+cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const float* x0, const float* Sigma0,
+                           const float* v, const uint32_t* ctr, float* S, float* eps, float* mean, float* var,
+                           cudaStream_t st);
+cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, float* xn, int64_t n,
+                              cudaStream_t st);
+cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st);
+cudaError_t box_muller_launch(const uint32_t* words, float* z, int64_t n, cudaStream_t st);
+
+// Weights + update: the number of blocks for K samples, and the launch.
+int update_blocks(int K);
+struct UpdateIO {
+    const float* S;       // K costs
+    const float* eps;     // K*T*2 effective perturbations
+    float* v;             // T*2 nominal, updated in place to v+
+    float* w;             // K normalised weights (out)
+    float* u0;            // 2 (out) or nullptr
+    float* diag;          // 4 (out) or nullptr
+    uint32_t* ctr;        // solve counter, incremented by one
+    float* partial;       // scratch: update_blocks(K) * T*2 partial sums
+    unsigned int* ticket; // scratch: one zero-initialised counter, left at zero
+};
+cudaError_t update_launch(int K, int T, float lambda, bool comp, const UpdateIO& io, cudaStream_t st);
+cudaError_t shift_launch(float* v, int T, int n, cudaStream_t st);
+
+}  // namespace bss

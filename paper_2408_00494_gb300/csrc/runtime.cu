@@ -1,0 +1,494 @@
+// Host runtime of the C ABI declared in include/bssmppi.h: parameter validation, derived
+// constants (Cholesky factors, Sigma_eps^-1, back-off nu), device buffers and kernel launches.
+#include "../../include/bssmppi.h"
+#include "device.cuh"
+#include "internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+struct bssmppi_ctx {
+    bssmppi_params prm{};
+    bss::DevParams dp{};
+    int P = 1;            // particles per lane (1, 2, 4 or 8)
+    int nx = 6;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    float* d_kappa = nullptr;
+    float* d_S = nullptr;
+    float* d_w = nullptr;
+    float* d_eps = nullptr;
+    float* d_mean = nullptr;
+    float* d_var = nullptr;
+    float* d_v = nullptr;
+    float* d_x0 = nullptr;      // staging for the host-buffer solve
+    float* d_Sigma0 = nullptr;
+    float* d_u0 = nullptr;
+    float* d_diag = nullptr;
+    uint32_t* d_ctr = nullptr;
+    float* d_partial = nullptr;
+    unsigned int* d_ticket = nullptr;
+    float* h_stage = nullptr;   // pinned host staging: x0 | Sigma0 | v | u0
+    // per-phase timing ring: 4 events per recorded solve
+    cudaEvent_t* ev = nullptr;
+    int ev_cap = 0, ev_count = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(bssmppi_ctx* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(bssmppi_ctx* h, cudaError_t e, const char* what)
+{
+    return fail(h, BSSMPPI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define BSS_CUDA(h, call)                                               \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);        \
+    } while (0)
+
+// PSD-tolerant Cholesky (lower, row-major) in double; zero pivots give zero columns.
+// Returns false if the matrix is not symmetric positive semidefinite (within a tolerance).
+bool cholesky_psd(int n, const double* A, double* L)
+{
+    double scale = 0.0;
+    for (int i = 0; i < n; ++i) scale = std::fmax(scale, std::fabs(A[i * n + i]));
+    const double tol = 1e-12 * (scale > 0 ? scale : 1.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (std::fabs(A[i * n + j] - A[j * n + i]) > tol) return false;
+    std::memset(L, 0, sizeof(double) * n * n);
+    for (int j = 0; j < n; ++j) {
+        double d = A[j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+        if (d < -tol) return false;
+        if (d <= tol) {
+            // zero pivot: the rest of the column must vanish for the matrix to be PSD
+            for (int i = j + 1; i < n; ++i) {
+                double s = A[i * n + j];
+                for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+                if (std::fabs(s) > 1e-9 * (scale > 0 ? scale : 1.0)) return false;
+            }
+            continue;
+        }
+        const double ljj = std::sqrt(d);
+        L[j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = s / ljj;
+        }
+    }
+    return true;
+}
+
+// erfinv(y) for |y| < 1: Winitzki's closed-form approximation (S. Winitzki, "A handy
+// approximation for the error function and its inverse", 2008) refined by Newton steps on
+// std::erf, whose derivative is 2/sqrt(pi) exp(-x^2).
+double inverse_erf(double y)
+{
+    const double a = 0.147, pi = 3.14159265358979323846;
+    const double ln = std::log((1.0 - y) * (1.0 + y));
+    const double t = 2.0 / (pi * a) + 0.5 * ln;
+    double x = std::copysign(std::sqrt(std::sqrt(t * t - ln / a) - t), y);
+    for (int i = 0; i < 6; ++i) {
+        const double f = std::erf(x) - y;
+        x -= f / (2.0 / std::sqrt(pi) * std::exp(-x * x));
+    }
+    return x;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int validate(const bssmppi_params* p, std::string& why)
+{
+    auto bad = [&](const char* m) { why = m; return BSSMPPI_EINVAL; };
+    if (!p) return bad("params is NULL");
+    if (p->K < 1 || p->K > BSSMPPI_K_MAX) return bad("K out of range [1, 2^20]");
+    if (p->M < 2 || p->M > BSSMPPI_M_MAX) return bad("M out of range [2, 256] (an unbiased variance needs M >= 2)");
+    if (p->T < 1 || p->T > BSSMPPI_T_MAX) return bad("T out of range [1, 256]");
+    if (p->model != BSSMPPI_MODEL_BICYCLE6 && p->model != BSSMPPI_MODEL_DOUBLE_INT4) return bad("unknown model");
+    if (p->model == BSSMPPI_MODEL_BICYCLE6 && p->ey_index != 4) return bad("bicycle model constrains e_y: ey_index must be 4");
+    if (p->model == BSSMPPI_MODEL_DOUBLE_INT4 && p->ey_index != 1) return bad("double integrator constrains p_y: ey_index must be 1");
+    if (p->n_sub < 1 || p->n_sub > 64) return bad("n_sub out of range [1, 64]");
+    if (!(p->dt > 0.0f)) return bad("dt must be > 0");
+    if (p->model == BSSMPPI_MODEL_BICYCLE6) {
+        if (!(p->mass > 0 && p->Iz > 0 && p->lf > 0 && p->lr > 0 && p->g > 0 && p->vx_floor > 0)) return bad("model constants must be > 0");
+        if (!p->track_kappa) return bad("track_kappa is NULL");
+        if (!is_pow2(p->n_track) || p->n_track < 2 || p->n_track > BSSMPPI_NTRACK_MAX) return bad("n_track must be a power of two in [2, 16384]");
+        if (!(p->track_len > 0.0f)) return bad("track_len must be > 0");
+    }
+    for (int j = 0; j < 2; ++j)
+        if (!(p->u_min[j] < p->u_max[j])) return bad("u_min must be < u_max");
+    if (!(p->lambda > 0.0f) || !std::isfinite(p->lambda)) return bad("lambda must be finite and > 0");
+    if (!(p->delta > 0.0f && p->delta < 0.5f)) return bad("delta must be in (0, 0.5)");
+    if (!(p->gamma > 0.0f && p->gamma < 1.0f)) return bad("gamma must be in (0, 1)");
+    if (!(p->w_T > 0.0f)) return bad("w_T must be > 0");
+    if (p->reserved != 0) return bad("reserved must be 0");
+    const double* Se = p->Sigma_eps;
+    if (!(Se[0] > 0 && Se[3] > 0 && Se[0] * Se[3] - Se[1] * Se[2] > 0 && std::fabs(Se[1] - Se[2]) <= 1e-12 * (Se[0] + Se[3])))
+        return bad("Sigma_eps must be symmetric positive definite");
+    return BSSMPPI_OK;
+}
+
+template <typename T>
+int alloc(bssmppi_ctx* h, T** ptr, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T));
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return fail(h, e == cudaErrorMemoryAllocation ? BSSMPPI_ENOMEM : BSSMPPI_ECUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return BSSMPPI_OK;
+}
+
+void release(bssmppi_ctx* h)
+{
+    void* ptrs[] = {h->d_kappa, h->d_S, h->d_w, h->d_eps, h->d_mean, h->d_var, h->d_v, h->d_x0, h->d_Sigma0,
+                    h->d_u0, h->d_diag, h->d_ctr, h->d_partial, h->d_ticket};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    for (int i = 0; i < 4 * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
+    delete[] h->ev;
+    h->ev = nullptr;
+    h->ev_cap = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t bssmppi_abi_version(void) { return BSSMPPI_ABI_VERSION; }
+size_t bssmppi_params_size(void) { return sizeof(bssmppi_params); }
+
+const char* bssmppi_last_error(bssmppi_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
+{
+    if (!out) return fail(nullptr, BSSMPPI_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    int rc = validate(p, why);
+    if (rc != BSSMPPI_OK) return fail(nullptr, rc, why);
+
+    const int nx = p->model == BSSMPPI_MODEL_BICYCLE6 ? 6 : 4;
+    double Lw[36], Le[4];
+    if (!cholesky_psd(nx, p->Sigma_w, Lw)) return fail(nullptr, BSSMPPI_EINVAL, "Sigma_w must be symmetric positive semidefinite");
+    if (!cholesky_psd(2, p->Sigma_eps, Le)) return fail(nullptr, BSSMPPI_EINVAL, "Sigma_eps must be symmetric positive definite");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, BSSMPPI_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+
+    auto* h = new bssmppi_ctx();
+    h->prm = *p;
+    h->prm.track_kappa = nullptr;
+    h->nx = nx;
+    h->device = dev;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+
+    // Mapping of particles to lanes.
+    int seg = 1;
+    while (seg < p->M && seg < 32) seg <<= 1;
+    int ppl = (p->M + seg - 1) / seg;
+    int P = 1;
+    while (P < ppl) P <<= 1;
+    h->P = P;
+
+    bss::DevParams& d = h->dp;
+    d.K = p->K; d.M = p->M; d.T = p->T; d.nx = nx;
+    d.n_sub = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_sub : 1;
+    d.seg = seg; d.spw = 32 / seg;
+    d.uniform = (p->M == seg * P) ? 1 : 0;
+    d.ey = p->ey_index; d.crn = p->crn_disturbance ? 1 : 0; d.record = p->record_moments ? 1 : 0;
+    d.key0 = (uint32_t)(p->seed & 0xffffffffu); d.key1 = (uint32_t)(p->seed >> 32);
+    d.dt = p->dt; d.h = p->dt / (float)d.n_sub;
+    d.inv_m = 1.0f / p->mass; d.inv_Iz = 1.0f / p->Iz; d.lf = p->lf; d.lr = p->lr;
+    d.tB = p->tire_B; d.tC = p->tire_C;
+    d.Df = (float)((double)p->mu * p->mass * p->g * p->lr / ((double)p->lf + p->lr));
+    d.Dr = (float)((double)p->mu * p->mass * p->g * p->lf / ((double)p->lf + p->lr));
+    d.vx_floor = p->vx_floor;
+    d.umin0 = p->u_min[0]; d.umin1 = p->u_min[1]; d.umax0 = p->u_max[0]; d.umax1 = p->u_max[1];
+    d.Le00 = (float)Le[0]; d.Le10 = (float)Le[2]; d.Le11 = (float)Le[3];
+    const double* Se = p->Sigma_eps;
+    const double det = Se[0] * Se[3] - Se[1] * Se[2];
+    d.Si00 = (float)(Se[3] / det); d.Si01 = (float)(-Se[1] / det);
+    d.Si10 = (float)(-Se[2] / det); d.Si11 = (float)(Se[0] / det);
+    for (int i = 0; i < 21; ++i) d.Lw[i] = 0.0f;
+    for (int i = 0; i < nx; ++i)
+        for (int j = 0; j <= i; ++j) d.Lw[i * (i + 1) / 2 + j] = (float)Lw[i * nx + j];
+    d.inv_lambda = 1.0f / p->lambda;
+    d.nu = (float)(std::sqrt(2.0) * inverse_erf(1.0 - 2.0 * (double)p->delta));
+    d.one_m_gamma = 1.0f - p->gamma;
+    d.ctrl_w = p->ctrl_w; d.Csafe = p->C_safe; d.Cobs = p->C_obs; d.wT = p->w_T;
+    for (int i = 0; i < 6; ++i) {
+        d.xg[i] = p->x_goal[i];
+        d.Q[i] = i < nx ? p->Q[i] : 0.0f;
+        d.Qf[i] = i < nx ? p->Qf[i] : 0.0f;
+    }
+    const int ntab = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_track : 2;
+    d.n_track_mask = ntab - 1;
+    d.track_scale = p->model == BSSMPPI_MODEL_BICYCLE6 ? (float)((double)ntab / p->track_len) : 0.0f;
+    d.Mf = (float)p->M; d.invM = 1.0f / (float)p->M; d.invM1 = 1.0f / (float)(p->M - 1);
+
+    const size_t K = p->K, T = p->T;
+    const int G = bss::update_blocks(p->K);
+    rc = BSSMPPI_OK;
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_kappa, ntab + 1);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_S, K);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_w, K);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_eps, K * T * 2);
+    if (rc == BSSMPPI_OK && p->record_moments) rc = alloc(h, &h->d_mean, K * (T + 1) * nx);
+    if (rc == BSSMPPI_OK && p->record_moments) rc = alloc(h, &h->d_var, K * (T + 1) * nx);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_v, T * 2);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_x0, 6);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_Sigma0, 36);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_u0, 2);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_diag, BSSMPPI_NDIAG);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ctr, 1);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_partial, (size_t)G * T * 2);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ticket, 1);
+    if (rc == BSSMPPI_OK) {
+        e = cudaMallocHost(reinterpret_cast<void**>(&h->h_stage), sizeof(float) * (6 + 36 + 2 * T + 2));
+        if (e != cudaSuccess) {
+            h->h_stage = nullptr;
+            rc = fail(h, BSSMPPI_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+        }
+    }
+    if (rc == BSSMPPI_OK) {
+        std::string step;
+        e = cudaSuccess;
+        if (p->model == BSSMPPI_MODEL_BICYCLE6) {
+            float* tab = new float[ntab + 1];
+            std::memcpy(tab, p->track_kappa, sizeof(float) * ntab);
+            tab[ntab] = tab[0];
+            e = cudaMemcpy(h->d_kappa, tab, sizeof(float) * (ntab + 1), cudaMemcpyHostToDevice);
+            delete[] tab;
+        } else {
+            e = cudaMemset(h->d_kappa, 0, sizeof(float) * (ntab + 1));
+        }
+        if (e == cudaSuccess) e = cudaMemset(h->d_v, 0, sizeof(float) * T * 2);
+        if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMemset(h->d_ticket, 0, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(h->d_diag, 0, sizeof(float) * BSSMPPI_NDIAG);
+        if (e == cudaSuccess) e = bss::rollout_prepare(h->dp, h->P, p->compensated != 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "create");
+    }
+    h->dp.kappa = h->d_kappa;
+    if (rc != BSSMPPI_OK) {
+        g_create_error = h->err;
+        release(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return BSSMPPI_OK;
+}
+
+int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* d_v, float* d_u0)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!d_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
+    const size_t vbytes = sizeof(float) * 2 * h->prm.T;
+    if (d_v) BSS_CUDA(h, cudaMemcpyAsync(h->d_v, d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+    cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 4 * h->ev_count : nullptr;
+    if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], h->stream));
+    BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, d_x0, d_Sigma0, h->d_v, h->d_ctr,
+                                    h->d_S, h->d_eps, h->d_mean, h->d_var, h->stream));
+    if (ev) BSS_CUDA(h, cudaEventRecord(ev[1], h->stream));
+    bss::UpdateIO io{h->d_S, h->d_eps, h->d_v, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, h->d_ctr,
+                     h->d_partial, h->d_ticket};
+    if (ev) BSS_CUDA(h, cudaEventRecord(ev[2], h->stream));
+    BSS_CUDA(h, bss::update_launch(h->prm.K, h->prm.T, h->prm.lambda, h->prm.compensated != 0, io, h->stream));
+    if (ev) {
+        BSS_CUDA(h, cudaEventRecord(ev[3], h->stream));
+        ++h->ev_count;
+    }
+    if (d_v) BSS_CUDA(h, cudaMemcpyAsync(d_v, h->d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, float* h_v, float* h_u0)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!h_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
+    const int nx = h->nx, T = h->prm.T;
+    float* sx0 = h->h_stage;
+    float* sS0 = sx0 + 6;
+    float* sv = sS0 + 36;
+    float* su0 = sv + 2 * T;
+    std::memcpy(sx0, h_x0, sizeof(float) * nx);
+    BSS_CUDA(h, cudaMemcpyAsync(h->d_x0, sx0, sizeof(float) * nx, cudaMemcpyHostToDevice, h->stream));
+    if (h_Sigma0) {
+        std::memcpy(sS0, h_Sigma0, sizeof(float) * nx * nx);
+        BSS_CUDA(h, cudaMemcpyAsync(h->d_Sigma0, sS0, sizeof(float) * nx * nx, cudaMemcpyHostToDevice, h->stream));
+    }
+    if (h_v) {
+        std::memcpy(sv, h_v, sizeof(float) * 2 * T);
+        BSS_CUDA(h, cudaMemcpyAsync(h->d_v, sv, sizeof(float) * 2 * T, cudaMemcpyHostToDevice, h->stream));
+    }
+    int rc = bssmppi_solve(h, h->d_x0, h_Sigma0 ? h->d_Sigma0 : nullptr, nullptr, h->d_u0);
+    if (rc != BSSMPPI_OK) return rc;
+    if (h_v) BSS_CUDA(h, cudaMemcpyAsync(sv, h->d_v, sizeof(float) * 2 * T, cudaMemcpyDeviceToHost, h->stream));
+    if (h_u0) BSS_CUDA(h, cudaMemcpyAsync(su0, h->d_u0, sizeof(float) * 2, cudaMemcpyDeviceToHost, h->stream));
+    BSS_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h_v) std::memcpy(h_v, sv, sizeof(float) * 2 * T);
+    if (h_u0) std::memcpy(h_u0, su0, sizeof(float) * 2);
+    return BSSMPPI_OK;
+}
+
+int bssmppi_shift(bssmppi_t h, float* d_v, int32_t n)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (n < 0 || n > h->prm.T) return fail(h, BSSMPPI_EINVAL, "shift n must be in [0, T]");
+    if (n == 0) return BSSMPPI_OK;
+    BSS_CUDA(h, bss::shift_launch(d_v ? d_v : h->d_v, h->prm.T, n, h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_destroy(bssmppi_t h)
+{
+    if (!h) return BSSMPPI_OK;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+    return BSSMPPI_OK;
+}
+
+int bssmppi_timing(bssmppi_t h, int32_t n)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (n < 0 || n > 4096) return fail(h, BSSMPPI_EINVAL, "timing slots must be in [0, 4096]");
+    BSS_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < 4 * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
+    delete[] h->ev;
+    h->ev = nullptr;
+    h->ev_cap = 0;
+    h->ev_count = 0;
+    if (n == 0) return BSSMPPI_OK;
+    h->ev = new cudaEvent_t[4 * (size_t)n];
+    for (int i = 0; i < 4 * n; ++i) {
+        cudaError_t e = cudaEventCreate(&h->ev[i]);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(h->ev[j]);
+            delete[] h->ev;
+            h->ev = nullptr;
+            return cuda_fail(h, e, "cudaEventCreate");
+        }
+    }
+    h->ev_cap = n;
+    return BSSMPPI_OK;
+}
+
+int bssmppi_timing_read(bssmppi_t h, float* h_rollout_ms, float* h_update_ms, int32_t max, int32_t* count)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    const int n = h->ev_count < max ? h->ev_count : (max > 0 ? max : 0);
+    for (int i = 0; i < n; ++i) {
+        cudaEvent_t* ev = h->ev + 4 * i;
+        BSS_CUDA(h, cudaEventSynchronize(ev[3]));
+        float a = 0.0f, b = 0.0f;
+        BSS_CUDA(h, cudaEventElapsedTime(&a, ev[0], ev[1]));
+        BSS_CUDA(h, cudaEventElapsedTime(&b, ev[2], ev[3]));
+        if (h_rollout_ms) h_rollout_ms[i] = a;
+        if (h_update_ms) h_update_ms[i] = b;
+    }
+    if (count) *count = n;
+    return BSSMPPI_OK;
+}
+
+int bssmppi_set_counter(bssmppi_t h, uint32_t counter)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    uint32_t* stage = reinterpret_cast<uint32_t*>(h->h_stage);
+    BSS_CUDA(h, cudaStreamSynchronize(h->stream));
+    stage[0] = counter;
+    BSS_CUDA(h, cudaMemcpyAsync(h->d_ctr, stage, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
+    BSS_CUDA(h, cudaStreamSynchronize(h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_get_counter(bssmppi_t h, uint32_t* counter)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!counter) return fail(h, BSSMPPI_EINVAL, "counter is NULL");
+    BSS_CUDA(h, cudaMemcpyAsync(counter, h->d_ctr, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    BSS_CUDA(h, cudaStreamSynchronize(h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_set_nominal(bssmppi_t h, const float* d_v)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!d_v) return fail(h, BSSMPPI_EINVAL, "v is NULL");
+    BSS_CUDA(h, cudaMemcpyAsync(h->d_v, d_v, sizeof(float) * 2 * h->prm.T, cudaMemcpyDeviceToDevice, h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_read(bssmppi_t h, int32_t which, void* d_dst, size_t bytes)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!d_dst) return fail(h, BSSMPPI_EINVAL, "destination is NULL");
+    const size_t K = h->prm.K, T = h->prm.T, nx = h->nx;
+    const void* src = nullptr;
+    size_t need = 0;
+    switch (which) {
+    case BSSMPPI_BUF_S: src = h->d_S; need = K; break;
+    case BSSMPPI_BUF_W: src = h->d_w; need = K; break;
+    case BSSMPPI_BUF_EPS: src = h->d_eps; need = K * T * 2; break;
+    case BSSMPPI_BUF_MEAN: src = h->d_mean; need = K * (T + 1) * nx; break;
+    case BSSMPPI_BUF_VAR: src = h->d_var; need = K * (T + 1) * nx; break;
+    case BSSMPPI_BUF_DIAG: src = h->d_diag; need = BSSMPPI_NDIAG; break;
+    case BSSMPPI_BUF_V: src = h->d_v; need = T * 2; break;
+    default: return fail(h, BSSMPPI_EINVAL, "unknown buffer");
+    }
+    if (!src) return fail(h, BSSMPPI_ENOTSUP, "buffer not kept (record_moments = 0)");
+    need *= sizeof(float);
+    if (bytes < need) return fail(h, BSSMPPI_EINVAL, "destination too small");
+    BSS_CUDA(h, cudaMemcpyAsync(d_dst, src, need, cudaMemcpyDeviceToDevice, h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_model_step(bssmppi_t h, const float* d_x, const float* d_u, float* d_x_next, int64_t n)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (n < 0 || (n > 0 && (!d_x || !d_u || !d_x_next))) return fail(h, BSSMPPI_EINVAL, "bad arrays");
+    BSS_CUDA(h, bss::model_step_launch(h->dp, d_x, d_u, d_x_next, n, h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_philox4x32_10(const uint32_t* d_ctr, uint64_t seed, uint32_t* d_out, int64_t n, void* cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return fail(nullptr, BSSMPPI_EINVAL, "bad arrays");
+    if ((reinterpret_cast<uintptr_t>(d_ctr) | reinterpret_cast<uintptr_t>(d_out)) & 15u)
+        return fail(nullptr, BSSMPPI_EINVAL, "arrays must be 16-byte aligned");
+    cudaError_t e = bss::philox_launch(d_ctr, seed, d_out, n, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(nullptr, e, "philox");
+}
+
+int bssmppi_box_muller(const uint32_t* d_words, float* d_z, int64_t n, void* cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!d_words || !d_z))) return fail(nullptr, BSSMPPI_EINVAL, "bad arrays");
+    if ((reinterpret_cast<uintptr_t>(d_words) | reinterpret_cast<uintptr_t>(d_z)) & 7u)
+        return fail(nullptr, BSSMPPI_EINVAL, "arrays must be 8-byte aligned");
+    cudaError_t e = bss::box_muller_launch(d_words, d_z, n, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(nullptr, e, "box_muller");
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads and exports every entry point include/*.h declares (CPU only).
+
+No compute call runs here; without a GPU, create() must fail loudly instead of falling back.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workload
+from paper_2408_00494_gb300 import _build, bssmppi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(bssmppi_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("bssmppi_create", "bssmppi_solve", "bssmppi_shift", "bssmppi_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(_build.build())
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_params_layout_and_version():
+    L = bssmppi.load()
+    assert L.bssmppi_abi_version() == 1
+    assert L.bssmppi_params_size() == ctypes.sizeof(bssmppi.Params)
+
+
+def test_invalid_parameters_rejected_on_host():
+    """Validation happens before any CUDA call, so it works without a GPU."""
+    L = bssmppi.load()
+    p = workload.config0()
+    for field, bad in (("M", 1), ("K", 0), ("T", 0), ("delta", 0.7), ("gamma", 1.5), ("lam", 0.0)):
+        prm = bssmppi.make_params(p)
+        setattr(prm, field, bad)
+        h = ctypes.c_void_p()
+        rc = L.bssmppi_create(ctypes.byref(prm), None, ctypes.byref(h))
+        assert rc == -1, field
+        assert h.value is None
+        assert bssmppi.last_error(None)
+    prm = bssmppi.make_params(p)
+    prm.Sigma_w[0] = -1.0
+    assert L.bssmppi_create(ctypes.byref(prm), None, ctypes.byref(ctypes.c_void_p())) == -1
+
+
+def test_no_cpu_fallback_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = bssmppi.load()
+    prm = bssmppi.make_params(workload.config0())
+    h = ctypes.c_void_p()
+    rc = L.bssmppi_create(ctypes.byref(prm), None, ctypes.byref(h))
+    assert rc == -3  # ECUDA: the library refuses to run anywhere but on a CUDA device
+    assert "CUDA" in bssmppi.last_error(None) or "device" in bssmppi.last_error(None)

@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (FP32 kernels against the FP64 oracle on identical inputs and identical Philox integers):
+  * Philox words: bit-exact.
+  * Box-Muller Gaussians: |dz| <= 2e-6 (|z| + 1e-3), from single-rounding errors of logf, sqrtf and
+    sincospif on exactly representable uniforms.
+  * Control perturbations eps_eff = clamp(v + eps) - v: atol 1e-6 (a few FP32 ulps of |u| <= 3).
+  * Particle means and variances of every step: rel 1e-4 / abs 1e-5 (the stated moment tolerance).
+  * Trajectory costs S: rel 1e-4 of the cost scale, on samples whose mean e_y stays at least 1e-3
+    away from the collision boundary (the C_obs indicator is a jump; a sample within rounding of it
+    may legitimately flip and is counted, not compared).
+  * Weights from the GPU's own costs (isolates the weight kernel): rel 1e-5 / abs 1e-7.
+  * Update from the GPU's own costs and perturbations (isolates the update kernel): rel 1e-4 / abs 1e-5.
+  * End-to-end v+ against the oracle's own v+: within abs 1e-5 + rel 1e-4 plus twice the first-order
+    bound sum_k w_k |dS_k - <dS>| / lambda |u_k - v+| that the measured cost differences imply.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2408_00494_gb300 import bssmppi  # noqa: E402
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def gpu_solve(prob, x0, v, ctr=0, Sigma0=None, record=True, solves=1):
+    c = bssmppi.Controller(prob, record_moments=record)
+    try:
+        bssmppi.set_counter(c.h, ctr)
+        xt, vt = _dev(x0), _dev(v)
+        S0 = None if Sigma0 is None else _dev(Sigma0)
+        u0 = torch.zeros(2, device="cuda")
+        for _ in range(solves):
+            vt = _dev(v)
+            bssmppi.solve(c.h, xt, S0, vt, u0)
+        torch.cuda.synchronize()
+        out = {"v_plus": vt.cpu().numpy().astype(np.float64), "u0": u0.cpu().numpy().astype(np.float64)}
+        for name, buf in (("S", bssmppi.BUF_S), ("w", bssmppi.BUF_W), ("eps", bssmppi.BUF_EPS),
+                          ("diag", bssmppi.BUF_DIAG)):
+            out[name] = c.buffer(buf).cpu().numpy().astype(np.float64)
+        if record:
+            out["mean"] = c.buffer(bssmppi.BUF_MEAN).cpu().numpy().astype(np.float64)
+            out["var"] = c.buffer(bssmppi.BUF_VAR).cpu().numpy().astype(np.float64)
+        out["counter"] = bssmppi.get_counter(c.h)
+        return out
+    finally:
+        c.close()
+
+
+def assert_close(a, b, rtol, atol, what):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    err = np.abs(a - b)
+    bad = err > atol + rtol * np.abs(b)
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} outside tolerance, max err {err.max():.3e}"
+
+
+def check_solve(prob, x0, v, ctr=0, Sigma0=None):
+    o = oracle.Oracle(prob)
+    ref = o.solve(x0, v, ctr, Sigma0=Sigma0, want_cov=True)
+    g = gpu_solve(prob, x0, v, ctr, Sigma0=Sigma0)
+    T = prob.T
+    # control perturbations
+    assert_close(g["eps"], ref["eps"], 0.0, 1e-6, "eps_eff")
+    # moments of every step
+    assert_close(g["mean"], ref["mean"], 1e-4, 1e-5, "particle means")
+    ref_var = np.diagonal(ref["cov"], axis1=2, axis2=3)
+    assert_close(g["var"], ref_var, 1e-4, 1e-5, "particle variances")
+    # costs, away from the collision-indicator jump
+    ok = ref["margin"] > 1e-3
+    scale = np.maximum(np.abs(ref["S"]), 1.0)
+    dS = g["S"] - ref["S"]
+    assert np.all(np.abs(dS[ok]) <= 1e-4 * scale[ok]), f"S: max rel err {np.max(np.abs(dS[ok]) / scale[ok]):.3e}"
+    assert (~ok).sum() <= max(1, prob.K // 100)
+    # weights from the GPU's costs
+    u_gpu = v.astype(np.float64)[None] + g["eps"]
+    w_iso, vp_iso, diag_iso = oracle.optimal_control(g["S"], u_gpu, float(np.float32(prob.lam)))
+    assert_close(g["w"], w_iso, 1e-5, 1e-7, "weights (from GPU costs)")
+    assert_close(g["v_plus"], vp_iso, 1e-4, 1e-5, "v+ (from GPU costs and eps)")
+    assert_close(g["u0"], vp_iso[0], 1e-4, 1e-5, "u0")
+    assert_close(g["diag"][:3], diag_iso[:3], 1e-4, 1e-6, "diagnostics")
+    # end to end, with the bound implied by the measured cost differences
+    lam = float(np.float32(prob.lam))
+    wr = ref["w"]
+    dSc = np.where(ok, dS, 0.0)
+    dev = np.abs(dSc - np.sum(wr * dSc)) / lam
+    bound = np.einsum("k,kti->ti", wr * dev, np.abs(ref["u"] - ref["v_plus"][None]))
+    err = np.abs(g["v_plus"] - ref["v_plus"])
+    assert np.all(err <= 1e-5 + 1e-4 * np.abs(ref["v_plus"]) + 2 * bound), f"v+ e2e max err {err.max():.3e}"
+    assert g["counter"] == ctr + 1
+    return g, ref
+
+
+def test_philox_bit_exact():
+    rng = np.random.default_rng(0)
+    n = 1 << 20
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    # the layout the solve uses: steps, calls, particles, samples, streams, counters
+    ctr[:4096, 0] = np.arange(4096) % 256 | ((np.arange(4096) // 256 % 2) << 16)
+    ctr[:4096, 3] = (np.arange(4096) % 4 << 28) | 7
+    for seed in (0, 0x0123456789ABCDEF):
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        out = torch.zeros(n * 4, dtype=torch.int32, device="cuda")
+        bssmppi.philox4x32_10(torch.as_tensor(ctr.view(np.int32).reshape(-1), device="cuda"), seed, out)
+        gpu = out.cpu().numpy().view(np.uint32).reshape(n, 4)
+        ref = oracle.philox_batch(ctr, key)
+        assert np.array_equal(gpu, ref)
+
+
+def test_box_muller_matches_oracle():
+    rng = np.random.default_rng(1)
+    n = 1 << 16
+    words = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    words[:4] = [[0xFFFFFFFF, 0], [0, 0], [0, 1 << 30], [0x000000FF, 0xFFFFFFFF]]
+    z = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+    bssmppi.box_muller(torch.as_tensor(words.view(np.int32).reshape(-1), device="cuda"), z)
+    zg = z.cpu().numpy().reshape(n, 2).astype(np.float64)
+    zr = np.array([oracle.gaussian_pair(int(a), int(b)) for a, b in words])
+    r = np.hypot(zr[:, 0], zr[:, 1])
+    assert np.all(np.abs(zg - zr) <= 2e-6 * (r[:, None] + 1e-3))
+    assert zg[0, 0] == 0.0 and zg[0, 1] == 0.0
+
+
+@pytest.mark.parametrize("model", ["bicycle", "double_integrator"])
+def test_model_step_matches_oracle(model):
+    if model == "bicycle":
+        p = workload.config1()
+    else:
+        p = workload.double_integrator_problem(1, 2, 1)
+    c = bssmppi.Controller(p)
+    o = oracle.Oracle(p)
+    n = 4096
+    xs = np.stack([workload.random_state(p, i) for i in range(n)])
+    us = np.stack([workload.random_nominal(p, i)[0] for i in range(n)]) * 3.0
+    us = np.clip(us, p.u_min, p.u_max).astype(np.float32)
+    out = torch.zeros((n, p.nx), device="cuda")
+    bssmppi.model_step(c.h, _dev(xs), _dev(us), out)
+    g = out.cpu().numpy().astype(np.float64)
+    ref = np.stack([o.model_step(xs[i].astype(np.float64), us[i].astype(np.float64)) for i in range(n)])
+    c.close()
+    assert_close(g, ref, 2e-5, 2e-5, "model step")
+
+
+def test_solve_config0_from_start():
+    p = workload.config0()
+    check_solve(p, workload.racing_x0(p), np.zeros((p.T, 2), np.float32), ctr=0)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_solve_config0_random_states(seed):
+    p = workload.config0()
+    check_solve(p, workload.random_state(p, seed), workload.random_nominal(p, seed), ctr=100 + seed)
+
+
+@pytest.mark.parametrize("M", [2, 5, 20, 32, 50, 64, 128])
+def test_solve_particle_counts(M):
+    """Segments narrower than a warp, ragged lanes (M not a multiple of the segment) and P > 1."""
+    p = workload.config0()
+    p.K, p.M, p.T = 200, M, 12
+    check_solve(p, workload.random_state(p, M), workload.random_nominal(p, M), ctr=M)
+
+
+def test_solve_ragged_K_and_long_horizon():
+    p = workload.config1()
+    p.K, p.M, p.T = 1001, 64, 40
+    check_solve(p, workload.random_state(p, 5), workload.random_nominal(p, 5), ctr=3)
+
+
+def test_solve_single_sample_and_single_step():
+    p = workload.config0()
+    p.K, p.M, p.T = 1, 16, 1
+    g, ref = check_solve(p, workload.random_state(p, 6), workload.random_nominal(p, 6), ctr=0)
+    assert g["w"][0] == 1.0
+
+
+def test_solve_with_initial_covariance():
+    p = workload.config0()
+    p.K, p.T = 128, 10
+    Sig0 = np.diag([0.05, 0.01, 0.01, 0.001, 0.04, 0.1]).astype(np.float32) ** 2
+    check_solve(p, workload.random_state(p, 7), workload.random_nominal(p, 7), ctr=9, Sigma0=Sig0)
+
+
+def test_solve_common_random_numbers():
+    p = workload.config0()
+    p.K, p.T = 96, 15
+    p.crn_disturbance = 1
+    check_solve(p, workload.random_state(p, 8), workload.random_nominal(p, 8), ctr=4)
+
+
+def test_solve_near_boundary_with_active_barrier():
+    p = workload.config0()
+    p.K, p.T = 256, 20
+    x0 = workload.random_state(p, 9)
+    x0[4], x0[3] = 2.6, 0.08
+    g, ref = check_solve(p, x0, workload.random_nominal(p, 9), ctr=2)
+    assert np.any(ref["h"][:, 1:] < 0.7 * ref["h"][:, :-1])  # the DCBF penalty is active somewhere
+
+
+def test_solve_double_integrator():
+    p = workload.double_integrator_problem(K=300, M=40, T=16)
+    check_solve(p, workload.random_state(p, 10), workload.random_nominal(p, 10), ctr=5)
+
+
+def test_consecutive_solves_advance_counter():
+    p = workload.config0()
+    p.K, p.T = 64, 8
+    x0, v = workload.random_state(p, 11), workload.random_nominal(p, 11)
+    g = gpu_solve(p, x0, v, ctr=41, solves=2)
+    ref = oracle.Oracle(p).solve(x0, v, 42)
+    assert g["counter"] == 43
+    assert_close(g["eps"], ref["eps"], 0.0, 1e-6, "eps of the second solve")
+
+
+def test_shift_matches_definition():
+    p = workload.config0()
+    c = bssmppi.Controller(p)
+    v = workload.random_nominal(p, 12)
+    for n in (1, 3, p.T):
+        vt = _dev(v)
+        bssmppi.shift(c.h, vt, n)
+        exp = v[np.minimum(np.arange(p.T) + n, p.T - 1)]
+        assert np.array_equal(vt.cpu().numpy(), exp)
+    c.close()
+
+
+def test_solve_host_matches_device_path():
+    p = workload.config0()
+    x0, v = workload.random_state(p, 13), workload.random_nominal(p, 13)
+    g = gpu_solve(p, x0, v, ctr=7, record=False)
+    c = bssmppi.Controller(p)
+    bssmppi.set_counter(c.h, 7)
+    vh = v.copy()
+    u0 = np.zeros(2, np.float32)
+    bssmppi.solve_host(c.h, x0.astype(np.float32), None, vh, u0)
+    c.close()
+    assert np.array_equal(vh.astype(np.float64), g["v_plus"])
+    assert np.array_equal(u0.astype(np.float64), g["u0"])
+
+
+def test_full_size_config1_sampled_parity():
+    """The benchmark's workload and launch configuration (K=4096, M=64, T=40, moments not kept):
+    sampled costs and perturbations against the oracle sample by sample, the update against the
+    oracle's update from the GPU's costs, and properties of the weights."""
+    p = workload.config1()
+    x0, v = workload.random_state(p, 14), workload.random_nominal(p, 14)
+    g = gpu_solve(p, x0, v, ctr=123, record=False)
+    o = oracle.Oracle(p)
+    picks = [0, 1, 31, 32, 1000, 2047, 4064, 4095]
+    for k in picks:
+        r = o.solve(x0, v, 123, k_range=(k, k + 1))
+        assert_close(g["eps"][k], r["eps"][k], 0.0, 1e-6, f"eps[{k}]")
+        if r["margin"][k] > 1e-3:
+            assert abs(g["S"][k] - r["S"][k]) <= 1e-4 * max(1.0, abs(r["S"][k])), k
+    u_gpu = v.astype(np.float64)[None] + g["eps"]
+    w_iso, vp_iso, _ = oracle.optimal_control(g["S"], u_gpu, float(np.float32(p.lam)))
+    assert_close(g["w"], w_iso, 1e-5, 1e-7, "weights")
+    assert_close(g["v_plus"], vp_iso, 1e-4, 1e-5, "v+")
+    assert abs(g["w"].sum() - 1.0) < 1e-5 and g["w"].min() >= 0.0
+    lo, hi = np.asarray(p.u_min), np.asarray(p.u_max)
+    assert np.all(u_gpu >= lo - 1e-6) and np.all(u_gpu <= hi + 1e-6)
