@@ -6,7 +6,7 @@ Tolerances (FP32 kernels against the FP64 oracle on identical inputs and identic
     sincospif on exactly representable uniforms.
   * Control perturbations eps_eff = clamp(v + eps) - v: atol 1e-6 (a few FP32 ulps of |u| <= 3).
   * Particle means and variances of every step: rel 1e-4 / abs 1e-5 (the stated moment tolerance).
-  * Trajectory costs S: rel 1e-4 of the cost scale, on samples whose mean e_y stays at least 1e-3
+  * Trajectory costs S: rel 1e-4 of the cost scale, on samples whose mean e_y stays at least 1e-4
     away from the collision boundary (the C_obs indicator is a jump; a sample within rounding of it
     may legitimately flip and is counted, not compared).
   * Weights from the GPU's own costs (isolates the weight kernel): rel 1e-5 / abs 1e-7.
@@ -72,12 +72,13 @@ def check_solve(prob, x0, v, ctr=0, Sigma0=None):
     assert_close(g["mean"], ref["mean"], 1e-4, 1e-5, "particle means")
     ref_var = np.diagonal(ref["cov"], axis1=2, axis2=3)
     assert_close(g["var"], ref_var, 1e-4, 1e-5, "particle variances")
-    # costs, away from the collision-indicator jump
-    ok = ref["margin"] > 1e-3
+    # costs, away from the collision-indicator jump (FP32 moves the mean e_y by ~1e-6, so only a
+    # sample whose mean passes within 1e-4 of the wall can see the indicator decided differently)
+    ok = ref["margin"] > 1e-4
     scale = np.maximum(np.abs(ref["S"]), 1.0)
     dS = g["S"] - ref["S"]
     assert np.all(np.abs(dS[ok]) <= 1e-4 * scale[ok]), f"S: max rel err {np.max(np.abs(dS[ok]) / scale[ok]):.3e}"
-    assert (~ok).sum() <= max(1, prob.K // 100)
+    assert (~ok).sum() <= max(2, prob.K // 20)
     # weights from the GPU's costs
     u_gpu = v.astype(np.float64)[None] + g["eps"]
     w_iso, vp_iso, diag_iso = oracle.optimal_control(g["S"], u_gpu, float(np.float32(prob.lam)))
@@ -94,6 +95,11 @@ def check_solve(prob, x0, v, ctr=0, Sigma0=None):
     err = np.abs(g["v_plus"] - ref["v_plus"])
     assert np.all(err <= 1e-5 + 1e-4 * np.abs(ref["v_plus"]) + 2 * bound), f"v+ e2e max err {err.max():.3e}"
     assert g["counter"] == ctr + 1
+    rel = lambda a, b: float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-3)))
+    print(f"[parity K={prob.K} M={prob.M} T={prob.T}] S max rel {np.max(np.abs(dS[ok]) / scale[ok]):.2e}; "
+          f"mean max abs {np.abs(g['mean'] - ref['mean']).max():.2e}; var max abs {np.abs(g['var'] - ref_var).max():.2e}; "
+          f"v+ iso max rel {rel(g['v_plus'], vp_iso):.2e}; v+ e2e max abs {err.max():.2e} (bound {bound.max():.2e}); "
+          f"indicator-margin exclusions {(~ok).sum()}")
     return g, ref
 
 
@@ -197,9 +203,10 @@ def test_solve_near_boundary_with_active_barrier():
     p = workload.config0()
     p.K, p.T = 256, 20
     x0 = workload.random_state(p, 9)
-    x0[4], x0[3] = 2.6, 0.08
+    x0[4], x0[3] = 2.6, 0.3
     g, ref = check_solve(p, x0, workload.random_nominal(p, 9), ctr=2)
-    assert np.any(ref["h"][:, 1:] < 0.7 * ref["h"][:, :-1])  # the DCBF penalty is active somewhere
+    one_m_gamma = 1.0 - float(np.float32(p.gamma))
+    assert np.any(-ref["h"][:, 1:] + one_m_gamma * ref["h"][:, :-1] > 0)  # the DCBF penalty is active
 
 
 def test_solve_double_integrator():
