@@ -183,6 +183,29 @@ int bssmppi_timing(bssmppi_t h, int32_t n);
 int bssmppi_timing_read(bssmppi_t h, float* h_rollout_ms, float* h_update_ms, int32_t max, int32_t* count);
 
 /*
+ * Weights and update (the same computation as the second half of bssmppi_solve) for callers that
+ * cannot allocate device memory. Some callers cannot call cudaMalloc once they run: hard real-time
+ * control loops that forbid allocation after start-up (an allocation can block and synchronise the
+ * device within a control period), and plugins hosted by a process whose memory manager owns the
+ * device memory. This entry point allocates nothing: its scratch (partial sums and arrival ticket)
+ * is one fixed array of 303,360 bytes in the library's device memory, held by every GPU that loads
+ * the library until the process exits. The paper has no counterpart; it is an interface addition.
+ *   d_S [K] costs, d_eps [K*T*2] effective perturbations (inputs, device).
+ *   d_v [T*2] nominal in, v+ out (device). d_w [K] normalised weights out (device).
+ *   d_u0 [2], d_diag [BSSMPPI_NDIAG], d_counter [1] (incremented by one): optional, NULL to skip.
+ *   K in [1, BSSMPPI_K_MAX], T in [1, BSSMPPI_T_MAX]; larger sizes are rejected with EINVAL (the
+ *   scratch holds at most 148 x 512 partial sums). lambda > 0. compensated: 1 = Kahan sums.
+ * The first call on a device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture. Every call shares the one array
+ * and the ticket is cleared at the start of each call, so calls that overlap on the GPU (on
+ * different streams, or from different threads) race and must be serialised by the caller.
+ * Asynchronous on `cuda_stream`; errors are reported through bssmppi_last_error(NULL).
+ */
+int bssmppi_update_noalloc(const float* d_S, const float* d_eps, float* d_v, float* d_w, float* d_u0,
+                           float* d_diag, uint32_t* d_counter, int32_t K, int32_t T, float lambda,
+                           int32_t compensated, void* cuda_stream);
+
+/*
  * Deterministic model step x_{k+1} = f(x_k, u_k) (Eq. "DeterministicNonlinearSystem"; n_sub Euler
  * substeps of the handle's model, no disturbance) for n independent states: d_x [n*nx], d_u [n*2],
  * d_x_next [n*nx], device. Used to check the model on its own. Asynchronous.

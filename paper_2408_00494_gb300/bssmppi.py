@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True):
         "bssmppi_read": (ctypes.c_int, [vp, i32, vp, sz]),
         "bssmppi_timing": (ctypes.c_int, [vp, i32]),
         "bssmppi_timing_read": (ctypes.c_int, [vp, vp, vp, i32, ctypes.POINTER(i32)]),
+        "bssmppi_update_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, i32, vp]),
         "bssmppi_model_step": (ctypes.c_int, [vp, vp, vp, vp, i64]),
         "bssmppi_philox4x32_10": (ctypes.c_int, [vp, u64, vp, i64, vp]),
         "bssmppi_box_muller": (ctypes.c_int, [vp, vp, i64, vp]),
@@ -225,6 +226,14 @@ def timing_read(h, max_n: int = 4096):
     _check(load().bssmppi_timing_read(h, ctypes.c_void_p(roll.ctypes.data), ctypes.c_void_p(upd.ctypes.data),
                                       int(max_n), ctypes.byref(n)), h)
     return roll[: n.value].copy(), upd[: n.value].copy()
+
+
+def update_noalloc(S, eps, v, w, u0=None, diag=None, counter=None, lam=1.0, compensated=True, stream=None):
+    """Weights and update with no device allocation (scratch in the library's static array).
+    K and T are taken from the shapes of S [K] and eps [K, T, 2]."""
+    K, T = int(S.numel()), int(eps.numel() // (2 * max(1, S.numel())))
+    _check(load().bssmppi_update_noalloc(_ptr(S), _ptr(eps), _ptr(v), _ptr(w), _ptr(u0), _ptr(diag), _ptr(counter),
+                                         K, T, ctypes.c_float(lam), int(bool(compensated)), _stream_handle(stream)))
 
 
 def model_step(h, x, u, x_next):

@@ -39,4 +39,8 @@ struct UpdateIO {
 cudaError_t update_launch(int K, int T, float lambda, bool comp, const UpdateIO& io, cudaStream_t st);
 cudaError_t shift_launch(float* v, int T, int n, cudaStream_t st);
 
+// Records the calling thread's error message for entry points without a handle
+// (read back through bssmppi_last_error(NULL)).
+void set_thread_error(const char* msg);
+
 }  // namespace bss

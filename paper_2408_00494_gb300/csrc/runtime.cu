@@ -171,6 +171,8 @@ void release(bssmppi_ctx* h)
 
 }  // namespace
 
+void bss::set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 extern "C" {
 
 uint32_t bssmppi_abi_version(void) { return BSSMPPI_ABI_VERSION; }

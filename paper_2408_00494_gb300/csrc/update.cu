@@ -9,8 +9,13 @@
 // stride over samples). Partial sums go to scratch; the last block to finish (atomic ticket) adds
 // them in block order, writes v+ in place, u0 and the diagnostics, bumps the counter and resets
 // the ticket. No block waits on another.
+#include "../../include/bssmppi.h"
 #include "device.cuh"
 #include "internal.h"
+
+#include <cmath>
+#include <mutex>
+#include <string>
 
 namespace bss {
 
@@ -209,3 +214,89 @@ cudaError_t shift_launch(float* v, int T, int n, cudaStream_t st)
 }
 
 }  // namespace bss
+
+// ---------------------------------------------------------------------------------------------
+// Weights and update without any allocation (bssmppi_update_noalloc).
+//
+// Some callers cannot call cudaMalloc once they are running: hard real-time control loops that
+// forbid allocation after start-up (an allocation can block and synchronise the device in the
+// middle of a control period), and plugins hosted by a process whose own memory manager owns
+// the device memory. For them the weights/update step takes its scratch (the per-block partial
+// sums, the arrival ticket and a spare counter word) from the fixed array below instead of a
+// handle's buffers. Every GPU that loads this library holds the array until the process exits.
+// ---------------------------------------------------------------------------------------------
+namespace bss {
+namespace {
+
+constexpr int kNoallocPartialFloats = kUpdMaxBlocks * 2 * 256;  // 148 blocks x 2T (T <= 256) floats
+constexpr int kNoallocFloats = kNoallocPartialFloats + 64;        // + ticket and spare counter word
+static __device__ __align__(256) float g_noalloc_scratch[kNoallocFloats];  // 303,360 bytes
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per device. In host code
+// the array's name is only a host-side stand-in; the kernels must receive this address.
+cudaError_t noalloc_scratch(float** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace bss
+
+extern "C" int bssmppi_update_noalloc(const float* d_S, const float* d_eps, float* d_v, float* d_w, float* d_u0,
+                                      float* d_diag, uint32_t* d_counter, int32_t K, int32_t T, float lambda,
+                                      int32_t compensated, void* cuda_stream)
+{
+    using namespace bss;
+    if (K < 1 || K > BSSMPPI_K_MAX) {
+        set_thread_error("update_noalloc: K out of range [1, 2^20]");
+        return BSSMPPI_EINVAL;
+    }
+    if (T < 1 || T > BSSMPPI_T_MAX) {
+        set_thread_error("update_noalloc: T out of range [1, 256]");
+        return BSSMPPI_EINVAL;
+    }
+    if ((size_t)update_blocks(K) * 2 * (size_t)T > (size_t)kNoallocPartialFloats) {
+        set_thread_error("update_noalloc: K and T exceed the static scratch (148 x 512 partial sums)");
+        return BSSMPPI_EINVAL;
+    }
+    if (!(lambda > 0.0f) || !std::isfinite(lambda)) {
+        set_thread_error("update_noalloc: lambda must be finite and > 0");
+        return BSSMPPI_EINVAL;
+    }
+    if (!d_S || !d_eps || !d_v || !d_w) {
+        set_thread_error("update_noalloc: S, eps, v and w must be non-NULL");
+        return BSSMPPI_EINVAL;
+    }
+    float* scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    unsigned int* ticket = reinterpret_cast<unsigned int*>(scratch + kNoallocPartialFloats);
+    uint32_t* spare_counter = reinterpret_cast<uint32_t*>(scratch + kNoallocPartialFloats + 32);
+    // the arrival ticket must start at zero (the array keeps whatever the last call left)
+    if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        UpdateIO io{d_S, d_eps, d_v, d_w, d_u0, d_diag, d_counter ? d_counter : spare_counter, scratch, ticket};
+        e = update_launch(K, T, lambda, compensated != 0, io, st);
+    }
+    if (e != cudaSuccess) {
+        set_thread_error((std::string("update_noalloc: ") + cudaGetErrorString(e)).c_str());
+        return BSSMPPI_ECUDA;
+    }
+    return BSSMPPI_OK;
+}
