@@ -173,6 +173,28 @@ int bssmppi_set_nominal(bssmppi_t h, const float* d_v);
 int bssmppi_read(bssmppi_t h, int32_t which, void* d_dst, size_t bytes);
 
 /*
+ * Shield repair objective and its gradient by a hand-written adjoint. Shield-MPPI minimises the
+ * violation of the DCBF condition with path-integral and gradient-based steps (Sec. II; the
+ * LocalRepair step of Algorithm 1); the gradient step uses this objective, the belief-barrier
+ * penalty of Eq. "cbfpenalty" along the rollout of the nominal sequence itself:
+ *   J_r(v) = sum_{t=1..T} C max(-h_t + (1 - gamma) h_{t-1}, 0),  h_t = (w_T - nu sigma_t)^2 - mean_t^2,
+ * with the M particles driven by u_t = v_t (no control noise) and the disturbance draws of sample
+ * 0 of the current solve counter, so J_r is a deterministic function of v (common random numbers).
+ *   d_x0 [nx] (device). d_v [T*2] (device; NULL = the resident sequence).
+ *   d_grad [T*2] out: dJ_r/dv (device). d_J [1] out: J_r (device, or NULL).
+ * Needs M <= 256 (one thread per particle). Asynchronous.
+ */
+int bssmppi_repair_grad(bssmppi_t h, const float* d_x0, const float* d_v, float* d_grad, float* d_J);
+
+/*
+ * Local repair: `iters` projected gradient steps v <- clamp(v - step dJ_r/dv, u_min, u_max) on the
+ * objective of bssmppi_repair_grad, in one launch. d_v [T*2] in/out (device; NULL = resident).
+ * d_J [iters + 1] out: J_r before each step and after the last (device, or NULL).
+ * 1 <= iters <= 1000, step >= 0. Asynchronous.
+ */
+int bssmppi_repair(bssmppi_t h, const float* d_x0, float* d_v, int32_t iters, float step, float* d_J);
+
+/*
  * Per-phase timing with CUDA events recorded on the handle's stream around the rollout kernel and
  * around the weights/update kernel of every solve. bssmppi_timing(h, n) with n > 0 starts recording
  * the next n solves (older records are dropped; n <= 4096), n = 0 stops. bssmppi_timing_read waits

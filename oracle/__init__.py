@@ -80,7 +80,7 @@ def lib():
         L.orc_solve.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, _dp, ctypes.c_uint32,
                                 ctypes.POINTER(OrcOutputs)]
         L.orc_repair_objective.restype = ctypes.c_double
-        L.orc_repair_objective.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, ctypes.c_uint32, _dp]
+        L.orc_repair_objective.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, ctypes.c_uint32, _dp, _dp]
         _lib = L
     return _lib
 
@@ -165,13 +165,19 @@ class Oracle:
     def kappa_at(self, s):
         return lib().orc_track_kappa(ctypes.byref(self.p), float(s))
 
-    def repair_objective(self, x0, v, ctr, grad=True):
+    def repair_objective(self, x0, v, ctr, grad=True, want_args=False):
+        """J_r(v) and (optionally) its gradient dJ/dv [T, 2] and the hinge arguments [T + 1]."""
         T = self.prob.T
         x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
         v = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(T, 2))
         g = np.zeros((T, 2)) if grad else None
-        J = lib().orc_repair_objective(ctypes.byref(self.p), _ptr(x0), _ptr(v), ctypes.c_uint32(ctr), _ptr(g))
-        return (J, g) if grad else J
+        a = np.zeros(T + 1) if want_args else None
+        J = lib().orc_repair_objective(ctypes.byref(self.p), _ptr(x0), _ptr(v), ctypes.c_uint32(ctr), _ptr(g),
+                                       _ptr(a))
+        out = (J, g) if grad else (J,)
+        if want_args:
+            out = out + (a,)
+        return out if len(out) > 1 else out[0]
 
 
 def optimal_control(S, u, lam):

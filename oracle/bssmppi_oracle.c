@@ -454,7 +454,7 @@ void orc_shift(int T, double* v)
  * draws are common to every evaluation). The reverse sweep differentiates the Monte-Carlo mean
  * and unbiased variance of e_y, the barrier h and the hinge of C_safe, then the dynamics. */
 double orc_repair_objective(const orc_problem* p, const double* x0, const double* v,
-                            uint32_t solve_ctr, double* grad)
+                            uint32_t solve_ctr, double* grad, double* args_out)
 {
     const int nx = orc_nx(p), M = p->M, T = p->T, e = p->ey_index;
     double L_w[36];
@@ -500,6 +500,8 @@ double orc_repair_objective(const orc_problem* p, const double* x0, const double
         arg[t] = -hz[t] + (1.0 - p->gamma) * hz[t - 1];
         J += c_safe(p, hz[t], hz[t - 1]);
     }
+    if (args_out)
+        for (int t = 0; t <= T; ++t) args_out[t] = arg[t];
     if (grad) {
         double* G = (double*)calloc((size_t)M * nx, sizeof(double));   /* dJ/dx^n_t */
         for (int i = 0; i < 2 * T; ++i) grad[i] = 0.0;

@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
         "bssmppi_timing": (ctypes.c_int, [vp, i32]),
         "bssmppi_timing_read": (ctypes.c_int, [vp, vp, vp, i32, ctypes.POINTER(i32)]),
         "bssmppi_update_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, i32, vp]),
+        "bssmppi_repair_grad": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "bssmppi_repair": (ctypes.c_int, [vp, vp, vp, i32, ctypes.c_float, vp]),
         "bssmppi_model_step": (ctypes.c_int, [vp, vp, vp, vp, i64]),
         "bssmppi_philox4x32_10": (ctypes.c_int, [vp, u64, vp, i64, vp]),
         "bssmppi_box_muller": (ctypes.c_int, [vp, vp, i64, vp]),
@@ -234,6 +236,51 @@ def update_noalloc(S, eps, v, w, u0=None, diag=None, counter=None, lam=1.0, comp
     K, T = int(S.numel()), int(eps.numel() // (2 * max(1, S.numel())))
     _check(load().bssmppi_update_noalloc(_ptr(S), _ptr(eps), _ptr(v), _ptr(w), _ptr(u0), _ptr(diag), _ptr(counter),
                                          K, T, ctypes.c_float(lam), int(bool(compensated)), _stream_handle(stream)))
+
+
+def repair_grad(h, x0, v, grad, J=None):
+    _check(load().bssmppi_repair_grad(h, _ptr(x0), _ptr(v), _ptr(grad), _ptr(J)), h)
+
+
+def repair(h, x0, v=None, iters=5, step=2e-6, J=None):
+    _check(load().bssmppi_repair(h, _ptr(x0), _ptr(v), int(iters), ctypes.c_float(step), _ptr(J)), h)
+
+
+def _repair_objective_function():
+    import torch
+
+    class RepairObjective(torch.autograd.Function):
+        """J_r(v) of bssmppi_repair_grad as a differentiable torch function of the nominal v [T, 2].
+
+        forward runs the library's forward rollout and adjoint sweep once and keeps dJ/dv; backward
+        scales it by the incoming gradient. x0 and the handle are not differentiated."""
+
+        @staticmethod
+        def forward(ctx, v, x0, handle):
+            v = v.contiguous()
+            J = torch.empty(1, dtype=torch.float32, device=v.device)
+            grad = torch.empty_like(v)
+            repair_grad(handle, x0.contiguous(), v, grad, J)
+            ctx.save_for_backward(grad)
+            return J[0]
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (grad,) = ctx.saved_tensors
+            return gJ * grad, None, None
+
+    return RepairObjective
+
+
+_RepairObjective = None
+
+
+def repair_objective(v, x0, handle):
+    """Differentiable repair objective J_r(v) (a torch.autograd.Function backed by the adjoint kernel)."""
+    global _RepairObjective
+    if _RepairObjective is None:
+        _RepairObjective = _repair_objective_function()
+    return _RepairObjective.apply(v, x0, handle)
 
 
 def model_step(h, x, u, x_next):

@@ -18,7 +18,9 @@ struct DevParams {
     int spw;          // control samples per warp (32 / seg)
     int uniform;      // 1: every lane of a segment holds exactly P valid particles
     int ey, crn, record, n_track_mask;
+    int mean_mask;    // bit i: the cost needs the belief mean of state i (always all when recording)
     uint32_t key0, key1;
+    uint32_t rk0[10], rk1[10];       // Philox round keys k + r W (the key schedule, precomputed)
     float dt, h, inv_m, inv_Iz, lf, lr, tB, tC, Df, Dr, vx_floor;
     float umin0, umin1, umax0, umax1;
     float Le00, Le10, Le11;          // Cholesky factor of Sigma_eps
@@ -52,6 +54,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same ten rounds with the key schedule taken from precomputed round keys (kernel parameters),
+// which saves the two key additions of every round.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk0, const uint32_t* rk1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk0[round], lo1, hi0 ^ c.w ^ rk1[round], lo0);
+    }
+    return c;
+}
+
 // Counter layout of the solve's streams: word 0 = step | (call << 16), word 1 = particle,
 // word 2 = sample, word 3 = (stream << 28) | (solve counter & 0x0fffffff).
 enum : uint32_t { kStreamControl = 0u, kStreamDisturbance = 1u, kStreamInitial = 3u };
@@ -59,21 +74,23 @@ enum : uint32_t { kStreamControl = 0u, kStreamDisturbance = 1u, kStreamInitial =
 __device__ __forceinline__ uint4 draw_words(const DevParams& P, uint32_t step, uint32_t call, uint32_t particle,
                                             uint32_t sample, uint32_t stream, uint32_t ctr)
 {
-    return philox4x32_10(make_uint4(step | (call << 16), particle, sample, (stream << 28) | (ctr & 0x0fffffffu)),
-                         P.key0, P.key1);
+    return philox4x32_10_rk(make_uint4(step | (call << 16), particle, sample, (stream << 28) | (ctr & 0x0fffffffu)),
+                            P.rk0, P.rk1);
 }
 
 // Box-Muller from two 32-bit words: u1 in (0, 1], u2 in [0, 1) from their top 24 bits (exact in
-// FP32), z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+// FP32), z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2). The angle is taken centred,
+// theta = 2 pi (u2 - 1/2) in [-pi, pi) (u2 - 1/2 is exact), where the hardware sine and cosine are
+// accurate to 2^-21.4 absolute; (cos, sin)(2 pi u2) = -(cos, sin)(theta).
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 {
     const float two_m24 = 5.9604644775390625e-08f;
     const float u1 = (float)((a >> 8) + 1u) * two_m24;
-    const float u2 = (float)(b >> 8) * two_m24;
+    const float theta = 6.28318530717958647692f * ((float)(b >> 8) * two_m24 - 0.5f);
     const float rad = sqrtf(-2.0f * logf(u1));
     float sn, cs;
-    sincospif(2.0f * u2, &sn, &cs);
-    return make_float2(rad * cs, rad * sn);
+    __sincosf(theta, &sn, &cs);
+    return make_float2(-rad * cs, -rad * sn);
 }
 
 // Standard normals of one draw (Gaussian pair i from call i/2, words 2(i%2), 2(i%2)+1).
@@ -129,15 +146,18 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const float*
                                                 const Control& u, float (&x)[6])
 {
     const float vx = x[0], vy = x[1], r = x[2], ep = x[3], ey = x[4];
-    const float inv_vx = 1.0f / fmaxf(vx, P.vx_floor);
+    // v_x >= vx_floor >= 1 and 1 - kappa e_y is near 1, so the fast (2-ulp) quotients are safe.
+    const float inv_vx = __fdividef(1.0f, fmaxf(vx, P.vx_floor));
     const float alpha_f = u.steer - atanf((vy + P.lf * r) * inv_vx);
     const float alpha_r = -atanf((vy - P.lr * r) * inv_vx);
-    const float Ff = P.Df * sinf(P.tC * atanf(P.tB * alpha_f));
-    const float Fr = P.Dr * sinf(P.tC * atanf(P.tB * alpha_r));
+    // |C atan(B alpha)| < C pi / 2 < pi: inside the range where the hardware sine's absolute error
+    // is at most 2^-21.4 of the unit amplitude (a relative force error of a few FP32 ulps).
+    const float Ff = P.Df * __sinf(P.tC * atanf(P.tB * alpha_f));
+    const float Fr = P.Dr * __sinf(P.tC * atanf(P.tB * alpha_r));
     const float kap_s = track_curvature(P, kap, s0 + x[5]);
     float sp, cp;
-    sincosf(ep, &sp, &cp);
-    const float sdot = (vx * cp - vy * sp) / (1.0f - kap_s * ey);
+    sincosf(ep, &sp, &cp);  // e_psi is small and multiplies v_x: keep the ulp-accurate version
+    const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
     const float dvx = u.accel - Ff * u.sin_steer * P.inv_m + vy * r;
     const float dvy = (Ff * u.cos_steer + Fr) * P.inv_m - vx * r;
     const float dr = (P.lf * Ff * u.cos_steer - P.lr * Fr) * P.inv_Iz;
@@ -151,6 +171,74 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const float*
     x[5] = fmaf(P.h, sdot, x[5]);
 }
 
+// Reverse mode of one bicycle substep x' = x + h F(x, u). On entry g holds dL/dx'; on exit g holds
+// dL/dx, and dL/du is added to (g_steer, g_accel). The partial derivatives are those of the
+// forward formulas above: d atan(q)/dq = 1/(1 + q^2), d sin = cos, the quotient rule for s', and
+// the piecewise-linear slope of the curvature table.
+__device__ __forceinline__ void bicycle_substep_vjp(const DevParams& P, const float* __restrict__ kap, float s0,
+                                                    const Control& u, const float (&x)[6], float (&g)[6],
+                                                    float& g_steer, float& g_accel)
+{
+    const float vx = x[0], vy = x[1], r = x[2], ep = x[3], ey = x[4];
+    const float vxh = fmaxf(vx, P.vx_floor);
+    const float inv_vx = __fdividef(1.0f, vxh);
+    const float yf = vy + P.lf * r, yr = vy - P.lr * r;
+    const float alpha_f = u.steer - atanf(yf * inv_vx);
+    const float alpha_r = -atanf(yr * inv_vx);
+    const float bf = P.tB * alpha_f, br = P.tB * alpha_r;
+    const float tf = atanf(bf), tr = atanf(br);
+    float sf, cf;
+    __sincosf(P.tC * tf, &sf, &cf);
+    const float cr = __cosf(P.tC * tr);
+    const float Ff = P.Df * sf;
+    const float dFf = __fdividef(P.Df * cf * P.tC * P.tB, 1.0f + bf * bf);
+    const float dFr = __fdividef(P.Dr * cr * P.tC * P.tB, 1.0f + br * br);
+    const float s = s0 + x[5];
+    const float xs = s * P.track_scale;
+    const float fl = floorf(xs);
+    const int i = ((int)fl) & P.n_track_mask;
+    const float k0 = kap[i], k1 = kap[i + 1];
+    const float kap_s = fmaf(xs - fl, k1 - k0, k0);
+    const float dkap = (k1 - k0) * P.track_scale;
+    float sp, cp;
+    sincosf(ep, &sp, &cp);
+    const float num = vx * cp - vy * sp;
+    const float inv_den = __fdividef(1.0f, 1.0f - kap_s * ey);
+    const float sdot = num * inv_den;
+
+    float a[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a[j] = P.h * g[j];
+    const float gFf = a[0] * (-u.sin_steer * P.inv_m) + a[1] * (u.cos_steer * P.inv_m) + a[2] * (P.lf * u.cos_steer * P.inv_Iz);
+    const float gFr = a[1] * P.inv_m - a[2] * (P.lr * P.inv_Iz);
+    const float gsdot = -a[3] * kap_s + a[5];
+    const float gkap = -a[3] * sdot + gsdot * num * ey * inv_den * inv_den;
+    const float gnum = gsdot * inv_den;
+    const float gey = gsdot * num * kap_s * inv_den * inv_den;
+    float gvx = gnum * cp - a[1] * r + a[4] * sp;
+    float gvy = -gnum * sp + a[0] * r + a[4] * cp;
+    const float gep = gnum * (-vx * sp - vy * cp) + a[4] * (vx * cp - vy * sp);
+    float gr = a[0] * vy - a[1] * vx + a[3];
+    g_steer += a[0] * (-Ff * u.cos_steer * P.inv_m) + a[1] * (-Ff * u.sin_steer * P.inv_m)
+             + a[2] * (-P.lf * Ff * u.sin_steer * P.inv_Iz);
+    g_accel += a[0];
+    const float gaf = gFf * dFf, gar = gFr * dFr;
+    g_steer += gaf;
+    const float inv_qf = __fdividef(1.0f, vxh * vxh + yf * yf);
+    const float inv_qr = __fdividef(1.0f, vxh * vxh + yr * yr);
+    const float gyf = -gaf * vxh * inv_qf, gyr = -gar * vxh * inv_qr;
+    const float gvxh = gaf * yf * inv_qf + gar * yr * inv_qr;
+    gvy += gyf + gyr;
+    gr += P.lf * gyf - P.lr * gyr;
+    if (vx > P.vx_floor) gvx += gvxh;
+    g[0] += gvx;
+    g[1] += gvy;
+    g[2] += gr;
+    g[3] += gep;
+    g[4] += gey;
+    g[5] += gkap * dkap;
+}
+
 // Planar double integrator, exact zero-order-hold step.
 __device__ __forceinline__ void double_integrator_step(const DevParams& P, const Control& u, float (&x)[4])
 {
@@ -159,6 +247,16 @@ __device__ __forceinline__ void double_integrator_step(const DevParams& P, const
     x[1] = fmaf(hdt2, u.accel, fmaf(dt, x[3], x[1]));
     x[2] = fmaf(dt, u.steer, x[2]);
     x[3] = fmaf(dt, u.accel, x[3]);
+}
+
+// Reverse mode of the double-integrator step: g (dL/dx') -> dL/dx in place, dL/du added.
+__device__ __forceinline__ void double_integrator_step_vjp(const DevParams& P, float (&g)[4], float& g_ax, float& g_ay)
+{
+    const float dt = P.dt, hdt2 = 0.5f * P.dt * P.dt;
+    g_ax += hdt2 * g[0] + dt * g[2];
+    g_ay += hdt2 * g[1] + dt * g[3];
+    g[2] += dt * g[0];
+    g[3] += dt * g[1];
 }
 
 // One full model step f(x, u) (n_sub substeps for the bicycle).

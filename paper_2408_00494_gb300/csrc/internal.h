@@ -9,15 +9,20 @@ namespace bss {
 
 struct DevParams;
 
-constexpr int kRollWarps = 4;       // warps per rollout block
 constexpr int kUpdThreads = 512;    // threads per weights/update block
 constexpr int kUpdMaxBlocks = 148;  // upper bound on weights/update blocks (scratch is sized by it)
 
-size_t rollout_smem_bytes(const DevParams& dp);
-cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp);
-cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const float* x0, const float* Sigma0,
-                           const float* v, const uint32_t* ctr, float* S, float* eps, float* mean, float* var,
-                           cudaStream_t st);
+// Launch shape of the persistent rollout kernel, planned once per handle.
+struct RollLaunch {
+    int grid = 1;      // blocks (at most one per SM)
+    int wpb = 1;       // warps per block
+    size_t smem = 0;   // dynamic shared memory per block
+};
+size_t rollout_smem_bytes(const DevParams& dp, int wpb);
+cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, RollLaunch& L);
+cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
+                           const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
+                           float* var, cudaStream_t st);
 cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, float* xn, int64_t n,
                               cudaStream_t st);
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st);
@@ -38,6 +43,12 @@ struct UpdateIO {
 };
 cudaError_t update_launch(int K, int T, float lambda, bool comp, const UpdateIO& io, cudaStream_t st);
 cudaError_t shift_launch(float* v, int T, int n, cudaStream_t st);
+
+// Shield repair (adjoint of the belief-barrier penalty of the nominal rollout).
+size_t repair_scratch_floats(const DevParams& dp);
+cudaError_t repair_prepare(const DevParams& dp);
+cudaError_t repair_launch(const DevParams& dp, const float* x0, float* v, const uint32_t* ctr, float* X, float* grad,
+                          float* J, int iters, float step, cudaStream_t st);
 
 // Records the calling thread's error message for entry points without a handle
 // (read back through bssmppi_last_error(NULL)).

@@ -10,6 +10,8 @@
 #include "device.cuh"
 #include "internal.h"
 
+#include <algorithm>
+
 namespace bss {
 
 struct RollIO {
@@ -25,7 +27,8 @@ struct RollIO {
 
 // Moments of the M particles of one sample. x[p] is particle ls + seg p (valid iff < M).
 // mean[i] = particle mean, var[i] = unbiased variance 1/(M-1) sum (x - mean)^2 (Algorithm 2);
-// var is produced for EY only unless all_var.
+// var is produced for EY only unless all_var. Means outside dp.mean_mask (states no cost term
+// weights) are not merged across lanes and are left lane-local.
 template <int NX, int EY, int P, bool COMP>
 __device__ __forceinline__ void belief_moments(const DevParams& dp, const float (&x)[P][NX], int ls, int seg,
                                                bool all_var, float (&mean)[NX], float (&var)[NX])
@@ -64,6 +67,7 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
                 const float half_n = 0.5f * cnt;
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
+                    if (!((dp.mean_mask >> i) & 1)) continue;  // a mean no cost term reads
                     const float mb = __shfl_xor_sync(0xffffffffu, mean[i], off);
                     if (i == EY || all_var) {
                         const float d = mb - mean[i];
@@ -82,6 +86,7 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
                 const float fa = cnt * inv, fb = cb * inv, fab = cnt * cb * inv;
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
+                    if (!((dp.mean_mask >> i) & 1)) continue;
                     const float mb = __shfl_xor_sync(0xffffffffu, mean[i], off);
                     if (i == EY || all_var) {
                         const float d = mb - mean[i];
@@ -112,6 +117,7 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
         for (int off = seg >> 1; off > 0; off >>= 1) {
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
+                if (!((dp.mean_mask >> i) & 1)) continue;
                 s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
                 if (i == EY || all_var) q[i] += __shfl_xor_sync(0xffffffffu, q[i], off);
             }
@@ -151,34 +157,28 @@ __device__ __forceinline__ void cholesky_psd(const float* A, float (&L)[NX][NX])
     }
 }
 
+// Largest block each particle count is compiled for (bounds the registers ptxas may use).
+template <int P>
+constexpr int roll_max_threads()
+{
+    return P <= 2 ? 1024 : (P == 4 ? 768 : 512);
+}
+
+// One sample group (the spw samples of one warp): control sequence, rollout, moments, cost.
 template <int MODEL, int P, bool COMP>
-__global__ void __launch_bounds__(kRollWarps * kWarp) rollout_kernel(const DevParams dp, const RollIO io)
+__device__ __forceinline__ void rollout_group(const DevParams& dp, const RollIO& io, const float* __restrict__ kap_s,
+                                              const float* __restrict__ v_s, float* __restrict__ my_u, int group,
+                                              uint32_t ctr)
 {
     constexpr int NX = MODEL == 0 ? 6 : 4;
     constexpr int EY = MODEL == 0 ? 4 : 1;
-    extern __shared__ float smem[];
-    const int ntab = dp.n_track_mask + 1;
-    float* kap_s = smem;
-    float* v_s = smem + ((ntab + 1 + 3) & ~3);
-    float* u_s = v_s + 2 * dp.T;
-
-    if constexpr (MODEL == 0) {
-        for (int i = threadIdx.x; i <= ntab; i += blockDim.x) kap_s[i] = dp.kappa[i];
-    }
-    for (int i = threadIdx.x; i < 2 * dp.T; i += blockDim.x) v_s[i] = io.v[i];
-    __syncthreads();
-
-    const uint32_t ctr = *io.ctr;
     const int lane = threadIdx.x & (kWarp - 1);
-    const int warp = threadIdx.x / kWarp;
     const int seg = dp.seg;
     const int ls = lane & (seg - 1);
-    const int slot = warp * dp.spw + lane / seg;
-    const int k = blockIdx.x * (kRollWarps * dp.spw) + slot;
+    const int k = group * dp.spw + lane / seg;
     const bool active = k < dp.K;
     const int kc = active ? k : dp.K - 1;  // inactive segments shadow a valid sample, write nothing
     const uint32_t kk = dp.crn ? 0u : (uint32_t)kc;
-    float* my_u = u_s + slot * 2 * dp.T;
 
     // (a1, a2) control noise eps ~ N(0, Sigma_eps) and clamped samples u = clamp(v + eps); the
     // lanes of the segment split the horizon. eps_eff = u - v feeds the update.
@@ -303,56 +303,126 @@ __global__ void __launch_bounds__(kRollWarps * kWarp) rollout_kernel(const DevPa
     if (writer) io.S[k] = total;
 }
 
-size_t rollout_smem_bytes(const DevParams& dp)
+// Persistent rollout: the block's warps walk the sample groups with a grid stride. The curvature
+// table and the nominal sequence are staged in shared memory once per block.
+template <int MODEL, int P, bool COMP>
+__global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const DevParams dp, const RollIO io)
+{
+    extern __shared__ float smem[];
+    const int ntab = dp.n_track_mask + 1;
+    float* kap_s = smem;
+    float* v_s = smem + ((ntab + 1 + 3) & ~3);
+    float* u_s = v_s + 2 * dp.T;
+
+    if constexpr (MODEL == 0) {
+        for (int i = threadIdx.x; i <= ntab; i += blockDim.x) kap_s[i] = dp.kappa[i];
+    }
+    for (int i = threadIdx.x; i < 2 * dp.T; i += blockDim.x) v_s[i] = io.v[i];
+    __syncthreads();
+
+    const uint32_t ctr = *io.ctr;
+    const int warp = threadIdx.x / kWarp;
+    const int wpb = blockDim.x / kWarp;
+    const int lane = threadIdx.x & (kWarp - 1);
+    float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * 2 * dp.T;
+    const int n_groups = (dp.K + dp.spw - 1) / dp.spw;
+    for (int group = blockIdx.x * wpb + warp; group < n_groups; group += gridDim.x * wpb) {
+        rollout_group<MODEL, P, COMP>(dp, io, kap_s, v_s, my_u, group, ctr);
+        __syncwarp();  // the next group's prologue rewrites my_u
+    }
+}
+
+size_t rollout_smem_bytes(const DevParams& dp, int wpb)
 {
     const int ntab = dp.n_track_mask + 1;
-    const size_t floats = (size_t)((ntab + 1 + 3) & ~3) + 2 * (size_t)dp.T + (size_t)kRollWarps * dp.spw * 2 * dp.T;
+    const size_t floats = (size_t)((ntab + 1 + 3) & ~3) + 2 * (size_t)dp.T + (size_t)wpb * dp.spw * 2 * dp.T;
     return floats * sizeof(float);
 }
 
-template <int MODEL, bool COMP>
-static cudaError_t launch_model(const DevParams& dp, const RollIO& io, int P, cudaStream_t st)
+template <int MODEL, int P, bool COMP>
+static cudaError_t launch_one(const DevParams& dp, const RollIO& io, const RollLaunch& L, cudaStream_t st)
 {
-    const int per_block = kRollWarps * dp.spw;
-    const dim3 grid((dp.K + per_block - 1) / per_block);
-    const dim3 block(kRollWarps * kWarp);
-    const size_t smem = rollout_smem_bytes(dp);
-    switch (P) {
-    case 1: rollout_kernel<MODEL, 1, COMP><<<grid, block, smem, st>>>(dp, io); break;
-    case 2: rollout_kernel<MODEL, 2, COMP><<<grid, block, smem, st>>>(dp, io); break;
-    case 4: rollout_kernel<MODEL, 4, COMP><<<grid, block, smem, st>>>(dp, io); break;
-    case 8: rollout_kernel<MODEL, 8, COMP><<<grid, block, smem, st>>>(dp, io); break;
-    default: return cudaErrorInvalidValue;
-    }
+    rollout_kernel<MODEL, P, COMP><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io);
     return cudaGetLastError();
 }
 
 template <int MODEL, bool COMP>
-static cudaError_t configure_model(int P, size_t smem)
+static cudaError_t launch_model(const DevParams& dp, const RollIO& io, int P, const RollLaunch& L, cudaStream_t st)
 {
-    cudaError_t e = cudaSuccess;
-#define BSS_SET(PP)                                                                                        \
-    if (P == PP) e = cudaFuncSetAttribute(rollout_kernel<MODEL, PP, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    BSS_SET(1) BSS_SET(2) BSS_SET(4) BSS_SET(8)
-#undef BSS_SET
-    return e;
+    switch (P) {
+    case 1: return launch_one<MODEL, 1, COMP>(dp, io, L, st);
+    case 2: return launch_one<MODEL, 2, COMP>(dp, io, L, st);
+    case 4: return launch_one<MODEL, 4, COMP>(dp, io, L, st);
+    case 8: return launch_one<MODEL, 8, COMP>(dp, io, L, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
-cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp)
+// Block shape: one block per SM with w warps, w chosen to minimise the makespan of an issue-bound
+// kernel, ceil(groups / (SMs w)) rounds of w warps each, among the w that fit on an SM.
+template <int MODEL, int P, bool COMP>
+static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
 {
-    const size_t smem = rollout_smem_bytes(dp);
-    if (smem <= 48 * 1024) return cudaSuccess;
-    if (dp.nx == 6) return comp ? configure_model<0, true>(P, smem) : configure_model<0, false>(P, smem);
-    return comp ? configure_model<1, true>(P, smem) : configure_model<1, false>(P, smem);
+    auto kern = rollout_kernel<MODEL, P, COMP>;
+    int dev = 0, sms = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int max_w = roll_max_threads<P>() / kWarp;
+    const size_t smem_cap = std::min(rollout_smem_bytes(dp, max_w), (size_t)optin);
+    if (rollout_smem_bytes(dp, 1) > smem_cap) return cudaErrorInvalidValue;  // one warp's share does not fit
+    if (smem_cap > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+        if (e != cudaSuccess) return e;
+    }
+    const long groups = (dp.K + dp.spw - 1) / dp.spw;
+    long best_cost = -1;
+    int best_w = 1;
+    for (int w = max_w; w >= 1; --w) {
+        if (rollout_smem_bytes(dp, w) > smem_cap) continue;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, w * kWarp, rollout_smem_bytes(dp, w));
+        if (e != cudaSuccess) return e;
+        if (nb < 1) continue;
+        const long slots = (long)sms * w;
+        const long cost = ((groups + slots - 1) / slots) * w;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_w = w;
+        }
+    }
+    L.wpb = best_w;
+    L.grid = (int)std::min<long>(sms, (groups + best_w - 1) / best_w);
+    L.smem = rollout_smem_bytes(dp, best_w);
+    return cudaSuccess;
 }
 
-cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const float* x0, const float* Sigma0,
-                           const float* v, const uint32_t* ctr, float* S, float* eps, float* mean, float* var,
-                           cudaStream_t st)
+template <int MODEL, bool COMP>
+static cudaError_t plan_model(const DevParams& dp, int P, RollLaunch& L)
+{
+    switch (P) {
+    case 1: return plan_one<MODEL, 1, COMP>(dp, L);
+    case 2: return plan_one<MODEL, 2, COMP>(dp, L);
+    case 4: return plan_one<MODEL, 4, COMP>(dp, L);
+    case 8: return plan_one<MODEL, 8, COMP>(dp, L);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, RollLaunch& L)
+{
+    if (dp.nx == 6) return comp ? plan_model<0, true>(dp, P, L) : plan_model<0, false>(dp, P, L);
+    return comp ? plan_model<1, true>(dp, P, L) : plan_model<1, false>(dp, P, L);
+}
+
+cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
+                           const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
+                           float* var, cudaStream_t st)
 {
     RollIO io{x0, Sigma0, v, ctr, S, eps, mean, var};
-    if (dp.nx == 6) return comp ? launch_model<0, true>(dp, io, P, st) : launch_model<0, false>(dp, io, P, st);
-    return comp ? launch_model<1, true>(dp, io, P, st) : launch_model<1, false>(dp, io, P, st);
+    if (dp.nx == 6) return comp ? launch_model<0, true>(dp, io, P, L, st) : launch_model<0, false>(dp, io, P, L, st);
+    return comp ? launch_model<1, true>(dp, io, P, L, st) : launch_model<1, false>(dp, io, P, L, st);
 }
 
 // Deterministic model step for n independent states (no disturbance), for model checks.

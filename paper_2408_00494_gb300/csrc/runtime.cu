@@ -13,6 +13,7 @@ struct bssmppi_ctx {
     bssmppi_params prm{};
     bss::DevParams dp{};
     int P = 1;            // particles per lane (1, 2, 4 or 8)
+    bss::RollLaunch roll; // persistent rollout launch shape
     int nx = 6;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -30,6 +31,8 @@ struct bssmppi_ctx {
     uint32_t* d_ctr = nullptr;
     float* d_partial = nullptr;
     unsigned int* d_ticket = nullptr;
+    float* d_repair_X = nullptr;  // stored particle states of the repair rollout
+    float* d_repair_J = nullptr;  // objective of the last repair_grad call
     float* h_stage = nullptr;   // pinned host staging: x0 | Sigma0 | v | u0
     // per-phase timing ring: 4 events per recorded solve
     cudaEvent_t* ev = nullptr;
@@ -159,7 +162,7 @@ int alloc(bssmppi_ctx* h, T** ptr, size_t count)
 void release(bssmppi_ctx* h)
 {
     void* ptrs[] = {h->d_kappa, h->d_S, h->d_w, h->d_eps, h->d_mean, h->d_var, h->d_v, h->d_x0, h->d_Sigma0,
-                    h->d_u0, h->d_diag, h->d_ctr, h->d_partial, h->d_ticket};
+                    h->d_u0, h->d_diag, h->d_ctr, h->d_partial, h->d_ticket, h->d_repair_X, h->d_repair_J};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_stage) cudaFreeHost(h->h_stage);
@@ -219,6 +222,10 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     d.uniform = (p->M == seg * P) ? 1 : 0;
     d.ey = p->ey_index; d.crn = p->crn_disturbance ? 1 : 0; d.record = p->record_moments ? 1 : 0;
     d.key0 = (uint32_t)(p->seed & 0xffffffffu); d.key1 = (uint32_t)(p->seed >> 32);
+    for (int r = 0; r < 10; ++r) {  // Philox key schedule: k + r (0x9E3779B9, 0xBB67AE85)
+        d.rk0[r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
+        d.rk1[r] = d.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     d.dt = p->dt; d.h = p->dt / (float)d.n_sub;
     d.inv_m = 1.0f / p->mass; d.inv_Iz = 1.0f / p->Iz; d.lf = p->lf; d.lr = p->lr;
     d.tB = p->tire_B; d.tC = p->tire_C;
@@ -238,10 +245,12 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     d.nu = (float)(std::sqrt(2.0) * inverse_erf(1.0 - 2.0 * (double)p->delta));
     d.one_m_gamma = 1.0f - p->gamma;
     d.ctrl_w = p->ctrl_w; d.Csafe = p->C_safe; d.Cobs = p->C_obs; d.wT = p->w_T;
+    d.mean_mask = 0;
     for (int i = 0; i < 6; ++i) {
         d.xg[i] = p->x_goal[i];
         d.Q[i] = i < nx ? p->Q[i] : 0.0f;
         d.Qf[i] = i < nx ? p->Qf[i] : 0.0f;
+        if (i < nx && (d.Q[i] != 0.0f || d.Qf[i] != 0.0f || i == p->ey_index || p->record_moments)) d.mean_mask |= 1 << i;
     }
     const int ntab = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_track : 2;
     d.n_track_mask = ntab - 1;
@@ -265,6 +274,8 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ctr, 1);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_partial, (size_t)G * T * 2);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ticket, 1);
+    if (rc == BSSMPPI_OK && p->M <= 256) rc = alloc(h, &h->d_repair_X, bss::repair_scratch_floats(h->dp));
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_repair_J, 1);
     if (rc == BSSMPPI_OK) {
         e = cudaMallocHost(reinterpret_cast<void**>(&h->h_stage), sizeof(float) * (6 + 36 + 2 * T + 2));
         if (e != cudaSuccess) {
@@ -288,7 +299,8 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
         if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMemset(h->d_ticket, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(h->d_diag, 0, sizeof(float) * BSSMPPI_NDIAG);
-        if (e == cudaSuccess) e = bss::rollout_prepare(h->dp, h->P, p->compensated != 0);
+        if (e == cudaSuccess) e = bss::rollout_prepare(h->dp, h->P, p->compensated != 0, h->roll);
+        if (e == cudaSuccess) e = bss::repair_prepare(h->dp);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = cuda_fail(h, e, "create");
     }
@@ -311,7 +323,7 @@ int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* 
     if (d_v) BSS_CUDA(h, cudaMemcpyAsync(h->d_v, d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
     cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 4 * h->ev_count : nullptr;
     if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], h->stream));
-    BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, d_x0, d_Sigma0, h->d_v, h->d_ctr,
+    BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, h->d_v, h->d_ctr,
                                     h->d_S, h->d_eps, h->d_mean, h->d_var, h->stream));
     if (ev) BSS_CUDA(h, cudaEventRecord(ev[1], h->stream));
     bss::UpdateIO io{h->d_S, h->d_eps, h->d_v, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, h->d_ctr,
@@ -412,6 +424,29 @@ int bssmppi_timing_read(bssmppi_t h, float* h_rollout_ms, float* h_update_ms, in
         if (h_update_ms) h_update_ms[i] = b;
     }
     if (count) *count = n;
+    return BSSMPPI_OK;
+}
+
+int bssmppi_repair_grad(bssmppi_t h, const float* d_x0, const float* d_v, float* d_grad, float* d_J)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!d_x0 || !d_grad) return fail(h, BSSMPPI_EINVAL, "x0 and grad must be non-NULL");
+    if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256");
+    const float* v = d_v ? d_v : h->d_v;
+    BSS_CUDA(h, bss::repair_launch(h->dp, d_x0, const_cast<float*>(v), h->d_ctr, h->d_repair_X, d_grad,
+                                   d_J ? d_J : h->d_repair_J, 0, 0.0f, h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_repair(bssmppi_t h, const float* d_x0, float* d_v, int32_t iters, float step, float* d_J)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!d_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
+    if (iters < 1 || iters > 1000) return fail(h, BSSMPPI_EINVAL, "iters must be in [1, 1000]");
+    if (!(step >= 0.0f) || !std::isfinite(step)) return fail(h, BSSMPPI_EINVAL, "step must be finite and >= 0");
+    if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256");
+    BSS_CUDA(h, bss::repair_launch(h->dp, d_x0, d_v ? d_v : h->d_v, h->d_ctr, h->d_repair_X, nullptr, d_J, iters,
+                                   step, h->stream));
     return BSSMPPI_OK;
 }
 

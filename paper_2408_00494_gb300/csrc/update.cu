@@ -159,11 +159,25 @@ __global__ void __launch_bounds__(kUpdThreads) weights_update_kernel(int K, int 
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (tid < TN) {
+    // Thread (g, o) adds the partials of blocks g, g + NG, ... for output o (independent loads in
+    // flight across the group), then the NG group sums are added in group order.
+    {
         float ps = 0.0f, pc = 0.0f;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-            const float x = __ldcg(io.partial + (size_t)b * TN + tid);
-            if constexpr (COMP) comp_merge(ps, pc, x, 0.0f); else ps += x;
+        if (g < NG) {
+            for (int b = g; b < (int)gridDim.x; b += NG) {
+                const float x = __ldcg(io.partial + (size_t)b * TN + o);
+                if constexpr (COMP) comp_merge(ps, pc, x, 0.0f); else ps += x;
+            }
+        }
+        grid_acc[tid] = ps;
+        grid_cmp[tid] = pc;
+    }
+    __syncthreads();
+    if (tid < TN) {
+        float ps = grid_acc[tid], pc = grid_cmp[tid];
+        for (int gg = 1; gg < NG; ++gg) {
+            if constexpr (COMP) comp_merge(ps, pc, grid_acc[gg * TN + tid], grid_cmp[gg * TN + tid]);
+            else ps += grid_acc[gg * TN + tid];
         }
         const float vn = io.v[tid] + (COMP ? ps + pc : ps);
         io.v[tid] = vn;

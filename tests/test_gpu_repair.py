@@ -1,0 +1,109 @@
+"""Shield repair through the hand-written adjoint kernel (bssmppi_repair_grad / bssmppi_repair).
+
+The GPU objective and gradient are compared with the FP64 oracle's objective and adjoint, and the
+gradient with central finite differences (eps = 1e-4) of the oracle's objective. Cases are chosen
+with every hinge argument of the DCBF penalty at least 1e-2 away from its kink, where FP32 and FP64
+could decide the hinge differently. Tolerances: J rel 1e-4; gradient 2e-3 of each control
+channel's largest component (FP32 through T steps of dynamics, adjoint and sample variance).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2408_00494_gb300 import bssmppi  # noqa: E402
+
+
+def _case(model):
+    if model == "racing":
+        p = workload.config1()
+        p.K = 64
+        x0 = np.array([10.0, 0.1, 0.05, 0.1, 2.0, 5.0], np.float32)
+        v = np.zeros((p.T, 2), np.float32)
+        v[:, 0] = 0.043
+    else:
+        p = workload.double_integrator_problem(K=64, M=48, T=30, q_w=0.05)
+        p.w_T = 2.0
+        x0 = np.array([0.0, 1.0, 0.5, 0.9], np.float32)
+        v = workload.random_nominal(p, 3, scale=(0.5, 0.5))
+    return p, x0, v
+
+
+def _gpu_grad(c, x0, v):
+    g = torch.empty((v.shape[0], 2), device="cuda")
+    J = torch.empty(1, device="cuda")
+    bssmppi.repair_grad(c.h, torch.as_tensor(x0, device="cuda"), torch.as_tensor(v, device="cuda"), g, J)
+    torch.cuda.synchronize()
+    return float(J.item()), g.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("model", ["racing", "double_integrator"])
+def test_repair_gradient_matches_oracle_adjoint_and_finite_differences(model):
+    p, x0, v = _case(model)
+    ctr = 17
+    o = oracle.Oracle(p)
+    J_ref, g_ref, args = o.repair_objective(x0, v.astype(np.float64), ctr, grad=True, want_args=True)
+    assert J_ref > 0.0 and np.min(np.abs(args[1:])) > 1e-2
+    c = bssmppi.Controller(p)
+    bssmppi.set_counter(c.h, ctr)
+    J, g = _gpu_grad(c, x0, v)
+    c.close()
+    assert J == pytest.approx(J_ref, rel=1e-4)
+    scale = np.abs(g_ref).max(axis=0)
+    assert np.all(np.abs(g - g_ref) <= 2e-3 * scale), np.abs(g - g_ref).max(axis=0) / scale
+    # central differences of the FP64 objective along random directions
+    rng = np.random.default_rng(0)
+    eps = 1e-4
+    for _ in range(3):
+        d = rng.normal(size=v.shape)
+        fd = (o.repair_objective(x0, v + eps * d, ctr, grad=False)
+              - o.repair_objective(x0, v - eps * d, ctr, grad=False)) / (2 * eps)
+        assert float(np.sum(g * d)) == pytest.approx(fd, rel=2e-3)
+    print(f"[repair {model}] J {J:.6g} (oracle {J_ref:.6g}); grad max rel err per channel "
+          f"{(np.abs(g - g_ref).max(axis=0) / scale).tolist()}")
+
+
+def test_repair_iterations_match_oracle_projected_gradient():
+    p, x0, v = _case("racing")
+    ctr, iters, step = 5, 5, 2e-6
+    o = oracle.Oracle(p)
+    vr = v.astype(np.float64)
+    Jr = []
+    lo, hi = np.array(p.u_min, float), np.array(p.u_max, float)
+    lo32, hi32 = lo.astype(np.float32).astype(float), hi.astype(np.float32).astype(float)
+    for _ in range(iters):
+        J, g = o.repair_objective(x0, vr, ctr)
+        Jr.append(J)
+        vr = np.clip(vr - float(np.float32(step)) * g, lo32, hi32)
+    Jr.append(o.repair_objective(x0, vr, ctr, grad=False))
+    c = bssmppi.Controller(p)
+    bssmppi.set_counter(c.h, ctr)
+    vt = torch.as_tensor(v, device="cuda").contiguous()
+    Jt = torch.empty(iters + 1, device="cuda")
+    bssmppi.repair(c.h, torch.as_tensor(x0, device="cuda"), vt, iters, step, Jt)
+    torch.cuda.synchronize()
+    c.close()
+    Jg = Jt.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(Jg, Jr, rtol=2e-3)
+    assert Jg[-1] < Jg[0]
+    dv = np.abs(vt.cpu().numpy() - vr)
+    assert np.all(dv <= 1e-5 + 2e-3 * np.abs(vr - v).max(axis=0)), dv.max(axis=0)
+    print(f"[repair] J over {iters} steps: GPU {np.round(Jg, 2).tolist()} oracle {np.round(Jr, 2).tolist()}")
+
+
+def test_repair_autograd_function():
+    p, x0, v = _case("racing")
+    c = bssmppi.Controller(p)
+    bssmppi.set_counter(c.h, 9)
+    x0t = torch.as_tensor(x0, device="cuda")
+    vt = torch.as_tensor(v, device="cuda").clone().requires_grad_(True)
+    J = bssmppi.repair_objective(vt, x0t, c.h)
+    (3.0 * J).backward()
+    _, g = _gpu_grad(c, x0, v)
+    c.close()
+    np.testing.assert_allclose(vt.grad.cpu().numpy(), 3.0 * g, rtol=1e-6, atol=1e-6)
+    assert J.requires_grad is True or J.grad_fn is not None
