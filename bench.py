@@ -180,6 +180,86 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+SERVE_BATCH_WORK = 40_000_000  # particle-steps per batch: about 2 ms of GPU time
+
+
+def _serve_stream(bssmppi, n_ctrl, rate_hz, duration_s, seed, batched, probs_params):
+    """Replay a Poisson arrival stream against a server; returns latency/throughput statistics."""
+    reqs = workload.serving_requests(n_ctrl=n_ctrl, rate_hz=rate_hz, duration_s=duration_s, seed=seed)
+    if batched:
+        s = bssmppi.server_create(n_ctrl, max_batch=512, T_max=60, slots=2, use_graphs=True,
+                                  hbm_budget_bytes=2 << 30, max_batch_work=SERVE_BATCH_WORK)
+    else:
+        s = bssmppi.server_create(n_ctrl, max_batch=1, T_max=60, slots=1, use_graphs=False,
+                                  hbm_budget_bytes=2 << 30)
+    try:
+        for prm in probs_params:
+            bssmppi.server_add_controller(s, prm)
+        x0 = np.array([10.0, 0.0, 0.0, 0.0, 0.0, 5.0], np.float32)
+        t0 = time.perf_counter()
+        for j, (ta, c, K, M, T) in enumerate(reqs):
+            while time.perf_counter() - t0 < ta:
+                pass
+            bssmppi.server_submit(s, c, x0, K, M, T, req_id=j)
+        t_sub = time.perf_counter() - t0
+        bssmppi.server_drain(s, 600000)
+        t_all = time.perf_counter() - t0
+        res = bssmppi.server_poll(s, max_n=len(reqs) + 16)
+        stats = bssmppi.server_get_stats(s)
+    finally:
+        bssmppi.server_destroy(s)
+    ok = [r for r in res if r.status == 0]
+    lat = np.array([r.t_done_us - r.t_submit_us for r in ok]) * 1e-3
+    cls = np.array([r.t_done_us - r.t_submit_us for r in ok if (r.K, r.M, r.T) == (4096, 64, 40)]) * 1e-3
+    work = sum(r.K * r.M * r.T for r in ok)
+    span = (max(r.t_done_us for r in ok) - min(r.t_submit_us for r in res)) * 1e-6 if ok else float("nan")
+    pct = lambda a, q: float(np.percentile(a, q)) if a.size else None
+    return {"offered_req_per_s": len(reqs) / duration_s, "submitted": stats["submitted"],
+            "completed": len(ok), "replaced_by_newer": stats["superseded"], "batches": stats["batches"],
+            "max_batch": stats["max_batch_seen"], "solves_per_s": len(ok) / span,
+            "particle_steps_per_s": work / span, "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
+            "class_4096_64_40_latency_ms_p50": pct(cls, 50), "class_4096_64_40_latency_ms_p99": pct(cls, 99),
+            "class_4096_64_40_completed": int(cls.size), "submit_window_s": t_sub, "wall_s": t_all}
+
+
+def run_serving(args):
+    """Serving: 512 controllers on independent tracks, Poisson arrivals at 20 Hz each, (K, M, T)
+    drawn from {512, 2048, 4096, 8192} x {8, 32, 64, 128} x {20, 40, 60}; the batched server against
+    the one-solve-at-a-time path on the same arrival stream, and a rate sweep."""
+    from paper_2408_00494_gb300 import bssmppi
+
+    n_ctrl = 512
+    params = []
+    for i in range(n_ctrl):
+        kappa, length = workload.make_track(1000 + i, n_theta=1 << 12)
+        p = workload.racing_problem(256, 16, 20, track_seed=0, noise_scale=2.0, seed=10_000 + i)
+        p.kappa, p.track_len = kappa, length
+        params.append(bssmppi.make_params(p))
+    out = {"controllers": n_ctrl, "rate_hz_per_controller": 20.0, "duration_s": args.serve_seconds,
+           "policy": "latest state wins: a newer request of a controller replaces its pending one"}
+    out["batch_work_limit_particle_steps"] = SERVE_BATCH_WORK
+    out["batched"] = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, True, params)
+    out["plain"] = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, False, params)
+    # rate sweep of both paths on the same arrival streams: the highest sustained solves/s at which
+    # the K=4096, M=64, T=40 class keeps its p99 latency under 10 ms
+    for name, batched in (("batched", True), ("plain", False)):
+        sweep, best = [], None
+        for rate in (0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0):
+            r = _serve_stream(bssmppi, n_ctrl, rate, max(1.0, args.serve_seconds), 5, batched, params)
+            p99 = r["class_4096_64_40_latency_ms_p99"]
+            sweep.append({"rate_hz_per_controller": rate, "offered_req_per_s": r["offered_req_per_s"],
+                          "solves_per_s": r["solves_per_s"], "latency_ms_p99": r["latency_ms_p99"],
+                          "class_4096_64_40_latency_ms_p99": p99, "replaced_by_newer": r["replaced_by_newer"]})
+            if p99 is not None and p99 < 10.0 and r["replaced_by_newer"] <= 0.01 * r["completed"]:
+                best = {"rate_hz_per_controller": rate, "solves_per_s": r["solves_per_s"],
+                        "class_4096_64_40_latency_ms_p99": p99}
+            elif p99 is not None and p99 > 50.0:
+                break
+        out[f"rate_sweep_{name}"] = sweep
+        out[f"{name}_max_solves_per_s_with_p99_under_10ms"] = best
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -285,6 +365,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed_region": t_wall,
     }
+    if rank == 0 and world == 1 and not args.no_serving:
+        line["serving"] = run_serving(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(p, args.cpu_budget)
     return line
@@ -300,6 +382,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-samples", type=int, default=128)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--repair-iters", type=int, default=5)
     ap.add_argument("--repair-step", type=float, default=2e-6)
     args = ap.parse_args()

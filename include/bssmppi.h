@@ -204,6 +204,73 @@ int bssmppi_repair(bssmppi_t h, const float* d_x0, float* d_v, int32_t iters, fl
 int bssmppi_timing(bssmppi_t h, int32_t n);
 int bssmppi_timing_read(bssmppi_t h, float* h_rollout_ms, float* h_update_ms, int32_t max, int32_t* count);
 
+/* ------------------------------------------------------------------------------------------------
+ * Serving: many controllers, requests batched continuously.
+ *
+ * A server keeps every registered controller's problem, curvature table, warm-start nominal
+ * sequence (T_max x 2) and solve counter resident on the device. Each request is one solve of
+ * Algorithm 1 for one controller with its own K, M, T and state estimate; after it, the
+ * controller's nominal becomes v+ shifted by one step (the receding-horizon warm start) and its
+ * counter advances, exactly as bssmppi_solve followed by bssmppi_shift(h, NULL, 1) would leave them.
+ * A newer request of a controller replaces its older pending one (reported with status
+ * BSSMPPI_EBUSY). A scheduler thread admits requests in arrival order while the batch has room
+ * and the slot's share of hbm_budget_bytes holds their buffers (K*T*2 + 2K floats each); requests
+ * that arrive while a batch runs are admitted into the other slot and run beside it on the device.
+ * Batches run as captured CUDA graphs (use_graphs = 1) of persistent batched kernels. With
+ * max_batch = 1 and slots = 1 the server runs one solve at a time (the one-launch-per-solve path).
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct bssmppi_server* bssmppi_server_t;
+
+typedef struct bssmppi_server_config {
+    int32_t max_controllers;   /* controller table size, 1..65536 */
+    int32_t max_batch;         /* requests per batch, 1..4096 */
+    int32_t T_max;             /* largest horizon of any request, 1..BSSMPPI_T_MAX */
+    int32_t slots;             /* 1 or 2 batches in flight */
+    int32_t use_graphs;        /* 1: replay one captured CUDA graph per batch */
+    int32_t reserved;          /* must be 0 */
+    size_t hbm_budget_bytes;   /* device memory for the in-flight requests' buffers (split over slots) */
+    int64_t max_batch_work;    /* particle-steps (sum of K*M*T) per batch, 0 = no limit; a batch always
+                                  takes its oldest request, so the limit bounds batch duration */
+} bssmppi_server_config;
+
+typedef struct bssmppi_result {
+    uint64_t req_id;           /* the id given at submit */
+    int32_t ctrl_id;
+    int32_t status;            /* BSSMPPI_OK, or BSSMPPI_EBUSY: replaced by a newer request */
+    float u0[2];               /* first control of v+ (valid when status = OK) */
+    float beta;                /* minimum trajectory cost of the solve */
+    int32_t K, M, T;
+    double t_submit_us, t_start_us, t_done_us; /* server clock; t_start = batch launch (-1 if replaced) */
+} bssmppi_result;
+
+typedef struct bssmppi_server_stats {
+    int64_t submitted, superseded, admitted, completed, batches, max_batch_seen, queued;
+    double now_us;             /* server clock at the call */
+} bssmppi_server_stats;
+
+/* Create a server on the current device. Allocates the controller table, two slots' descriptors,
+ * results and HBM arenas, captures the batch graphs and starts the scheduler thread. */
+int bssmppi_server_create(const bssmppi_server_config* cfg, bssmppi_server_t* out);
+/* Register a controller (bicycle model, compensated; K, M, T of params are ignored: each request
+ * brings its own). Its nominal starts at zero and its counter at 0. *ctrl_id receives its index. */
+int bssmppi_server_add_controller(bssmppi_server_t s, const bssmppi_params* params, int32_t* ctrl_id);
+/* Queue a solve for controller ctrl_id from state h_x0 [6] (host; copied). 2 <= M <= 128,
+ * 1 <= T <= T_max. Thread-safe; returns immediately. */
+int bssmppi_server_submit(bssmppi_server_t s, int32_t ctrl_id, const float* h_x0, int32_t K, int32_t M, int32_t T,
+                          uint64_t req_id);
+/* Move up to max finished results (completed or replaced) into out; *n receives how many. */
+int bssmppi_server_poll(bssmppi_server_t s, bssmppi_result* out, int32_t max, int32_t* n);
+/* Wait until no request is queued or in flight (ETIMEOUT after timeout_ms). */
+int bssmppi_server_drain(bssmppi_server_t s, int32_t timeout_ms);
+/* Read or overwrite a controller's resident nominal (h_v [T_max*2], host) and counter; EBUSY while
+ * the controller has work queued or in flight. Synchronous. */
+int bssmppi_server_get_state(bssmppi_server_t s, int32_t ctrl_id, float* h_v, uint32_t* counter);
+int bssmppi_server_set_state(bssmppi_server_t s, int32_t ctrl_id, const float* h_v, uint32_t counter);
+int bssmppi_server_get_stats(bssmppi_server_t s, bssmppi_server_stats* out);
+const char* bssmppi_server_last_error(bssmppi_server_t s);
+/* Stop the scheduler, wait for the device and free everything. NULL is accepted. */
+int bssmppi_server_destroy(bssmppi_server_t s);
+
 /*
  * Weights and update (the same computation as the second half of bssmppi_solve) for callers that
  * cannot allocate device memory. Some callers cannot call cudaMalloc once they run: hard real-time

@@ -48,6 +48,24 @@ class Params(ctypes.Structure):
     ]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_controllers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("T_max", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("max_batch_work", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("ctrl_id", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("u0", ctypes.c_float * 2), ("beta", ctypes.c_float), ("K", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("T", ctypes.c_int32), ("t_submit_us", ctypes.c_double), ("t_start_us", ctypes.c_double),
+                ("t_done_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "superseded", "admitted", "completed", "batches",
+                                               "max_batch_seen", "queued")] + [("now_us", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -80,6 +98,16 @@ def load(build_if_missing: bool = True):
         "bssmppi_timing": (ctypes.c_int, [vp, i32]),
         "bssmppi_timing_read": (ctypes.c_int, [vp, vp, vp, i32, ctypes.POINTER(i32)]),
         "bssmppi_update_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, i32, vp]),
+        "bssmppi_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+        "bssmppi_server_add_controller": (ctypes.c_int, [vp, ctypes.POINTER(Params), ctypes.POINTER(i32)]),
+        "bssmppi_server_submit": (ctypes.c_int, [vp, i32, vp, i32, i32, i32, u64]),
+        "bssmppi_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(Result), i32, ctypes.POINTER(i32)]),
+        "bssmppi_server_drain": (ctypes.c_int, [vp, i32]),
+        "bssmppi_server_get_state": (ctypes.c_int, [vp, i32, vp, ctypes.POINTER(u32)]),
+        "bssmppi_server_set_state": (ctypes.c_int, [vp, i32, vp, u32]),
+        "bssmppi_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+        "bssmppi_server_last_error": (ctypes.c_char_p, [vp]),
+        "bssmppi_server_destroy": (ctypes.c_int, [vp]),
         "bssmppi_repair_grad": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "bssmppi_repair": (ctypes.c_int, [vp, vp, vp, i32, ctypes.c_float, vp]),
         "bssmppi_model_step": (ctypes.c_int, [vp, vp, vp, vp, i64]),
@@ -326,3 +354,65 @@ class Controller:
         out = torch.empty(shape, dtype=torch.float32, device="cuda")
         read(self.h, which, out)
         return out
+
+
+# ---- serving ----------------------------------------------------------------------------------
+
+def _srv_check(rc, s):
+    if rc != 0:
+        msg = load().bssmppi_server_last_error(s)
+        raise BssmppiError(rc, msg.decode() if msg else "")
+
+
+def server_create(max_controllers, max_batch=256, T_max=60, slots=2, use_graphs=True, hbm_budget_bytes=1 << 30,
+                  max_batch_work=0):
+    cfg = ServerConfig(int(max_controllers), int(max_batch), int(T_max), int(slots), int(bool(use_graphs)), 0,
+                       int(hbm_budget_bytes), int(max_batch_work))
+    s = ctypes.c_void_p()
+    _srv_check(load().bssmppi_server_create(ctypes.byref(cfg), ctypes.byref(s)), None)
+    return s
+
+
+def server_add_controller(s, params: Params) -> int:
+    cid = ctypes.c_int32()
+    _srv_check(load().bssmppi_server_add_controller(s, ctypes.byref(params), ctypes.byref(cid)), s)
+    return cid.value
+
+
+def server_submit(s, ctrl_id, x0, K, M, T, req_id):
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float32).reshape(-1)[:6])
+    _srv_check(load().bssmppi_server_submit(s, int(ctrl_id), ctypes.c_void_p(x.ctypes.data), int(K), int(M), int(T),
+                                            ctypes.c_uint64(req_id)), s)
+
+
+def server_poll(s, max_n=4096):
+    buf = (Result * max_n)()
+    n = ctypes.c_int32()
+    _srv_check(load().bssmppi_server_poll(s, buf, int(max_n), ctypes.byref(n)), s)
+    return [buf[i] for i in range(n.value)]
+
+
+def server_drain(s, timeout_ms=60000):
+    _srv_check(load().bssmppi_server_drain(s, int(timeout_ms)), s)
+
+
+def server_get_state(s, ctrl_id, T_max):
+    v = np.zeros((T_max, 2), np.float32)
+    c = ctypes.c_uint32()
+    _srv_check(load().bssmppi_server_get_state(s, int(ctrl_id), ctypes.c_void_p(v.ctypes.data), ctypes.byref(c)), s)
+    return v, c.value
+
+
+def server_set_state(s, ctrl_id, v, counter):
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    _srv_check(load().bssmppi_server_set_state(s, int(ctrl_id), ctypes.c_void_p(v.ctypes.data), int(counter)), s)
+
+
+def server_get_stats(s) -> dict:
+    st = ServerStats()
+    _srv_check(load().bssmppi_server_get_stats(s, ctypes.byref(st)), s)
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def server_destroy(s):
+    _srv_check(load().bssmppi_server_destroy(s), None)

@@ -55,3 +55,14 @@ cudaError_t repair_launch(const DevParams& dp, const float* x0, float* v, const 
 void set_thread_error(const char* msg);
 
 }  // namespace bss
+
+struct bssmppi_params;
+#include <string>
+
+namespace bss {
+
+// Validates a problem and derives the kernels' constants (d) and particles per lane (P); returns
+// BSSMPPI_OK or BSSMPPI_EINVAL with the reason in `why`.
+int derive_params(const bssmppi_params* p, DevParams& d, int& P, std::string& why);
+
+}  // namespace bss

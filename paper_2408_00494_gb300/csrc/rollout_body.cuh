@@ -1,0 +1,308 @@
+// Body of the fused belief rollout for one group of control samples, shared by the per-solve kernel
+// (rollout.cu) and the batched serving kernels (serve.cu).
+//
+// Fused belief rollout: for every control sample, draw its perturbed control sequence, roll its M
+// disturbance particles through the model for T steps, reduce the particle mean and variance of
+// every step across the lanes that hold them, and accumulate the augmented trajectory cost.
+//
+// Mapping: a segment of `seg` lanes (seg = min(32, next power of two >= M)) owns one control
+// sample; lane l of the segment holds particles l, l + seg, ..., l + (P-1) seg in registers.
+// Particle states never touch memory. Per step, the moments are merged across the segment by a
+// shuffle butterfly (Chan's parallel merge of counts, means and M2 when compensated), so every
+// lane ends with the same belief and computes the cost redundantly; lane 0 writes the result.
+#pragma once
+
+#include "device.cuh"
+
+namespace bss {
+
+struct RollIO {
+    const float* x0;
+    const float* Sigma0;
+    const float* v;
+    const uint32_t* ctr;
+    float* S;
+    float* eps;
+    float* mean;
+    float* var;
+};
+
+// Moments of the M particles of one sample. x[p] is particle ls + seg p (valid iff < M).
+// mean[i] = particle mean, var[i] = unbiased variance 1/(M-1) sum (x - mean)^2 (Algorithm 2);
+// var is produced for EY only unless all_var. Means outside dp.mean_mask (states no cost term
+// weights) are not merged across lanes and are left lane-local.
+template <int NX, int EY, int P, bool COMP>
+__device__ __forceinline__ void belief_moments(const DevParams& dp, const float (&x)[P][NX], int ls, int seg,
+                                               bool all_var, float (&mean)[NX], float (&var)[NX])
+{
+    if constexpr (COMP) {
+        // Per lane: exact two-pass mean and M2 over its (at most P) particles.
+        float cnt = 0.0f;
+        if (dp.uniform) {
+            cnt = (float)P;
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) cnt += (ls + seg * p < dp.M) ? 1.0f : 0.0f;
+        }
+        const float inv_cnt = dp.uniform ? (1.0f / (float)P) : (cnt > 0.0f ? 1.0f / cnt : 0.0f);
+        float m2[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            float s = 0.0f;
+#pragma unroll
+            for (int p = 0; p < P; ++p) s += (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
+            mean[i] = s * inv_cnt;
+            float q = 0.0f;
+            if (i == EY || all_var) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float d = x[p][i] - mean[i];
+                    q += (dp.uniform || ls + seg * p < dp.M) ? d * d : 0.0f;
+                }
+            }
+            m2[i] = q;
+        }
+        // Chan et al. pairwise merge across the segment; the formulas are symmetric in the two
+        // partners, so both ends of every exchange compute bit-identical results.
+        if (dp.uniform) {
+            for (int off = seg >> 1; off > 0; off >>= 1) {
+                const float half_n = 0.5f * cnt;
+#pragma unroll
+                for (int i = 0; i < NX; ++i) {
+                    if (!((dp.mean_mask >> i) & 1)) continue;  // a mean no cost term reads
+                    const float mb = __shfl_xor_sync(0xffffffffu, mean[i], off);
+                    if (i == EY || all_var) {
+                        const float d = mb - mean[i];
+                        const float m2b = __shfl_xor_sync(0xffffffffu, m2[i], off);
+                        m2[i] = (m2[i] + m2b) + d * d * half_n;
+                    }
+                    mean[i] = 0.5f * (mean[i] + mb);
+                }
+                cnt *= 2.0f;
+            }
+        } else {
+            for (int off = seg >> 1; off > 0; off >>= 1) {
+                const float cb = __shfl_xor_sync(0xffffffffu, cnt, off);
+                const float n = cnt + cb;
+                const float inv = n > 0.0f ? 1.0f / n : 0.0f;
+                const float fa = cnt * inv, fb = cb * inv, fab = cnt * cb * inv;
+#pragma unroll
+                for (int i = 0; i < NX; ++i) {
+                    if (!((dp.mean_mask >> i) & 1)) continue;
+                    const float mb = __shfl_xor_sync(0xffffffffu, mean[i], off);
+                    if (i == EY || all_var) {
+                        const float d = mb - mean[i];
+                        const float m2b = __shfl_xor_sync(0xffffffffu, m2[i], off);
+                        m2[i] = (m2[i] + m2b) + d * d * fab;
+                    }
+                    mean[i] = __fadd_rn(__fmul_rn(fa, mean[i]), __fmul_rn(fb, mb));
+                }
+                cnt = n;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) var[i] = m2[i] * dp.invM1;
+    } else {
+        // Naive one-pass sums: mean = sum x / M, var = (sum x^2 - M mean^2) / (M - 1).
+        float s[NX], q[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            s[i] = 0.0f;
+            q[i] = 0.0f;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float xv = (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
+                s[i] += xv;
+                if (i == EY || all_var) q[i] += xv * xv;
+            }
+        }
+        for (int off = seg >> 1; off > 0; off >>= 1) {
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                if (!((dp.mean_mask >> i) & 1)) continue;
+                s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
+                if (i == EY || all_var) q[i] += __shfl_xor_sync(0xffffffffu, q[i], off);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            mean[i] = s[i] * dp.invM;
+            var[i] = (q[i] - dp.Mf * mean[i] * mean[i]) * dp.invM1;
+        }
+    }
+}
+
+// PSD-tolerant Cholesky factor (lower, row-major) of the caller's initial covariance.
+template <int NX>
+__device__ __forceinline__ void cholesky_psd(const float* A, float (&L)[NX][NX])
+{
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+        for (int j = 0; j < NX; ++j) L[i][j] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+        float d = A[j * NX + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (d > 1e-30f) {
+            const float ljj = sqrtf(d);
+            L[j][j] = ljj;
+#pragma unroll
+            for (int i = j + 1; i < NX; ++i) {
+                float s = A[i * NX + j];
+#pragma unroll
+                for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+                L[i][j] = s / ljj;
+            }
+        }
+    }
+}
+
+// Largest block each particle count is compiled for (bounds the registers ptxas may use).
+template <int P>
+constexpr int roll_max_threads()
+{
+    return P <= 2 ? 1024 : (P == 4 ? 768 : 512);
+}
+
+// One sample group (the spw samples of one warp): control sequence, rollout, moments, cost.
+template <int MODEL, int P, bool COMP>
+__device__ __forceinline__ void rollout_group(const DevParams& dp, const RollIO& io, const float* __restrict__ kap_s,
+                                              const float* __restrict__ v_s, float* __restrict__ my_u, int group,
+                                              uint32_t ctr)
+{
+    constexpr int NX = MODEL == 0 ? 6 : 4;
+    constexpr int EY = MODEL == 0 ? 4 : 1;
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int seg = dp.seg;
+    const int ls = lane & (seg - 1);
+    const int k = group * dp.spw + lane / seg;
+    const bool active = k < dp.K;
+    const int kc = active ? k : dp.K - 1;  // inactive segments shadow a valid sample, write nothing
+    const uint32_t kk = dp.crn ? 0u : (uint32_t)kc;
+
+    // (a1, a2) control noise eps ~ N(0, Sigma_eps) and clamped samples u = clamp(v + eps); the
+    // lanes of the segment split the horizon. eps_eff = u - v feeds the update.
+    for (int t = ls; t < dp.T; t += seg) {
+        const uint4 w = draw_words(dp, (uint32_t)t, 0u, 0u, (uint32_t)kc, kStreamControl, ctr);
+        const float2 z = box_muller(w.x, w.y);
+        const float e0 = dp.Le00 * z.x;
+        const float e1 = fmaf(dp.Le10, z.x, dp.Le11 * z.y);
+        const float v0 = v_s[2 * t], v1 = v_s[2 * t + 1];
+        const float u0 = fminf(fmaxf(v0 + e0, dp.umin0), dp.umax0);
+        const float u1 = fminf(fmaxf(v1 + e1, dp.umin1), dp.umax1);
+        my_u[2 * t] = u0;
+        my_u[2 * t + 1] = u1;
+        if (active) reinterpret_cast<float2*>(io.eps)[(size_t)k * dp.T + t] = make_float2(u0 - v0, u1 - v1);
+    }
+    __syncwarp();
+
+    // Initial particles: the estimate x_bar_0, spread by Sigma_{x_0} when one is given.
+    float x0[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) x0[i] = io.x0[i];
+    const float s0 = (MODEL == 0) ? x0[5] : 0.0f;
+    float x[P][NX];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int i = 0; i < NX; ++i) x[p][i] = (MODEL == 0 && i == 5) ? 0.0f : x0[i];
+    float var0_ey = 0.0f;
+    float var0[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) var0[i] = 0.0f;
+    if (io.Sigma0 != nullptr) {
+        float L0[NX][NX];
+        cholesky_psd<NX>(io.Sigma0, L0);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) var0[i] = io.Sigma0[i * NX + i];
+        var0_ey = var0[EY];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            float xi[NX];
+            draw_normals<NX>(dp, 0u, (uint32_t)(ls + seg * p), kk, kStreamInitial, ctr, xi);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                float w = 0.0f;
+#pragma unroll
+                for (int j = 0; j <= i; ++j) w = fmaf(L0[i][j], xi[j], w);
+                x[p][i] += w;
+            }
+        }
+    }
+
+    // Belief z_0 = (z_hat_0, z_hat_{-1} = z_hat_0) from the given estimate (Algorithm 1).
+    float mean[NX], var[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mean[i] = x0[i];
+    float h_cur = belief_barrier(dp, mean[EY], var0_ey);
+    float h_prev = h_cur;
+    const bool writer = active && ls == 0;
+    if (dp.record && writer) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            io.mean[(size_t)k * (dp.T + 1) * NX + i] = mean[i];
+            io.var[(size_t)k * (dp.T + 1) * NX + i] = var0[i];
+        }
+    }
+
+    CompSum S;
+    float S_naive = 0.0f;
+    for (int t = 0; t < dp.T; ++t) {
+        // (a7) S += q(x_bar_t) + ctrl_w v_t^T Sigma_eps^-1 u_t + C_safe(z_t)
+        const float u0 = my_u[2 * t], u1 = my_u[2 * t + 1];
+        const float v0 = v_s[2 * t], v1 = v_s[2 * t + 1];
+        const float ctrl = dp.ctrl_w * (v0 * fmaf(dp.Si00, u0, dp.Si01 * u1) + v1 * fmaf(dp.Si10, u0, dp.Si11 * u1));
+        const float csafe = dp.Csafe * fmaxf(fmaf(dp.one_m_gamma, h_prev, -h_cur), 0.0f);
+        const float term = state_cost<NX>(dp, dp.Q, mean) + ctrl + csafe;
+        if constexpr (COMP) S.add(term); else S_naive += term;
+
+        // (a3, a4) propagate every particle: x <- f(x, u_t) + L_w z.
+        Control c;
+        c.steer = u0;
+        c.accel = u1;
+        if constexpr (MODEL == 0) sincosf(u0, &c.sin_steer, &c.cos_steer);
+        if constexpr (MODEL == 0) {
+            for (int j = 0; j < dp.n_sub; ++j) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) bicycle_substep(dp, kap_s, s0, c, x[p]);
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) double_integrator_step(dp, c, x[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            float z[NX];
+            draw_normals<NX>(dp, (uint32_t)t, (uint32_t)(ls + seg * p), kk, kStreamDisturbance, ctr, z);
+            add_correlated<NX>(dp.Lw, z, x[p]);
+        }
+
+        // (a5) belief moments of step t+1, (a6) barrier.
+        belief_moments<NX, EY, P, COMP>(dp, x, ls, seg, dp.record != 0, mean, var);
+        if constexpr (MODEL == 0) mean[5] += s0;
+        h_prev = h_cur;
+        h_cur = belief_barrier(dp, mean[EY], var[EY]);
+        if (dp.record && writer) {
+            const size_t base = ((size_t)k * (dp.T + 1) + t + 1) * NX;
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                io.mean[base + i] = mean[i];
+                io.var[base + i] = var[i];
+            }
+        }
+    }
+    // Terminal: phi(x_bar_T) + C_safe(z_T).
+    const float term = state_cost<NX>(dp, dp.Qf, mean) + dp.Csafe * fmaxf(fmaf(dp.one_m_gamma, h_prev, -h_cur), 0.0f);
+    float total;
+    if constexpr (COMP) {
+        S.add(term);
+        total = S.value();
+    } else {
+        total = S_naive + term;
+    }
+    if (writer) io.S[k] = total;
+}
+
+}  // namespace bss

@@ -176,50 +176,32 @@ void release(bssmppi_ctx* h)
 
 void bss::set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
-extern "C" {
-
-uint32_t bssmppi_abi_version(void) { return BSSMPPI_ABI_VERSION; }
-size_t bssmppi_params_size(void) { return sizeof(bssmppi_params); }
-
-const char* bssmppi_last_error(bssmppi_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
-
-int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
+// Validates the parameters and derives the kernels' constants: lane mapping (seg, spw, P),
+// Cholesky factors, Sigma_eps^-1, the back-off nu, the Philox round keys and the model constants.
+int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::string& why)
 {
-    if (!out) return fail(nullptr, BSSMPPI_EINVAL, "out is NULL");
-    *out = nullptr;
-    std::string why;
     int rc = validate(p, why);
-    if (rc != BSSMPPI_OK) return fail(nullptr, rc, why);
-
+    if (rc != BSSMPPI_OK) return rc;
     const int nx = p->model == BSSMPPI_MODEL_BICYCLE6 ? 6 : 4;
     double Lw[36], Le[4];
-    if (!cholesky_psd(nx, p->Sigma_w, Lw)) return fail(nullptr, BSSMPPI_EINVAL, "Sigma_w must be symmetric positive semidefinite");
-    if (!cholesky_psd(2, p->Sigma_eps, Le)) return fail(nullptr, BSSMPPI_EINVAL, "Sigma_eps must be symmetric positive definite");
-
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(nullptr, BSSMPPI_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
-
-    auto* h = new bssmppi_ctx();
-    h->prm = *p;
-    h->prm.track_kappa = nullptr;
-    h->nx = nx;
-    h->device = dev;
-    h->stream = static_cast<cudaStream_t>(cuda_stream);
-
+    if (!cholesky_psd(nx, p->Sigma_w, Lw)) {
+        why = "Sigma_w must be symmetric positive semidefinite";
+        return BSSMPPI_EINVAL;
+    }
+    if (!cholesky_psd(2, p->Sigma_eps, Le)) {
+        why = "Sigma_eps must be symmetric positive definite";
+        return BSSMPPI_EINVAL;
+    }
     // Mapping of particles to lanes.
     int seg = 1;
     while (seg < p->M && seg < 32) seg <<= 1;
-    int ppl = (p->M + seg - 1) / seg;
-    int P = 1;
+    const int ppl = (p->M + seg - 1) / seg;
+    P = 1;
     while (P < ppl) P <<= 1;
-    h->P = P;
-
-    bss::DevParams& d = h->dp;
     d.K = p->K; d.M = p->M; d.T = p->T; d.nx = nx;
-    d.n_sub = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_sub : 1;
     d.seg = seg; d.spw = 32 / seg;
     d.uniform = (p->M == seg * P) ? 1 : 0;
+    d.n_sub = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_sub : 1;
     d.ey = p->ey_index; d.crn = p->crn_disturbance ? 1 : 0; d.record = p->record_moments ? 1 : 0;
     d.key0 = (uint32_t)(p->seed & 0xffffffffu); d.key1 = (uint32_t)(p->seed >> 32);
     for (int r = 0; r < 10; ++r) {  // Philox key schedule: k + r (0x9E3779B9, 0xBB67AE85)
@@ -256,6 +238,40 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     d.n_track_mask = ntab - 1;
     d.track_scale = p->model == BSSMPPI_MODEL_BICYCLE6 ? (float)((double)ntab / p->track_len) : 0.0f;
     d.Mf = (float)p->M; d.invM = 1.0f / (float)p->M; d.invM1 = 1.0f / (float)(p->M - 1);
+    return BSSMPPI_OK;
+}
+
+extern "C" {
+
+uint32_t bssmppi_abi_version(void) { return BSSMPPI_ABI_VERSION; }
+size_t bssmppi_params_size(void) { return sizeof(bssmppi_params); }
+
+const char* bssmppi_last_error(bssmppi_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
+{
+    if (!out) return fail(nullptr, BSSMPPI_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    bss::DevParams dp{};
+    int P = 1;
+    int rc = bss::derive_params(p, dp, P, why);
+    if (rc != BSSMPPI_OK) return fail(nullptr, rc, why);
+    const int nx = dp.nx;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, BSSMPPI_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+
+    auto* h = new bssmppi_ctx();
+    h->prm = *p;
+    h->prm.track_kappa = nullptr;
+    h->nx = nx;
+    h->device = dev;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->P = P;
+    h->dp = dp;
+    const int ntab = dp.n_track_mask + 1;
 
     const size_t K = p->K, T = p->T;
     const int G = bss::update_blocks(p->K);

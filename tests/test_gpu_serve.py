@@ -1,0 +1,171 @@
+"""Continuous-batching server: results must not depend on the batch they run in.
+
+A request's result is a deterministic function of its controller's state (nominal, counter), its
+state estimate and its (K, M, T): alone or in a mix of other controllers' requests, with or without
+CUDA graphs, it must come out bit for bit the same, and equal to bssmppi_solve + bssmppi_shift on
+a single handle within the update tolerance (rel 1e-4 / abs 1e-5; the two update kernels add the
+weighted perturbations in different orders).
+"""
+import time
+
+import numpy as np
+import pytest
+
+import workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2408_00494_gb300 import bssmppi  # noqa: E402
+
+T_MAX = 60
+
+
+def _problem(i):
+    kappa, length = workload.make_track(1000 + i, n_theta=1 << 13)
+    p = workload.racing_problem(256, 16, 20, track_seed=0, noise_scale=2.0, seed=i)
+    p.kappa, p.track_len = kappa, length
+    return p
+
+
+def _server(n_ctrl, **kw):
+    s = bssmppi.server_create(n_ctrl, T_max=T_MAX, **kw)
+    probs = [_problem(i) for i in range(n_ctrl)]
+    for p in probs:
+        bssmppi.server_add_controller(s, bssmppi.make_params(p))
+    return s, probs
+
+
+def _v0(i):
+    v = np.zeros((T_MAX, 2), np.float32)
+    v[:, 0] = 0.04 + 0.002 * i
+    v[:, 1] = 0.1 * np.sin(np.arange(T_MAX) * 0.2 + i)
+    return v
+
+
+MIX = [(512, 8, 20), (2048, 32, 40), (4096, 64, 40), (1024, 128, 60), (700, 64, 20), (333, 8, 60),
+       (4096, 32, 60), (8192, 64, 40), (1500, 128, 20), (64, 8, 40)]
+
+
+def _x0(i):
+    return np.array([9.0 + 0.1 * i, 0.05, 0.01, 0.02 * ((i % 5) - 2), 0.3 * ((i % 7) - 3), 3.0 * i], np.float32)
+
+
+def _run(s, requests, ctr0=5):
+    """requests: list of (ctrl, K, M, T). Resets the controllers, submits all, drains, returns
+    {ctrl: (u0, v_after, counter_after)}."""
+    for c, *_ in requests:
+        bssmppi.server_set_state(s, c, _v0(c), ctr0)
+    for j, (c, K, M, T) in enumerate(requests):
+        bssmppi.server_submit(s, c, _x0(c), K, M, T, req_id=1000 * c + j)
+    bssmppi.server_drain(s, 60000)
+    res = {r.ctrl_id: r for r in bssmppi.server_poll(s)}
+    out = {}
+    for c, *_ in requests:
+        assert res[c].status == 0
+        v, ctr = bssmppi.server_get_state(s, c, T_MAX)
+        out[c] = (np.array(res[c].u0), v, ctr)
+    return out
+
+
+def test_result_alone_equals_in_mix_and_without_graphs():
+    s, _ = _server(len(MIX))
+    try:
+        mix = [(c, K, M, T) for c, (K, M, T) in enumerate(MIX)]
+        together = _run(s, mix)
+        for c, K, M, T in mix[:4] + mix[-2:]:
+            alone = _run(s, [(c, K, M, T)])
+            assert np.array_equal(alone[c][0], together[c][0]), c
+            assert np.array_equal(alone[c][1], together[c][1]), c
+            assert alone[c][2] == together[c][2] == 6
+        st = bssmppi.server_get_stats(s)
+        assert st["superseded"] == 0 and st["completed"] == st["submitted"]
+    finally:
+        bssmppi.server_destroy(s)
+    s2, _ = _server(len(MIX), use_graphs=False, slots=1)
+    try:
+        eager = _run(s2, [(c, K, M, T) for c, (K, M, T) in enumerate(MIX)])
+        for c in eager:
+            assert np.array_equal(eager[c][0], together[c][0]) and np.array_equal(eager[c][1], together[c][1])
+    finally:
+        bssmppi.server_destroy(s2)
+
+
+@pytest.mark.parametrize("K,M,T", [(4096, 64, 40), (512, 8, 20), (1024, 128, 60), (700, 33, 20)])
+def test_server_matches_single_solve(K, M, T):
+    s, probs = _server(3)
+    try:
+        got = _run(s, [(2, K, M, T)])[2]
+    finally:
+        bssmppi.server_destroy(s)
+    p = probs[2]
+    p.K, p.M, p.T = K, M, T
+    c = bssmppi.Controller(p)
+    bssmppi.set_counter(c.h, 5)
+    v = torch.as_tensor(_v0(2)[:T], device="cuda").contiguous()
+    u0 = torch.zeros(2, device="cuda")
+    bssmppi.solve(c.h, torch.as_tensor(_x0(2), device="cuda"), None, v, u0)
+    bssmppi.shift(c.h, v, 1)
+    torch.cuda.synchronize()
+    ctr = bssmppi.get_counter(c.h)
+    c.close()
+    ref_u0, ref_v = u0.cpu().numpy(), v.cpu().numpy()
+    assert np.all(np.abs(got[0] - ref_u0) <= 1e-5 + 1e-4 * np.abs(ref_u0))
+    assert np.all(np.abs(got[1][:T] - ref_v) <= 1e-5 + 1e-4 * np.abs(ref_v))
+    assert got[2] == ctr == 6
+
+
+def test_newer_request_replaces_pending_one_and_every_request_gets_a_result():
+    s, _ = _server(2, max_batch=1, slots=1)
+    try:
+        for c in range(2):
+            bssmppi.server_set_state(s, c, _v0(c), 0)
+        ids = []
+        for j in range(6):  # a burst for controller 0: the first runs, later ones replace each other
+            bssmppi.server_submit(s, 0, _x0(0), 8192, 128, 60, req_id=j)
+            ids.append(j)
+        bssmppi.server_submit(s, 1, _x0(1), 256, 16, 20, req_id=99)
+        bssmppi.server_drain(s, 60000)
+        res = bssmppi.server_poll(s)
+        got = sorted(r.req_id for r in res)
+        assert got == sorted(ids + [99])
+        ok = [r for r in res if r.status == 0]
+        replaced = [r for r in res if r.status != 0]
+        assert len(ok) >= 2 and len(replaced) >= 1
+        assert all(r.status == -5 for r in replaced)  # BSSMPPI_EBUSY
+        assert max(r.req_id for r in ok if r.ctrl_id == 0) == 5  # the newest always runs
+        _, ctr0 = bssmppi.server_get_state(s, 0, T_MAX)
+        assert ctr0 == len([r for r in ok if r.ctrl_id == 0])
+        for r in ok:
+            assert r.t_submit_us <= r.t_start_us <= r.t_done_us
+    finally:
+        bssmppi.server_destroy(s)
+
+
+def test_admission_respects_hbm_budget():
+    # 4 MiB per slot holds 3 requests of K=4096, T=40 (1.31 MB of perturbations + costs each)
+    s, _ = _server(12, hbm_budget_bytes=8 << 20)
+    try:
+        for c in range(12):
+            bssmppi.server_set_state(s, c, _v0(c), 0)
+        for c in range(12):
+            bssmppi.server_submit(s, c, _x0(c), 4096, 64, 40, req_id=c)
+        bssmppi.server_drain(s, 60000)
+        res = bssmppi.server_poll(s)
+        assert sorted(r.req_id for r in res if r.status == 0) == list(range(12))
+        st = bssmppi.server_get_stats(s)
+        assert 1 <= st["max_batch_seen"] <= 3 and st["batches"] >= 4
+    finally:
+        bssmppi.server_destroy(s)
+
+
+def test_server_rejects_bad_requests():
+    s, _ = _server(1, hbm_budget_bytes=2 << 20)
+    try:
+        x0 = _x0(0)
+        for args in ((0, x0, 256, 256, 20), (0, x0, 256, 16, 61), (3, x0, 256, 16, 20), (0, x0, 0, 16, 20),
+                     (0, x0, 1 << 17, 64, 60)):
+            with pytest.raises(bssmppi.BssmppiError):
+                bssmppi.server_submit(s, *args, req_id=1)
+    finally:
+        bssmppi.server_destroy(s)
