@@ -260,6 +260,67 @@ def run_serving(args):
     return out
 
 
+def run_closed_loop(bssmppi, p, dev, stream, steps: int, seed: int = 1):
+    """Closed loop: every step solves from the plant state, applies u0 to the plant (the same model,
+    stepped on the device, plus a seeded disturbance drawn with Sigma_w) and shifts the nominal.
+    Reports the constraint-violation rate (|e_y| > w_T), the near-violation rate (|e_y| > 0.9 w_T),
+    the fraction of steps satisfying the DCBF condition h_{k+1} >= (1 - gamma) h_k with
+    h = w_T^2 - e_y^2 on the executed states, and the time per closed-loop step."""
+    import torch
+
+    ctl = bssmppi.Controller(p, stream=stream)
+    try:
+        u0 = torch.zeros(1, 2, device=dev)
+        rng = np.random.default_rng(seed)
+        std = np.sqrt(np.diag(np.asarray(p.Sigma_w)))
+        W = torch.as_tensor((rng.standard_normal((steps, 6)) * std).astype(np.float32), device=dev)
+        traj = torch.empty(steps + 1, 6, device=dev)
+        traj[0] = torch.as_tensor(workload.racing_x0(p), device=dev)
+        bssmppi.timing(ctl.h, min(steps, 4096))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):  # only library calls inside the loop
+            bssmppi.solve(ctl.h, traj[k], None, None, u0[0])
+            bssmppi.model_step(ctl.h, traj[k:k + 1], u0, traj[k + 1:k + 2], W[k:k + 1])
+            bssmppi.shift(ctl.h, None, 1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        roll_ms, upd_ms = bssmppi.timing_read(ctl.h, min(steps, 4096))
+        bssmppi.timing(ctl.h, 0)
+        ey = traj[:, 4].double().cpu().numpy()
+        s = traj[:, 5].double().cpu().numpy()
+        vx = traj[:, 0].double().cpu().numpy()
+    finally:
+        ctl.close()
+    wT, g = float(p.w_T), float(p.gamma)
+    h = wT * wT - ey * ey
+    return {"steps": steps, "ms_per_step": dt * 1e3 / steps,
+            "rollout_ms_mean": float(np.mean(roll_ms)), "rollout_ms_max": float(np.max(roll_ms)),
+            "update_ms_mean": float(np.mean(upd_ms)),
+            "violation_rate": float(np.mean(np.abs(ey[1:]) > wT)),
+            "near_violation_rate": float(np.mean(np.abs(ey[1:]) > 0.9 * wT)),
+            "dcbf_condition_satisfied": float(np.mean(h[1:] >= (1.0 - g) * h[:-1])),
+            "max_abs_e_y_m": float(np.abs(ey).max()), "distance_m": float(s[-1] - s[0]),
+            "mean_speed_mps": float(vx.mean()),
+            "plant": "same bicycle model stepped on the device (bssmppi_model_step) + N(0, Sigma_w) per step "
+                     "(numpy generator, seed 1, drawn before the loop)"}
+
+
+def reduce_over_ranks(values, device, world):
+    """Element-wise MAX of per-rank values across the job (identity on one rank)."""
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_throughput(units_per_rank, slowest_ms, world):
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / (slowest_ms * 1e-3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -336,12 +397,9 @@ def run_ours(args, rank, world, local_rank):
     mean_ms = statistics.fmean(step_ms)
     mean_roll = statistics.fmean(roll_ms)
     mean_e2e = statistics.fmean(e2e_s)
-    stats = torch.tensor([mean_ms, mean_roll, mean_e2e * 1e3, t_wall], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(stats, op=torch.distributed.ReduceOp.MAX)
-    mean_ms, mean_roll, mean_e2e_ms, t_wall = stats.tolist()
+    mean_ms, mean_roll, mean_e2e_ms, t_wall = reduce_over_ranks([mean_ms, mean_roll, mean_e2e * 1e3, t_wall], dev, world)
     units = p.K * p.M * p.T
-    value = world * units / (mean_ms * 1e-3)
+    value = whole_job_throughput(units, mean_ms, world)
     flops = algorithmic_flops_per_particle_step(p) * units
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / (mean_roll * 1e-3) / 1e12
@@ -355,7 +413,7 @@ def run_ours(args, rank, world, local_rank):
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 (fma) x 2070 MHz max SM clock",
                      "flops_per_particle_step": algorithmic_flops_per_particle_step(p)},
-        "e2e": {"value": world * units / (mean_e2e_ms * 1e-3), "unit": "particle-steps/s",
+        "e2e": {"value": whole_job_throughput(units, mean_e2e_ms, world), "unit": "particle-steps/s",
                 "h2d_bytes_per_step": 4 * (p.nx + 2 * p.T), "d2h_bytes_per_step": 4 * (2 * p.T + 2)},
         "gpu_launches": 3 * args.steps,
         "shield_repair": {"iters": args.repair_iters, "step": args.repair_step, "ms_per_step": rep_ms,
@@ -365,6 +423,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed_region": t_wall,
     }
+    if rank == 0 and args.closed_loop_steps > 0:
+        line["closed_loop"] = run_closed_loop(bssmppi, _problem(args.workload), dev, stream, args.closed_loop_steps)
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = run_serving(args)
     if rank == 0 and not args.no_cpu_baseline:
@@ -383,6 +443,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-samples", type=int, default=128)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--closed-loop-steps", type=int, default=1000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--repair-iters", type=int, default=5)
     ap.add_argument("--repair-step", type=float, default=2e-6)

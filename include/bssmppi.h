@@ -295,11 +295,12 @@ int bssmppi_update_noalloc(const float* d_S, const float* d_eps, float* d_v, flo
                            int32_t compensated, void* cuda_stream);
 
 /*
- * Deterministic model step x_{k+1} = f(x_k, u_k) (Eq. "DeterministicNonlinearSystem"; n_sub Euler
- * substeps of the handle's model, no disturbance) for n independent states: d_x [n*nx], d_u [n*2],
- * d_x_next [n*nx], device. Used to check the model on its own. Asynchronous.
+ * Model step x_{k+1} = f(x_k, u_k) + w_k (Eq. "DeterministicNonlinearSystem" / "DisturbedNonlinearSystem";
+ * n_sub Euler substeps of the handle's model) for n independent states: d_x [n*nx], d_u [n*2],
+ * d_w [n*nx] additive disturbance or NULL for none, d_x_next [n*nx], device. Used to check the model
+ * on its own and to step a simulated plant. Asynchronous.
  */
-int bssmppi_model_step(bssmppi_t h, const float* d_x, const float* d_u, float* d_x_next, int64_t n);
+int bssmppi_model_step(bssmppi_t h, const float* d_x, const float* d_u, const float* d_w, float* d_x_next, int64_t n);
 
 /*
  * Philox4x32-10 (Salmon et al., SC'11), the counter-based generator of every random number the solve

@@ -110,7 +110,7 @@ def load(build_if_missing: bool = True):
         "bssmppi_server_destroy": (ctypes.c_int, [vp]),
         "bssmppi_repair_grad": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "bssmppi_repair": (ctypes.c_int, [vp, vp, vp, i32, ctypes.c_float, vp]),
-        "bssmppi_model_step": (ctypes.c_int, [vp, vp, vp, vp, i64]),
+        "bssmppi_model_step": (ctypes.c_int, [vp, vp, vp, vp, vp, i64]),
         "bssmppi_philox4x32_10": (ctypes.c_int, [vp, u64, vp, i64, vp]),
         "bssmppi_box_muller": (ctypes.c_int, [vp, vp, i64, vp]),
     }
@@ -311,8 +311,10 @@ def repair_objective(v, x0, handle):
     return _RepairObjective.apply(v, x0, handle)
 
 
-def model_step(h, x, u, x_next):
-    _check(load().bssmppi_model_step(h, _ptr(x), _ptr(u), _ptr(x_next), x.shape[0]), h)
+def model_step(h, x, u, x_next, w=None):
+    """x_next = f(x, u) + w for n states (rows of x); w may be None."""
+    n = x.shape[0] if x.dim() > 1 else 1
+    _check(load().bssmppi_model_step(h, _ptr(x), _ptr(u), _ptr(w), _ptr(x_next), n), h)
 
 
 def philox4x32_10(ctr, seed: int, out, stream=None):

@@ -23,7 +23,7 @@ cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, RollLaunch& L
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
                            const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
                            float* var, cudaStream_t st);
-cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, float* xn, int64_t n,
+cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, const float* w, float* xn, int64_t n,
                               cudaStream_t st);
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st);
 cudaError_t box_muller_launch(const uint32_t* words, float* z, int64_t n, cudaStream_t st);

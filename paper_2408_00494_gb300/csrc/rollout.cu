@@ -131,10 +131,11 @@ cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaun
     return comp ? launch_model<1, true>(dp, io, P, L, st) : launch_model<1, false>(dp, io, P, L, st);
 }
 
-// Deterministic model step for n independent states (no disturbance), for model checks.
+// Model step for n independent states, plus an optional additive disturbance (model checks and
+// simulated plants).
 template <int MODEL>
 __global__ void model_step_kernel(const DevParams dp, const float* __restrict__ xin, const float* __restrict__ uin,
-                                  float* __restrict__ xout, int64_t n)
+                                  const float* __restrict__ win, float* __restrict__ xout, int64_t n)
 {
     constexpr int NX = MODEL == 0 ? 6 : 4;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,16 +155,17 @@ __global__ void model_step_kernel(const DevParams dp, const float* __restrict__ 
     model_step<MODEL, NX>(dp, dp.kappa, s0, c, x);
     if constexpr (MODEL == 0) x[5] += s0;
 #pragma unroll
-    for (int j = 0; j < NX; ++j) xout[i * NX + j] = x[j];
+    for (int j = 0; j < NX; ++j) xout[i * NX + j] = x[j] + (win != nullptr ? win[i * NX + j] : 0.0f);
 }
 
-cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, float* xn, int64_t n, cudaStream_t st)
+cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, const float* w, float* xn, int64_t n,
+                              cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const int threads = 128;
     const dim3 grid((unsigned)((n + threads - 1) / threads));
-    if (dp.nx == 6) model_step_kernel<0><<<grid, threads, 0, st>>>(dp, x, u, xn, n);
-    else model_step_kernel<1><<<grid, threads, 0, st>>>(dp, x, u, xn, n);
+    if (dp.nx == 6) model_step_kernel<0><<<grid, threads, 0, st>>>(dp, x, u, w, xn, n);
+    else model_step_kernel<1><<<grid, threads, 0, st>>>(dp, x, u, w, xn, n);
     return cudaGetLastError();
 }
 

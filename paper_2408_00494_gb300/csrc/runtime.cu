@@ -518,11 +518,11 @@ int bssmppi_read(bssmppi_t h, int32_t which, void* d_dst, size_t bytes)
     return BSSMPPI_OK;
 }
 
-int bssmppi_model_step(bssmppi_t h, const float* d_x, const float* d_u, float* d_x_next, int64_t n)
+int bssmppi_model_step(bssmppi_t h, const float* d_x, const float* d_u, const float* d_w, float* d_x_next, int64_t n)
 {
     if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
     if (n < 0 || (n > 0 && (!d_x || !d_u || !d_x_next))) return fail(h, BSSMPPI_EINVAL, "bad arrays");
-    BSS_CUDA(h, bss::model_step_launch(h->dp, d_x, d_u, d_x_next, n, h->stream));
+    BSS_CUDA(h, bss::model_step_launch(h->dp, d_x, d_u, d_w, d_x_next, n, h->stream));
     return BSSMPPI_OK;
 }
 

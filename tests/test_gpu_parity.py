@@ -150,8 +150,13 @@ def test_model_step_matches_oracle(model):
     bssmppi.model_step(c.h, _dev(xs), _dev(us), out)
     g = out.cpu().numpy().astype(np.float64)
     ref = np.stack([o.model_step(xs[i].astype(np.float64), us[i].astype(np.float64)) for i in range(n)])
-    c.close()
     assert_close(g, ref, 2e-5, 2e-5, "model step")
+    # with an additive disturbance: x_next = f(x, u) + w
+    w = np.random.default_rng(2).normal(0, 0.1, size=xs.shape).astype(np.float32)
+    out_w = torch.zeros((n, p.nx), device="cuda")
+    bssmppi.model_step(c.h, _dev(xs), _dev(us), out_w, _dev(w))
+    c.close()
+    assert np.array_equal(out_w.cpu().numpy(), (out.cpu().numpy() + w).astype(np.float32))
 
 
 def test_solve_config0_from_start():
