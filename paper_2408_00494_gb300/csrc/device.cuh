@@ -171,37 +171,64 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const float*
     x[5] = fmaf(P.h, sdot, x[5]);
 }
 
-// Reverse mode of one bicycle substep x' = x + h F(x, u). On entry g holds dL/dx'; on exit g holds
-// dL/dx, and dL/du is added to (g_steer, g_accel). The partial derivatives are those of the
-// forward formulas above: d atan(q)/dq = 1/(1 + q^2), d sin = cos, the quotient rule for s', and
-// the piecewise-linear slope of the curvature table.
-__device__ __forceinline__ void bicycle_substep_vjp(const DevParams& P, const float* __restrict__ kap, float s0,
-                                                    const Control& u, const float (&x)[6], float (&g)[6],
-                                                    float& g_steer, float& g_accel)
+// Tape of one bicycle substep: the transcendental results its adjoint needs
+// {F_yf, dF_yf/dalpha_f, dF_yr/dalpha_r, sin e_psi, cos e_psi, kappa(s), dkappa/ds}.
+constexpr int kTapeFloats = 7;
+
+// The same substep as bicycle_substep, also writing its tape (the repair's forward pass records it
+// so that the reverse sweep needs no transcendental functions).
+__device__ __forceinline__ void bicycle_substep_taped(const DevParams& P, const float* __restrict__ kap, float s0,
+                                                      const Control& u, float (&x)[6], float (&tp)[kTapeFloats])
 {
     const float vx = x[0], vy = x[1], r = x[2], ep = x[3], ey = x[4];
-    const float vxh = fmaxf(vx, P.vx_floor);
-    const float inv_vx = __fdividef(1.0f, vxh);
-    const float yf = vy + P.lf * r, yr = vy - P.lr * r;
-    const float alpha_f = u.steer - atanf(yf * inv_vx);
-    const float alpha_r = -atanf(yr * inv_vx);
+    const float inv_vx = __fdividef(1.0f, fmaxf(vx, P.vx_floor));
+    const float alpha_f = u.steer - atanf((vy + P.lf * r) * inv_vx);
+    const float alpha_r = -atanf((vy - P.lr * r) * inv_vx);
     const float bf = P.tB * alpha_f, br = P.tB * alpha_r;
-    const float tf = atanf(bf), tr = atanf(br);
-    float sf, cf;
-    __sincosf(P.tC * tf, &sf, &cf);
-    const float cr = __cosf(P.tC * tr);
-    const float Ff = P.Df * sf;
-    const float dFf = __fdividef(P.Df * cf * P.tC * P.tB, 1.0f + bf * bf);
-    const float dFr = __fdividef(P.Dr * cr * P.tC * P.tB, 1.0f + br * br);
-    const float s = s0 + x[5];
-    const float xs = s * P.track_scale;
+    float sf, cf, sr, cr;
+    __sincosf(P.tC * atanf(bf), &sf, &cf);
+    __sincosf(P.tC * atanf(br), &sr, &cr);
+    const float Ff = P.Df * sf, Fr = P.Dr * sr;
+    const float xs = (s0 + x[5]) * P.track_scale;
     const float fl = floorf(xs);
     const int i = ((int)fl) & P.n_track_mask;
     const float k0 = kap[i], k1 = kap[i + 1];
     const float kap_s = fmaf(xs - fl, k1 - k0, k0);
-    const float dkap = (k1 - k0) * P.track_scale;
     float sp, cp;
     sincosf(ep, &sp, &cp);
+    const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
+    const float dvx = u.accel - Ff * u.sin_steer * P.inv_m + vy * r;
+    const float dvy = (Ff * u.cos_steer + Fr) * P.inv_m - vx * r;
+    const float dr = (P.lf * Ff * u.cos_steer - P.lr * Fr) * P.inv_Iz;
+    const float dep = r - kap_s * sdot;
+    const float dey = vx * sp + vy * cp;
+    tp[0] = Ff;
+    tp[1] = __fdividef(P.Df * cf * P.tC * P.tB, 1.0f + bf * bf);
+    tp[2] = __fdividef(P.Dr * cr * P.tC * P.tB, 1.0f + br * br);
+    tp[3] = sp;
+    tp[4] = cp;
+    tp[5] = kap_s;
+    tp[6] = (k1 - k0) * P.track_scale;
+    x[0] = fmaf(P.h, dvx, vx);
+    x[1] = fmaf(P.h, dvy, vy);
+    x[2] = fmaf(P.h, dr, r);
+    x[3] = fmaf(P.h, dep, ep);
+    x[4] = fmaf(P.h, dey, ey);
+    x[5] = fmaf(P.h, sdot, x[5]);
+}
+
+// Reverse mode of one bicycle substep x' = x + h F(x, u) from its tape. On entry g holds dL/dx';
+// on exit g holds dL/dx, and dL/du is added to (g_steer, g_accel). The partial derivatives are
+// those of the forward formulas: d atan(q)/dq = 1/(1 + q^2), d sin = cos, the quotient rule for
+// s', and the piecewise-linear slope of the curvature table.
+__device__ __forceinline__ void bicycle_substep_vjp_taped(const DevParams& P, const Control& u, const float (&x)[6],
+                                                          const float (&tp)[kTapeFloats], float (&g)[6],
+                                                          float& g_steer, float& g_accel)
+{
+    const float vx = x[0], vy = x[1], r = x[2], ey = x[4];
+    const float vxh = fmaxf(vx, P.vx_floor);
+    const float yf = vy + P.lf * r, yr = vy - P.lr * r;
+    const float Ff = tp[0], dFf = tp[1], dFr = tp[2], sp = tp[3], cp = tp[4], kap_s = tp[5], dkap = tp[6];
     const float num = vx * cp - vy * sp;
     const float inv_den = __fdividef(1.0f, 1.0f - kap_s * ey);
     const float sdot = num * inv_den;

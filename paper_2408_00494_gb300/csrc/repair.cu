@@ -6,12 +6,15 @@
 // disturbance draws are those of sample 0 of the current solve counter, fixed across evaluations
 // (common random numbers), so J_r is a deterministic, piecewise-smooth function of v.
 //
-// One block, one thread per particle (M <= 256). Forward: propagate, store the particle states of
-// every step in scratch, merge count/mean/M2 of e_y across the block (Chan's pairwise update),
-// and form h_t, the hinge arguments and J. Reverse: for t = T..1 add dJ/dh_t through the mean and
-// the unbiased standard deviation to each particle's e_y cotangent, then pull the cotangent back
-// through the n_sub Euler substeps (recomputed from the stored state) and sum dJ/du_{t-1} over the
-// particles. `iters` projected gradient steps v <- clamp(v - step dJ/dv) run inside one launch.
+// One block, one thread per particle (M <= 256). Forward: propagate, store every particle's state
+// at every Euler substep in scratch (L2-resident), merge count/mean/M2 of e_y across the block
+// (Chan's pairwise update), and form h_t, the hinge arguments and J. Reverse: for t = T..1 add
+// dJ/dh_t through the mean and the unbiased standard deviation to each particle's e_y cotangent,
+// then pull the cotangent back through the n_sub substeps from their stored states (the next
+// state is loaded while the current adjoint runs) and sum dJ/du_{t-1} over the particles. The
+// kernel is latency-bound (a serial chain per particle); storing the substates removes the
+// forward recomputation from the reverse chain. `iters` projected gradient steps
+// v <- clamp(v - step dJ/dv) run inside one launch.
 #include "device.cuh"
 #include "internal.h"
 
@@ -73,10 +76,17 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
 #pragma unroll
     for (int i = 0; i < NX; ++i) x0[i] = io.x0[i];
     const float s0 = (MODEL == 0) ? x0[5] : 0.0f;
-    auto Xat = [&](int t, int i) -> float* { return io.X + ((size_t)t * NX + i) * M + n; };
+    // Records of the forward pass, component-major so each field of all particles is contiguous:
+    // record (t, j) = the state entering Euler substep j of step t, then (bicycle) that substep's
+    // tape. Xat(t, i) = component i of the state at the start of step t.
+    const int nsub = (MODEL == 0) ? dp.n_sub : 1;
+    constexpr int R = (MODEL == 0) ? NX + kTapeFloats : NX;
+    auto Xs = [&](int t, int j, int i) -> float* { return io.X + (((size_t)t * nsub + j) * R + i) * M + n; };
+    auto Xat = [&](int t, int i) -> float* { return Xs(t, 0, i); };
 
     for (int it = 0; it <= io.iters; ++it) {
         const bool last = (it == io.iters);
+        if (last && io.grad == nullptr && io.J == nullptr) break;  // nobody reads the final objective
         // ---------------- forward rollout of the nominal sequence
         float x[NX];
 #pragma unroll
@@ -94,7 +104,25 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
             c.steer = v_s[2 * t];
             c.accel = v_s[2 * t + 1];
             if constexpr (MODEL == 0) sincosf(c.steer, &c.sin_steer, &c.cos_steer);
-            model_step<MODEL, NX>(dp, kap_s, s0, c, x);
+            if constexpr (MODEL == 0) {
+                for (int j = 0; j < nsub; ++j) {
+                    float tp[kTapeFloats];
+                    float xb[6];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) xb[i] = x[i];
+                    bicycle_substep_taped(dp, kap_s, s0, c, x, tp);
+                    if (valid) {  // the state of substep 0 is stored with the previous step's result
+                        if (j > 0) {
+#pragma unroll
+                            for (int i = 0; i < 6; ++i) *Xs(t, j, i) = xb[i];
+                        }
+#pragma unroll
+                        for (int i = 0; i < kTapeFloats; ++i) *Xs(t, j, 6 + i) = tp[i];
+                    }
+                }
+            } else {
+                model_step<MODEL, NX>(dp, kap_s, s0, c, x);
+            }
             float z[NX];
             draw_normals<NX>(dp, (uint32_t)t, (uint32_t)n, 0u, kStreamDisturbance, ctr, z);
             add_correlated<NX>(dp.Lw, z, x);
@@ -158,31 +186,24 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
                 }
                 g[EY] += gh * term;
             }
-            float xp[NX];
-#pragma unroll
-            for (int i = 0; i < NX; ++i) xp[i] = valid ? *Xat(t - 1, i) : x0[i];
             Control c;
             c.steer = v_s[2 * (t - 1)];
             c.accel = v_s[2 * (t - 1) + 1];
             float gs = 0.0f, ga = 0.0f;
             if constexpr (MODEL == 0) {
                 sincosf(c.steer, &c.sin_steer, &c.cos_steer);
-                float xs[kRepairMaxSub + 1][6];
+                // The forward pass stored each substep's state and tape; the next record is loaded
+                // while the current substep's adjoint runs, so the loads stay off the chain.
+                float cur[R], nxt[R];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) xs[0][i] = xp[i];
-                for (int j = 0; j < dp.n_sub; ++j) {
-                    float y[6];
+                for (int i = 0; i < R; ++i) cur[i] = valid ? *Xs(t - 1, nsub - 1, i) : (i < 6 ? x0[i] : 0.0f);
+                for (int j = nsub - 1; j >= 0; --j) {
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) y[i] = xs[j][i];
-                    bicycle_substep(dp, kap_s, s0, c, y);
+                    for (int i = 0; i < R; ++i) nxt[i] = (valid && j > 0) ? *Xs(t - 1, j - 1, i) : cur[i];
+                    bicycle_substep_vjp_taped(dp, c, *reinterpret_cast<const float(*)[6]>(cur),
+                                              *reinterpret_cast<const float(*)[kTapeFloats]>(cur + 6), g, gs, ga);
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) xs[j + 1][i] = y[i];
-                }
-                for (int j = dp.n_sub - 1; j >= 0; --j) {
-                    float y[6];
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) y[i] = xs[j][i];
-                    bicycle_substep_vjp(dp, kap_s, s0, c, y, g, gs, ga);
+                    for (int i = 0; i < R; ++i) cur[i] = nxt[i];
                 }
             } else {
                 double_integrator_step_vjp(dp, g, gs, ga);
@@ -229,7 +250,12 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
     }
 }
 
-size_t repair_scratch_floats(const DevParams& dp) { return (size_t)(dp.T + 1) * dp.nx * dp.M; }
+size_t repair_scratch_floats(const DevParams& dp)
+{
+    const size_t nsub = dp.nx == 6 ? (size_t)dp.n_sub : 1;
+    const size_t record = dp.nx == 6 ? (size_t)dp.nx + kTapeFloats : (size_t)dp.nx;
+    return ((size_t)dp.T * nsub + 1) * record * dp.M;
+}
 
 static size_t repair_smem_bytes(const DevParams& dp)
 {
