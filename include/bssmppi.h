@@ -195,11 +195,13 @@ int bssmppi_repair_grad(bssmppi_t h, const float* d_x0, const float* d_v, float*
 int bssmppi_repair(bssmppi_t h, const float* d_x0, float* d_v, int32_t iters, float step, float* d_J);
 
 /*
- * Per-phase timing with CUDA events recorded on the handle's stream around the rollout kernel and
- * around the weights/update kernel of every solve. bssmppi_timing(h, n) with n > 0 starts recording
- * the next n solves (older records are dropped; n <= 4096), n = 0 stops. bssmppi_timing_read waits
- * for the recorded events and writes up to `max` durations in milliseconds (rollout_ms[i],
- * update_ms[i], either may be NULL) for the solves recorded so far; *count receives how many.
+ * Kernel timing with CUDA events recorded on the handle's stream around the single launch of every
+ * solve (rollout, costs, and the weights/update fused into that kernel's tail).
+ * bssmppi_timing(h, n) with n > 0 starts recording the next n solves (older records are dropped;
+ * n <= 4096), n = 0 stops. bssmppi_timing_read waits for the recorded events and writes up to `max`
+ * durations in milliseconds (rollout_ms[i]: the whole launch; update_ms[i]: always 0, the update
+ * has no launch of its own; either array may be NULL) for the solves recorded so far; *count
+ * receives how many.
  */
 int bssmppi_timing(bssmppi_t h, int32_t n);
 int bssmppi_timing_read(bssmppi_t h, float* h_rollout_ms, float* h_update_ms, int32_t max, int32_t* count);

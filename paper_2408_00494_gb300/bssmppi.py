@@ -249,7 +249,8 @@ def timing(h, n: int):
 
 
 def timing_read(h, max_n: int = 4096):
-    """Per-phase durations (ms) of the solves recorded since timing(h, n): (rollout, update) arrays."""
+    """Durations (ms) of the solves recorded since timing(h, n): (solve kernel, update) arrays; the update
+    is fused into the solve kernel, so its entries are 0."""
     roll = np.zeros(max_n, np.float32)
     upd = np.zeros(max_n, np.float32)
     n = ctypes.c_int32()

@@ -26,7 +26,7 @@ struct DevParams {
     float Le00, Le10, Le11;          // Cholesky factor of Sigma_eps
     float Si00, Si01, Si10, Si11;    // Sigma_eps^-1
     float Lw[21];                    // Cholesky factor of Sigma_w, packed lower triangle by rows
-    float inv_lambda, nu, one_m_gamma, ctrl_w, Csafe, Cobs, wT;
+    float lambda, inv_lambda, nu, one_m_gamma, ctrl_w, Csafe, Cobs, wT;
     float xg[6], Q[6], Qf[6];
     float track_scale;               // n_track / track_len
     float Mf, invM, invM1;           // M, 1/M, 1/(M-1)

@@ -18,11 +18,23 @@ struct RollLaunch {
     int wpb = 1;       // warps per block
     size_t smem = 0;   // dynamic shared memory per block
 };
+constexpr int kTailMaxBlocks = 256;  // grid bound of the fused rollout (one block per SM)
+
+// Outputs and scratch of the weights/update fused into the rollout kernel's tail.
+struct TailIO {
+    float* part;            // scratch: grid x (3 + 2T) block partials
+    unsigned int* ticket;   // scratch: zero on entry, left at zero
+    float* w;               // K normalised weights (out)
+    float* u0;              // 2 (out) or nullptr
+    float* diag;            // 4 (out) or nullptr
+    uint32_t* ctr_out;      // the solve counter, incremented by the last block
+    float* v_out;           // T*2: v+ (the resident nominal, read by every block first)
+};
 size_t rollout_smem_bytes(const DevParams& dp, int wpb);
 cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, RollLaunch& L);
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
                            const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
-                           float* var, cudaStream_t st);
+                           float* var, const TailIO& tail, cudaStream_t st);
 cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, const float* w, float* xn, int64_t n,
                               cudaStream_t st);
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st);

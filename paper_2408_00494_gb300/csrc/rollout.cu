@@ -9,57 +9,319 @@
 
 namespace bss {
 
-// Persistent rollout: the block's warps walk the sample groups with a grid stride. The curvature
-// table and the nominal sequence are staged in shared memory once per block.
+// The last block's merge of the block partials (block order; out of line so that its registers
+// do not weigh on the rollout loop). red: max(2T, threads) floats of shared scratch; fac_s, red_e,
+// red_q: one float per block.
+constexpr int kTailBatch = 8;  // independent L2 loads a thread keeps in flight in the merge
+
+template <bool COMP>
+__device__ __noinline__ void tail_merge(const int K, const int T, const float lambda, const float inv_lambda,
+                                        const float* S, const TailIO tail, const float* v_s, float* red,
+                                        float* fac_s, float* red_e, float* red_q, float* bc_s)
+{
+    const int G = gridDim.x, tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid / kWarp, lane = tid & (kWarp - 1), wpb = nthr / kWarp;
+    const int TN = 2 * T;
+    const size_t stride = 3 + TN;
+    // beta = min over blocks, then every block's factor exp(-(beta_b - beta)/lambda)
+    float b = INFINITY;
+    for (int g = tid; g < G; g += nthr) b = fminf(b, __ldcg(tail.part + g * stride));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) b = fminf(b, __shfl_xor_sync(0xffffffffu, b, off));
+    if (lane == 0) red[warp] = b;
+    __syncthreads();
+    if (tid == 0) {
+        float x = red[0];
+        for (int w = 1; w < wpb; ++w) x = fminf(x, red[w]);
+        bc_s[0] = x;
+    }
+    __syncthreads();
+    const float beta = bc_s[0];
+    for (int g = tid; g < G; g += nthr) {
+        const float bg = __ldcg(tail.part + g * stride);
+        const float f = (bg < INFINITY) ? expf((beta - bg) * inv_lambda) : 0.0f;
+        fac_s[g] = f;
+        red_e[g] = __ldcg(tail.part + g * stride + 1) * f;
+        red_q[g] = __ldcg(tail.part + g * stride + 2) * f * f;
+    }
+    __syncthreads();
+    if (warp == 0) {  // eta and sum of squares: lane l adds blocks l, l+32, ... then a fixed tree
+        CompSum e, q;
+        float e_n = 0.0f, q_n = 0.0f;
+        for (int g = lane; g < G; g += kWarp) {
+            if constexpr (COMP) {
+                e.add(red_e[g]);
+                q.add(red_q[g]);
+            } else {
+                e_n += red_e[g];
+                q_n += red_q[g];
+            }
+        }
+        float es = COMP ? e.s : e_n, ec = COMP ? e.c : 0.0f, qs = COMP ? q.s : q_n, qc = COMP ? q.c : 0.0f;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float es2 = __shfl_xor_sync(0xffffffffu, es, off), ec2 = __shfl_xor_sync(0xffffffffu, ec, off);
+            const float qs2 = __shfl_xor_sync(0xffffffffu, qs, off), qc2 = __shfl_xor_sync(0xffffffffu, qc, off);
+            comp_merge(es, ec, es2, ec2);
+            comp_merge(qs, qc, qs2, qc2);
+        }
+        if (lane == 0) {
+            bc_s[1] = es + ec;
+            bc_s[2] = qs + qc;
+        }
+    }
+    // sum_b N_b[i] f_b: thread (group, i) adds blocks group, group + NG, ...; then the NG group sums
+    const int NG = max(1, nthr / TN);
+    for (int idx = tid; idx < TN * NG; idx += nthr) {
+        const int i = idx % TN, grp = idx / TN;
+        CompSum n;
+        float n_n = 0.0f;
+        for (int g0 = grp; g0 < G; g0 += kTailBatch * NG) {  // loads of a batch in flight together
+            float x[kTailBatch];
+#pragma unroll
+            for (int j = 0; j < kTailBatch; ++j) {
+                const int g = g0 + j * NG;
+                x[j] = g < G ? __ldcg(tail.part + g * stride + 3 + i) * fac_s[g] : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < kTailBatch; ++j) {
+                if constexpr (COMP) n.add(x[j]); else n_n += x[j];
+            }
+        }
+        red[grp * TN + i] = COMP ? n.value() : n_n;
+    }
+    __syncthreads();
+    const float eta = bc_s[1], sumsq = bc_s[2];
+    for (int i = tid; i < TN; i += nthr) {
+        CompSum n;
+        float n_n = 0.0f;
+        for (int grp = 0; grp < NG; ++grp) {
+            if constexpr (COMP) n.add(red[grp * TN + i]); else n_n += red[grp * TN + i];
+        }
+        const float vn = v_s[i] + (COMP ? n.value() : n_n) / eta;
+        tail.v_out[i] = vn;
+        if (tail.u0 != nullptr && i < 2) tail.u0[i] = vn;
+    }
+    for (int k0 = tid; k0 < K; k0 += kTailBatch * nthr) {
+        float s[kTailBatch];
+#pragma unroll
+        for (int j = 0; j < kTailBatch; ++j) s[j] = k0 + j * nthr < K ? __ldcg(S + k0 + j * nthr) : 0.0f;
+#pragma unroll
+        for (int j = 0; j < kTailBatch; ++j) {
+            if (k0 + j * nthr < K) tail.w[k0 + j * nthr] = expf(-(s[j] - beta) * inv_lambda) / eta;
+        }
+    }
+    if (tid == 0) {
+        if (tail.diag != nullptr) {
+            tail.diag[0] = beta;
+            tail.diag[1] = eta;
+            tail.diag[2] = eta * eta / sumsq;
+            tail.diag[3] = beta - lambda * logf(eta / (float)K);
+        }
+        *tail.ctr_out += 1u;
+        *tail.ticket = 0u;
+    }
+}
+
+// A block's partial of the weights/update over the samples it rolled out, read back from S and
+// eps (written by the block's own warps, still in L2): beta_b = min S, eta_b = sum exp(-(S - beta_b)/
+// lambda), q_b = sum of their squares, N_b[i] = sum exp(-(S - beta_b)/lambda) eps[i]. Samples are taken
+// in a fixed order (t -> round j, warp w, slot s), so the result does not depend on timing. red:
+// max(2T, threads) floats of shared scratch.
+template <bool COMP>
+__device__ __noinline__ void block_partial(const int K, const int T, const int spw, const float inv_lambda,
+                                           const float* S, const float* eps, float* part, float* red, float* bc_s)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x, wpb = nthr / kWarp;
+    const int warp = tid / kWarp, lane = tid & (kWarp - 1);
+    const int TN = 2 * T;
+    const int n_groups = (K + spw - 1) / spw;
+    const int rounds = (n_groups + gridDim.x * wpb - 1) / (gridDim.x * wpb);
+    const int nb = rounds * wpb * spw;  // candidate samples of this block (some past K)
+    auto sample = [&](int t) -> int {   // global sample index of block-local t, or -1
+        const int s = t % spw, jw = t / spw;
+        const int g = blockIdx.x * wpb + (jw % wpb) + (jw / wpb) * gridDim.x * wpb;
+        const int k = g * spw + s;
+        return (g < n_groups && k < K) ? k : -1;
+    };
+    // beta_b
+    float b = INFINITY;
+    for (int t = tid; t < nb; t += nthr) {
+        const int k = sample(t);
+        if (k >= 0) b = fminf(b, __ldcg(S + k));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) b = fminf(b, __shfl_xor_sync(0xffffffffu, b, off));
+    if (lane == 0) red[warp] = b;
+    __syncthreads();
+    if (tid == 0) {
+        float x = red[0];
+        for (int w = 1; w < wpb; ++w) x = fminf(x, red[w]);
+        bc_s[0] = x;
+    }
+    __syncthreads();
+    const float beta = bc_s[0];
+    if (!(beta < INFINITY)) {  // no samples in this block
+        for (int i = tid; i < 3 + TN; i += nthr) part[i] = i == 0 ? INFINITY : 0.0f;
+        return;
+    }
+    // eta_b and q_b: thread sums over t = tid, tid + nthr, ...; fixed trees over lanes, then warps
+    {
+        CompSum e, q;
+        float e_n = 0.0f, q_n = 0.0f;
+        for (int t = tid; t < nb; t += nthr) {
+            const int k = sample(t);
+            if (k < 0) continue;
+            const float w = expf(-(__ldcg(S + k) - beta) * inv_lambda);
+            if constexpr (COMP) {
+                e.add(w);
+                q.add(w * w);
+            } else {
+                e_n += w;
+                q_n = fmaf(w, w, q_n);
+            }
+        }
+        float es = COMP ? e.s : e_n, ec = COMP ? e.c : 0.0f, qs = COMP ? q.s : q_n, qc = COMP ? q.c : 0.0f;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float es2 = __shfl_xor_sync(0xffffffffu, es, off), ec2 = __shfl_xor_sync(0xffffffffu, ec, off);
+            const float qs2 = __shfl_xor_sync(0xffffffffu, qs, off), qc2 = __shfl_xor_sync(0xffffffffu, qc, off);
+            comp_merge(es, ec, es2, ec2);
+            comp_merge(qs, qc, qs2, qc2);
+        }
+        __syncthreads();  // red[] reads of the beta reduction are done
+        if (lane == 0) {
+            red[4 * warp + 0] = es;
+            red[4 * warp + 1] = ec;
+            red[4 * warp + 2] = qs;
+            red[4 * warp + 3] = qc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float es0 = red[0], ec0 = red[1], qs0 = red[2], qc0 = red[3];
+            for (int w = 1; w < wpb; ++w) {
+                comp_merge(es0, ec0, red[4 * w], red[4 * w + 1]);
+                comp_merge(qs0, qc0, red[4 * w + 2], red[4 * w + 3]);
+            }
+            part[0] = beta;
+            part[1] = es0 + ec0;
+            part[2] = qs0 + qc0;
+        }
+        __syncthreads();  // red[] is reused below
+    }
+    // N_b[i]: thread (sub, i) adds t = sub, sub + NG, ... (loads of a batch in flight together);
+    // then the NG sub-sums in order
+    const int NG = max(1, nthr / TN);
+    for (int idx = tid; idx < TN * NG; idx += nthr) {
+        const int i = idx % TN, sub = idx / TN;
+        CompSum n;
+        float n_n = 0.0f;
+        for (int t0 = sub; t0 < nb; t0 += kTailBatch * NG) {
+            float x[kTailBatch];
+#pragma unroll
+            for (int j = 0; j < kTailBatch; ++j) {
+                const int t = t0 + j * NG;
+                const int k = t < nb ? sample(t) : -1;
+                x[j] = k >= 0 ? expf(-(__ldcg(S + k) - beta) * inv_lambda) * __ldcg(eps + (size_t)k * TN + i) : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < kTailBatch; ++j) {
+                if constexpr (COMP) n.add(x[j]); else n_n += x[j];
+            }
+        }
+        red[sub * TN + i] = COMP ? n.value() : n_n;
+    }
+    __syncthreads();
+    for (int i = tid; i < TN; i += nthr) {
+        CompSum n;
+        float n_n = 0.0f;
+        for (int sub = 0; sub < NG; ++sub) {
+            if constexpr (COMP) n.add(red[sub * TN + i]); else n_n += red[sub * TN + i];
+        }
+        part[3 + i] = COMP ? n.value() : n_n;
+    }
+}
+
+// Persistent rollout with the weights and update fused into its tail.
+//
+// The block's warps walk the sample groups with a grid stride; the curvature table and the nominal
+// sequence are staged in shared memory once per block. Weights (Eq. "Weights") and update (Eq.
+// "MPPI update law") follow the last group without a second launch: every block publishes the
+// log-sum-exp partial of its own samples (block_partial), and the last block to arrive (atomic
+// ticket) merges the partials in block order and writes v+ = v + N / eta, u0, the normalised weights,
+// the diagnostics and the counter (tail_merge). No block waits for another.
 template <int MODEL, int P, bool COMP>
-__global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const DevParams dp, const RollIO io)
+__global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const DevParams dp, const RollIO io,
+                                                                       const TailIO tail)
 {
     extern __shared__ float smem[];
+    __shared__ float fac_s[kTailMaxBlocks];
+    __shared__ float red_e[kTailMaxBlocks], red_q[kTailMaxBlocks];
+    __shared__ float bc_s[3];
+    __shared__ bool is_last;
     const int ntab = dp.n_track_mask + 1;
+    const int TN = 2 * dp.T;
+    const int wpb = blockDim.x / kWarp;
     float* kap_s = smem;
     float* v_s = smem + ((ntab + 1 + 3) & ~3);
-    float* u_s = v_s + 2 * dp.T;
+    float* u_s = v_s + TN;
+    float* red = u_s + (size_t)wpb * dp.spw * TN;  // tail scratch: max(TN, threads) floats
 
     if constexpr (MODEL == 0) {
         for (int i = threadIdx.x; i <= ntab; i += blockDim.x) kap_s[i] = dp.kappa[i];
     }
-    for (int i = threadIdx.x; i < 2 * dp.T; i += blockDim.x) v_s[i] = io.v[i];
+    for (int i = threadIdx.x; i < TN; i += blockDim.x) v_s[i] = io.v[i];
     __syncthreads();
 
     const uint32_t ctr = *io.ctr;
     const int warp = threadIdx.x / kWarp;
-    const int wpb = blockDim.x / kWarp;
     const int lane = threadIdx.x & (kWarp - 1);
-    float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * 2 * dp.T;
+    float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * TN;
     const int n_groups = (dp.K + dp.spw - 1) / dp.spw;
-    for (int group = blockIdx.x * wpb + warp; group < n_groups; group += gridDim.x * wpb) {
+    for (int group = blockIdx.x * wpb + warp; group < n_groups; group += gridDim.x * wpb)
         rollout_group<MODEL, P, COMP>(dp, io, kap_s, v_s, my_u, group, ctr);
-        __syncwarp();  // the next group's prologue rewrites my_u
-    }
+    __syncthreads();
+
+    float* part = tail.part + (size_t)blockIdx.x * (3 + TN);
+    block_partial<COMP>(dp.K, dp.T, dp.spw, dp.inv_lambda, io.S, io.eps, part, red, bc_s);
+
+    // The last block to arrive merges the block partials in block order.
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(tail.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    tail_merge<COMP>(dp.K, dp.T, dp.lambda, dp.inv_lambda, io.S, tail, v_s, red, fac_s, red_e, red_q, bc_s);
 }
 
 size_t rollout_smem_bytes(const DevParams& dp, int wpb)
 {
     const int ntab = dp.n_track_mask + 1;
-    const size_t floats = (size_t)((ntab + 1 + 3) & ~3) + 2 * (size_t)dp.T + (size_t)wpb * dp.spw * 2 * dp.T;
+    const size_t TN = 2 * (size_t)dp.T;
+    const size_t floats = (size_t)((ntab + 1 + 3) & ~3) + TN + (size_t)wpb * dp.spw * TN
+                        + std::max(TN, (size_t)wpb * kWarp);
     return floats * sizeof(float);
 }
 
 template <int MODEL, int P, bool COMP>
-static cudaError_t launch_one(const DevParams& dp, const RollIO& io, const RollLaunch& L, cudaStream_t st)
+static cudaError_t launch_one(const DevParams& dp, const RollIO& io, const TailIO& tail, const RollLaunch& L,
+                              cudaStream_t st)
 {
-    rollout_kernel<MODEL, P, COMP><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io);
+    if (L.grid > kTailMaxBlocks) return cudaErrorInvalidValue;
+    rollout_kernel<MODEL, P, COMP><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io, tail);
     return cudaGetLastError();
 }
 
 template <int MODEL, bool COMP>
-static cudaError_t launch_model(const DevParams& dp, const RollIO& io, int P, const RollLaunch& L, cudaStream_t st)
+static cudaError_t launch_model(const DevParams& dp, const RollIO& io, const TailIO& tail, int P, const RollLaunch& L,
+                                cudaStream_t st)
 {
     switch (P) {
-    case 1: return launch_one<MODEL, 1, COMP>(dp, io, L, st);
-    case 2: return launch_one<MODEL, 2, COMP>(dp, io, L, st);
-    case 4: return launch_one<MODEL, 4, COMP>(dp, io, L, st);
-    case 8: return launch_one<MODEL, 8, COMP>(dp, io, L, st);
+    case 1: return launch_one<MODEL, 1, COMP>(dp, io, tail, L, st);
+    case 2: return launch_one<MODEL, 2, COMP>(dp, io, tail, L, st);
+    case 4: return launch_one<MODEL, 4, COMP>(dp, io, tail, L, st);
+    case 8: return launch_one<MODEL, 8, COMP>(dp, io, tail, L, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -75,8 +337,13 @@ static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
+    cudaFuncAttributes attr{};
+    e = cudaFuncGetAttributes(&attr, kern);
+    if (e != cudaSuccess) return e;
+    sms = std::min(sms, kTailMaxBlocks);
     const int max_w = roll_max_threads<P>() / kWarp;
-    const size_t smem_cap = std::min(rollout_smem_bytes(dp, max_w), (size_t)optin);
+    const size_t optin_dynamic = (size_t)optin > attr.sharedSizeBytes ? (size_t)optin - attr.sharedSizeBytes : 0;
+    const size_t smem_cap = std::min(rollout_smem_bytes(dp, max_w), optin_dynamic);
     if (rollout_smem_bytes(dp, 1) > smem_cap) return cudaErrorInvalidValue;  // one warp's share does not fit
     if (smem_cap > 48 * 1024) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
@@ -124,11 +391,12 @@ cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, RollLaunch& L
 
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
                            const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
-                           float* var, cudaStream_t st)
+                           float* var, const TailIO& tail, cudaStream_t st)
 {
     RollIO io{x0, Sigma0, v, ctr, S, eps, mean, var};
-    if (dp.nx == 6) return comp ? launch_model<0, true>(dp, io, P, L, st) : launch_model<0, false>(dp, io, P, L, st);
-    return comp ? launch_model<1, true>(dp, io, P, L, st) : launch_model<1, false>(dp, io, P, L, st);
+    if (dp.nx == 6)
+        return comp ? launch_model<0, true>(dp, io, tail, P, L, st) : launch_model<0, false>(dp, io, tail, P, L, st);
+    return comp ? launch_model<1, true>(dp, io, tail, P, L, st) : launch_model<1, false>(dp, io, tail, P, L, st);
 }
 
 // Model step for n independent states, plus an optional additive disturbance (model checks and

@@ -167,10 +167,12 @@ constexpr int roll_max_threads()
 }
 
 // One sample group (the spw samples of one warp): control sequence, rollout, moments, cost.
+// Returns the cost S of the lane's own sample (identical on every lane of its segment); my_u keeps
+// the segment's clamped control sequence u (T x 2) until the warp's next group.
 template <int MODEL, int P, bool COMP>
-__device__ __forceinline__ void rollout_group(const DevParams& dp, const RollIO& io, const float* __restrict__ kap_s,
-                                              const float* __restrict__ v_s, float* __restrict__ my_u, int group,
-                                              uint32_t ctr)
+__device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO& io, const float* __restrict__ kap_s,
+                                               const float* __restrict__ v_s, float* __restrict__ my_u, int group,
+                                               uint32_t ctr)
 {
     constexpr int NX = MODEL == 0 ? 6 : 4;
     constexpr int EY = MODEL == 0 ? 4 : 1;
@@ -303,6 +305,7 @@ __device__ __forceinline__ void rollout_group(const DevParams& dp, const RollIO&
         total = S_naive + term;
     }
     if (writer) io.S[k] = total;
+    return total;
 }
 
 }  // namespace bss

@@ -30,6 +30,7 @@ struct bssmppi_ctx {
     float* d_diag = nullptr;
     uint32_t* d_ctr = nullptr;
     float* d_partial = nullptr;
+    float* d_tail_part = nullptr;  // block partials of the rollout's fused weights/update tail
     unsigned int* d_ticket = nullptr;
     float* d_repair_X = nullptr;  // stored particle states of the repair rollout
     float* d_repair_J = nullptr;  // objective of the last repair_grad call
@@ -162,11 +163,12 @@ int alloc(bssmppi_ctx* h, T** ptr, size_t count)
 void release(bssmppi_ctx* h)
 {
     void* ptrs[] = {h->d_kappa, h->d_S, h->d_w, h->d_eps, h->d_mean, h->d_var, h->d_v, h->d_x0, h->d_Sigma0,
-                    h->d_u0, h->d_diag, h->d_ctr, h->d_partial, h->d_ticket, h->d_repair_X, h->d_repair_J};
+                    h->d_u0, h->d_diag, h->d_ctr, h->d_partial, h->d_ticket, h->d_repair_X, h->d_repair_J,
+                    h->d_tail_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_stage) cudaFreeHost(h->h_stage);
-    for (int i = 0; i < 4 * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < 2 * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
     delete[] h->ev;
     h->ev = nullptr;
     h->ev_cap = 0;
@@ -223,6 +225,7 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     for (int i = 0; i < 21; ++i) d.Lw[i] = 0.0f;
     for (int i = 0; i < nx; ++i)
         for (int j = 0; j <= i; ++j) d.Lw[i * (i + 1) / 2 + j] = (float)Lw[i * nx + j];
+    d.lambda = p->lambda;
     d.inv_lambda = 1.0f / p->lambda;
     d.nu = (float)(std::sqrt(2.0) * inverse_erf(1.0 - 2.0 * (double)p->delta));
     d.one_m_gamma = 1.0f - p->gamma;
@@ -290,6 +293,7 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ctr, 1);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_partial, (size_t)G * T * 2);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ticket, 1);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_tail_part, (size_t)bss::kTailMaxBlocks * (3 + 2 * T));
     if (rc == BSSMPPI_OK && p->M <= 256) rc = alloc(h, &h->d_repair_X, bss::repair_scratch_floats(h->dp));
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_repair_J, 1);
     if (rc == BSSMPPI_OK) {
@@ -337,17 +341,14 @@ int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* 
     if (!d_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
     const size_t vbytes = sizeof(float) * 2 * h->prm.T;
     if (d_v) BSS_CUDA(h, cudaMemcpyAsync(h->d_v, d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
-    cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 4 * h->ev_count : nullptr;
+    cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 2 * h->ev_count : nullptr;
     if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], h->stream));
+    // One launch: rollout, costs, and (in its tail) weights, update, u0, diagnostics, counter.
+    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, h->d_ctr, h->d_v};
     BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, h->d_v, h->d_ctr,
-                                    h->d_S, h->d_eps, h->d_mean, h->d_var, h->stream));
-    if (ev) BSS_CUDA(h, cudaEventRecord(ev[1], h->stream));
-    bss::UpdateIO io{h->d_S, h->d_eps, h->d_v, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, h->d_ctr,
-                     h->d_partial, h->d_ticket};
-    if (ev) BSS_CUDA(h, cudaEventRecord(ev[2], h->stream));
-    BSS_CUDA(h, bss::update_launch(h->prm.K, h->prm.T, h->prm.lambda, h->prm.compensated != 0, io, h->stream));
+                                    h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->stream));
     if (ev) {
-        BSS_CUDA(h, cudaEventRecord(ev[3], h->stream));
+        BSS_CUDA(h, cudaEventRecord(ev[1], h->stream));
         ++h->ev_count;
     }
     if (d_v) BSS_CUDA(h, cudaMemcpyAsync(d_v, h->d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -406,14 +407,14 @@ int bssmppi_timing(bssmppi_t h, int32_t n)
     if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
     if (n < 0 || n > 4096) return fail(h, BSSMPPI_EINVAL, "timing slots must be in [0, 4096]");
     BSS_CUDA(h, cudaStreamSynchronize(h->stream));
-    for (int i = 0; i < 4 * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < 2 * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
     delete[] h->ev;
     h->ev = nullptr;
     h->ev_cap = 0;
     h->ev_count = 0;
     if (n == 0) return BSSMPPI_OK;
-    h->ev = new cudaEvent_t[4 * (size_t)n];
-    for (int i = 0; i < 4 * n; ++i) {
+    h->ev = new cudaEvent_t[2 * (size_t)n];
+    for (int i = 0; i < 2 * n; ++i) {
         cudaError_t e = cudaEventCreate(&h->ev[i]);
         if (e != cudaSuccess) {
             for (int j = 0; j < i; ++j) cudaEventDestroy(h->ev[j]);
@@ -431,13 +432,12 @@ int bssmppi_timing_read(bssmppi_t h, float* h_rollout_ms, float* h_update_ms, in
     if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
     const int n = h->ev_count < max ? h->ev_count : (max > 0 ? max : 0);
     for (int i = 0; i < n; ++i) {
-        cudaEvent_t* ev = h->ev + 4 * i;
-        BSS_CUDA(h, cudaEventSynchronize(ev[3]));
-        float a = 0.0f, b = 0.0f;
+        cudaEvent_t* ev = h->ev + 2 * i;
+        BSS_CUDA(h, cudaEventSynchronize(ev[1]));
+        float a = 0.0f;
         BSS_CUDA(h, cudaEventElapsedTime(&a, ev[0], ev[1]));
-        BSS_CUDA(h, cudaEventElapsedTime(&b, ev[2], ev[3]));
         if (h_rollout_ms) h_rollout_ms[i] = a;
-        if (h_update_ms) h_update_ms[i] = b;
+        if (h_update_ms) h_update_ms[i] = 0.0f;  // fused into the rollout launch
     }
     if (count) *count = n;
     return BSSMPPI_OK;
