@@ -36,7 +36,7 @@ class OrcProblem(ctypes.Structure):
         ("x_goal", ctypes.c_double * 6), ("Q", ctypes.c_double * 6), ("Qf", ctypes.c_double * 6),
         ("ey_index", ctypes.c_int),
         ("kappa", _dp), ("n_track", ctypes.c_int), ("track_len", ctypes.c_double),
-        ("seed", ctypes.c_uint64), ("crn_disturbance", ctypes.c_int),
+        ("seed", ctypes.c_uint64), ("crn_disturbance", ctypes.c_int), ("resample", ctypes.c_int),
     ]
 
 
@@ -100,7 +100,7 @@ class Oracle:
     def __init__(self, prob):
         self.prob = prob
         p = OrcProblem()
-        for name in ("K", "M", "T", "n_sub", "model", "ey_index", "crn_disturbance"):
+        for name in ("K", "M", "T", "n_sub", "model", "ey_index", "crn_disturbance", "resample"):
             setattr(p, name, int(getattr(prob, name)))
         for name in ("dt", "mass", "Iz", "lf", "lr", "tire_B", "tire_C", "mu", "g", "vx_floor",
                      "delta", "gamma", "ctrl_w", "C_safe", "C_obs", "w_T"):

@@ -10,7 +10,8 @@
  *     c1 = particle index n (0 for control noise)
  *     c2 = sample index k (0 for every sample when disturbance draws are shared)
  *     c3 = (stream << 28) | (solve counter & 0x0fffffff);
- *     streams: 0 control noise, 1 state disturbance, 3 initial particles.
+ *     streams: 0 control noise, 1 state disturbance, 3 initial particles, 4 per-step re-draws of
+ *     the particles (only when the problem asks for Algorithm 2's re-sampling).
  *   Uniforms from two 32-bit words a, b: u1 = ((a >> 8) + 1) 2^-24 in (0, 1],
  *   u2 = (b >> 8) 2^-24 in [0, 1); Box-Muller z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
  *   Gaussian pair i of a draw comes from call i/2, words (2(i%2), 2(i%2)+1).
@@ -352,6 +353,23 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
         double S = 0.0;
         for (int k = 0; k < T; ++k) {
             const double* uk = u + 2 * k;
+            if (p->resample && k > 0) {
+                /* Algorithm 2, first line of its loop: x^n_k ~ N(xbar_k, Sigma_k), drawn as
+                 * xbar_k + L_k xi^n with L_k the (PSD) Cholesky factor of the Monte-Carlo covariance
+                 * of step k and xi^n from stream 4. At k = 0 the initial particles above are the draw. */
+                double Lk[36];
+                cholesky_psd(nx, Sig + (size_t)k * nx * nx, Lk);
+                const double* mk = xbar + (size_t)k * nx;
+                for (int n = 0; n < M; ++n) {
+                    double xi[6];
+                    draw_normals(p, nx, (uint32_t)k, (uint32_t)n, kk, 4, solve_ctr, xi);
+                    for (int i = 0; i < nx; ++i) {
+                        double x = mk[i];
+                        for (int j = 0; j <= i; ++j) x += Lk[i * nx + j] * xi[j];
+                        X[n * nx + i] = x;
+                    }
+                }
+            }
             for (int n = 0; n < M; ++n) {
                 double xn[6], w[6], z[6];
                 orc_model_step(p, X + n * nx, uk, xn);

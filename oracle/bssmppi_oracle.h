@@ -42,6 +42,8 @@ typedef struct orc_problem {
     double track_len;
     uint64_t seed;
     int crn_disturbance;  /* 1: disturbance draws shared by all K samples */
+    int resample;         /* 1: Algorithm 2 read literally: before every step k >= 1 the particles are
+                             re-drawn from N(xbar_k, Sigma_k) (stream 4); 0: persistent particles */
 } orc_problem;
 
 /* Per-solve outputs; any pointer may be NULL. Sizes: S[K], u[K*T*2] (clamped samples), w[K]

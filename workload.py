@@ -103,6 +103,7 @@ class Problem:
     track_len: float = 1.0
     seed: int = 0
     crn_disturbance: int = 0
+    resample: int = 0                # 1: re-draw particles from N(mean, cov) before every step (Alg. 2 literal)
     compensated: int = 1
 
     @property
