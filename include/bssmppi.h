@@ -103,7 +103,11 @@ typedef struct bssmppi_params {
     int32_t crn_disturbance; /* 1: disturbance draws shared by all K samples (common random numbers) */
     int32_t compensated;  /* 1: Welford/Chan moments and Kahan sums; 0: naive sums (precision study) */
     int32_t record_moments; /* 1: keep per-step particle means and variances (BSSMPPI_BUF_MEAN/VAR) */
-    int32_t reserved;     /* must be 0 */
+    int32_t resample;     /* 0: persistent particles x^n_{k+1} = f(x^n_k, u_k) + w (Sec. IV-C propagation);
+                             1: Algorithm 2 read literally: before every step k >= 1 the particles are
+                             re-drawn from N(mean_k, Sigma_k), the Monte-Carlo moments of step k (full
+                             covariance, PSD Cholesky), with Philox stream 4. Needs compensated = 1; not
+                             available to the shield repair or the server (BSSMPPI_ENOTSUP there). */
 } bssmppi_params;
 
 typedef struct bssmppi_ctx* bssmppi_t;

@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
         ("Sigma_eps", ctypes.c_double * 4), ("Sigma_w", ctypes.c_double * 36),
         ("seed", ctypes.c_uint64),
         ("crn_disturbance", ctypes.c_int32), ("compensated", ctypes.c_int32),
-        ("record_moments", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("record_moments", ctypes.c_int32), ("resample", ctypes.c_int32),
     ]
 
 
@@ -185,7 +185,7 @@ def make_params(prob, record_moments: bool = False, compensated: bool | None = N
     p.crn_disturbance = int(prob.crn_disturbance)
     p.compensated = int(prob.compensated if compensated is None else compensated)
     p.record_moments = int(record_moments)
-    p.reserved = 0
+    p.resample = int(getattr(prob, "resample", 0))
     return p
 
 

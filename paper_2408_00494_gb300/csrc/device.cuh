@@ -19,6 +19,7 @@ struct DevParams {
     int uniform;      // 1: every lane of a segment holds exactly P valid particles
     int ey, crn, record, n_track_mask;
     int mean_mask;    // bit i: the cost needs the belief mean of state i (always all when recording)
+    int resample;     // 1: particles re-drawn from N(mean, cov) before every step k >= 1 (Algorithm 2 literal)
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];       // Philox round keys k + r W (the key schedule, precomputed)
     float dt, h, inv_m, inv_Iz, lf, lr, tB, tC, Df, Dr, vx_floor;
@@ -69,7 +70,7 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk0, 
 
 // Counter layout of the solve's streams: word 0 = step | (call << 16), word 1 = particle,
 // word 2 = sample, word 3 = (stream << 28) | (solve counter & 0x0fffffff).
-enum : uint32_t { kStreamControl = 0u, kStreamDisturbance = 1u, kStreamInitial = 3u };
+enum : uint32_t { kStreamControl = 0u, kStreamDisturbance = 1u, kStreamInitial = 3u, kStreamResample = 4u };
 
 __device__ __forceinline__ uint4 draw_words(const DevParams& P, uint32_t step, uint32_t call, uint32_t particle,
                                             uint32_t sample, uint32_t stream, uint32_t ctr)

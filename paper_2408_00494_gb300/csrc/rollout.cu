@@ -250,7 +250,7 @@ __device__ __noinline__ void block_partial(const int K, const int T, const int s
 // log-sum-exp partial of its own samples (block_partial), and the last block to arrive (atomic
 // ticket) merges the partials in block order and writes v+ = v + N / eta, u0, the normalised weights,
 // the diagnostics and the counter (tail_merge). No block waits for another.
-template <int MODEL, int P, bool COMP>
+template <int MODEL, int P, bool COMP, bool RS>
 __global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const DevParams dp, const RollIO io,
                                                                        const TailIO tail)
 {
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const De
     float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * TN;
     const int n_groups = (dp.K + dp.spw - 1) / dp.spw;
     for (int group = blockIdx.x * wpb + warp; group < n_groups; group += gridDim.x * wpb)
-        rollout_group<MODEL, P, COMP>(dp, io, kap_s, v_s, my_u, group, ctr);
+        rollout_group<MODEL, P, COMP, RS>(dp, io, kap_s, v_s, my_u, group, ctr);
     __syncthreads();
 
     float* part = tail.part + (size_t)blockIdx.x * (3 + TN);
@@ -304,34 +304,34 @@ size_t rollout_smem_bytes(const DevParams& dp, int wpb)
     return floats * sizeof(float);
 }
 
-template <int MODEL, int P, bool COMP>
+template <int MODEL, int P, bool COMP, bool RS>
 static cudaError_t launch_one(const DevParams& dp, const RollIO& io, const TailIO& tail, const RollLaunch& L,
                               cudaStream_t st)
 {
     if (L.grid > kTailMaxBlocks) return cudaErrorInvalidValue;
-    rollout_kernel<MODEL, P, COMP><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io, tail);
+    rollout_kernel<MODEL, P, COMP, RS><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io, tail);
     return cudaGetLastError();
 }
 
-template <int MODEL, bool COMP>
+template <int MODEL, bool COMP, bool RS>
 static cudaError_t launch_model(const DevParams& dp, const RollIO& io, const TailIO& tail, int P, const RollLaunch& L,
                                 cudaStream_t st)
 {
     switch (P) {
-    case 1: return launch_one<MODEL, 1, COMP>(dp, io, tail, L, st);
-    case 2: return launch_one<MODEL, 2, COMP>(dp, io, tail, L, st);
-    case 4: return launch_one<MODEL, 4, COMP>(dp, io, tail, L, st);
-    case 8: return launch_one<MODEL, 8, COMP>(dp, io, tail, L, st);
+    case 1: return launch_one<MODEL, 1, COMP, RS>(dp, io, tail, L, st);
+    case 2: return launch_one<MODEL, 2, COMP, RS>(dp, io, tail, L, st);
+    case 4: return launch_one<MODEL, 4, COMP, RS>(dp, io, tail, L, st);
+    case 8: return launch_one<MODEL, 8, COMP, RS>(dp, io, tail, L, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // Block shape: one block per SM with w warps, w chosen to minimise the makespan of an issue-bound
 // kernel, ceil(groups / (SMs w)) rounds of w warps each, among the w that fit on an SM.
-template <int MODEL, int P, bool COMP>
+template <int MODEL, int P, bool COMP, bool RS>
 static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
 {
-    auto kern = rollout_kernel<MODEL, P, COMP>;
+    auto kern = rollout_kernel<MODEL, P, COMP, RS>;
     int dev = 0, sms = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -371,22 +371,29 @@ static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
     return cudaSuccess;
 }
 
-template <int MODEL, bool COMP>
+template <int MODEL, bool COMP, bool RS>
 static cudaError_t plan_model(const DevParams& dp, int P, RollLaunch& L)
 {
     switch (P) {
-    case 1: return plan_one<MODEL, 1, COMP>(dp, L);
-    case 2: return plan_one<MODEL, 2, COMP>(dp, L);
-    case 4: return plan_one<MODEL, 4, COMP>(dp, L);
-    case 8: return plan_one<MODEL, 8, COMP>(dp, L);
+    case 1: return plan_one<MODEL, 1, COMP, RS>(dp, L);
+    case 2: return plan_one<MODEL, 2, COMP, RS>(dp, L);
+    case 4: return plan_one<MODEL, 4, COMP, RS>(dp, L);
+    case 8: return plan_one<MODEL, 8, COMP, RS>(dp, L);
     default: return cudaErrorInvalidValue;
     }
 }
 
+// Variants: persistent particles with compensated or naive reductions; re-sampled particles (always
+// with the compensated cost sums; the host rejects re-sampling with naive reductions).
 cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, RollLaunch& L)
 {
-    if (dp.nx == 6) return comp ? plan_model<0, true>(dp, P, L) : plan_model<0, false>(dp, P, L);
-    return comp ? plan_model<1, true>(dp, P, L) : plan_model<1, false>(dp, P, L);
+    if (dp.resample && !comp) return cudaErrorInvalidValue;
+    if (dp.nx == 6) {
+        if (dp.resample) return plan_model<0, true, true>(dp, P, L);
+        return comp ? plan_model<0, true, false>(dp, P, L) : plan_model<0, false, false>(dp, P, L);
+    }
+    if (dp.resample) return plan_model<1, true, true>(dp, P, L);
+    return comp ? plan_model<1, true, false>(dp, P, L) : plan_model<1, false, false>(dp, P, L);
 }
 
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
@@ -394,9 +401,15 @@ cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaun
                            float* var, const TailIO& tail, cudaStream_t st)
 {
     RollIO io{x0, Sigma0, v, ctr, S, eps, mean, var};
-    if (dp.nx == 6)
-        return comp ? launch_model<0, true>(dp, io, tail, P, L, st) : launch_model<0, false>(dp, io, tail, P, L, st);
-    return comp ? launch_model<1, true>(dp, io, tail, P, L, st) : launch_model<1, false>(dp, io, tail, P, L, st);
+    if (dp.resample && !comp) return cudaErrorInvalidValue;
+    if (dp.nx == 6) {
+        if (dp.resample) return launch_model<0, true, true>(dp, io, tail, P, L, st);
+        return comp ? launch_model<0, true, false>(dp, io, tail, P, L, st)
+                    : launch_model<0, false, false>(dp, io, tail, P, L, st);
+    }
+    if (dp.resample) return launch_model<1, true, true>(dp, io, tail, P, L, st);
+    return comp ? launch_model<1, true, false>(dp, io, tail, P, L, st)
+                : launch_model<1, false, false>(dp, io, tail, P, L, st);
 }
 
 // Model step for n independent states, plus an optional additive disturbance (model checks and

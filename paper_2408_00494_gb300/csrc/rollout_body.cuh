@@ -132,6 +132,72 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
     }
 }
 
+// Full belief of one sample for the re-sampling reading of Algorithm 2: every mean and the unbiased
+// covariance (packed lower triangle by rows), in two passes over the segment: the sums give the
+// means, then the centred products are summed. xor-butterfly sums are symmetric in the two partners,
+// so every lane of the segment ends with bit-identical moments.
+template <int NX, int P>
+__device__ __forceinline__ void belief_moments_full(const DevParams& dp, const float (&x)[P][NX], int ls, int seg,
+                                                    float (&mean)[NX], float (&C)[NX * (NX + 1) / 2])
+{
+    float s[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+        s[i] = 0.0f;
+#pragma unroll
+        for (int p = 0; p < P; ++p) s[i] += (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
+    }
+    for (int off = seg >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
+    }
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mean[i] = s[i] * dp.invM;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float c = 0.0f;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float d = (x[p][i] - mean[i]) * (x[p][j] - mean[j]);
+                c += (dp.uniform || ls + seg * p < dp.M) ? d : 0.0f;
+            }
+            C[i * (i + 1) / 2 + j] = c;
+        }
+    }
+    for (int off = seg >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int e = 0; e < NX * (NX + 1) / 2; ++e) C[e] += __shfl_xor_sync(0xffffffffu, C[e], off);
+    }
+#pragma unroll
+    for (int e = 0; e < NX * (NX + 1) / 2; ++e) C[e] *= dp.invM1;
+}
+
+// In-place Cholesky factorisation of a packed (lower, by rows) PSD matrix; a pivot that is not
+// positive leaves a zero column (a direction without spread).
+template <int NX>
+__device__ __forceinline__ void cholesky_packed_psd(float (&C)[NX * (NX + 1) / 2])
+{
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+        float d = C[j * (j + 1) / 2 + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= C[j * (j + 1) / 2 + k] * C[j * (j + 1) / 2 + k];
+        const bool pos = d > 0.0f;
+        const float ljj = pos ? sqrtf(d) : 0.0f;
+        const float inv = pos ? 1.0f / ljj : 0.0f;
+        C[j * (j + 1) / 2 + j] = ljj;
+#pragma unroll
+        for (int i = j + 1; i < NX; ++i) {
+            float t = C[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= C[i * (i + 1) / 2 + k] * C[j * (j + 1) / 2 + k];
+            C[i * (i + 1) / 2 + j] = t * inv;
+        }
+    }
+}
+
 // PSD-tolerant Cholesky factor (lower, row-major) of the caller's initial covariance.
 template <int NX>
 __device__ __forceinline__ void cholesky_psd(const float* A, float (&L)[NX][NX])
@@ -168,8 +234,10 @@ constexpr int roll_max_threads()
 
 // One sample group (the spw samples of one warp): control sequence, rollout, moments, cost.
 // Returns the cost S of the lane's own sample (identical on every lane of its segment); my_u keeps
-// the segment's clamped control sequence u (T x 2) until the warp's next group.
-template <int MODEL, int P, bool COMP>
+// the segment's clamped control sequence u (T x 2) until the warp's next group. RS selects the
+// literal reading of Algorithm 2: full moments every step and the particles re-drawn from
+// N(mean, cov) before the next step.
+template <int MODEL, int P, bool COMP, bool RS = false>
 __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO& io, const float* __restrict__ kap_s,
                                                const float* __restrict__ v_s, float* __restrict__ my_u, int group,
                                                uint32_t ctr)
@@ -282,7 +350,25 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         }
 
         // (a5) belief moments of step t+1, (a6) barrier.
-        belief_moments<NX, EY, P, COMP>(dp, x, ls, seg, dp.record != 0, mean, var);
+        if constexpr (RS) {
+            float C[NX * (NX + 1) / 2];
+            belief_moments_full<NX, P>(dp, x, ls, seg, mean, C);
+#pragma unroll
+            for (int i = 0; i < NX; ++i) var[i] = C[i * (i + 1) / 2 + i];
+            if (t + 1 < dp.T) {  // re-draw x^n_{t+1} ~ N(mean, cov) for the next step (stream 4)
+                cholesky_packed_psd<NX>(C);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    float xi[NX];
+                    draw_normals<NX>(dp, (uint32_t)(t + 1), (uint32_t)(ls + seg * p), kk, kStreamResample, ctr, xi);
+#pragma unroll
+                    for (int i = 0; i < NX; ++i) x[p][i] = mean[i];
+                    add_correlated<NX>(C, xi, x[p]);
+                }
+            }
+        } else {
+            belief_moments<NX, EY, P, COMP>(dp, x, ls, seg, dp.record != 0, mean, var);
+        }
         if constexpr (MODEL == 0) mean[5] += s0;
         h_prev = h_cur;
         h_cur = belief_barrier(dp, mean[EY], var[EY]);

@@ -140,7 +140,8 @@ int validate(const bssmppi_params* p, std::string& why)
     if (!(p->delta > 0.0f && p->delta < 0.5f)) return bad("delta must be in (0, 0.5)");
     if (!(p->gamma > 0.0f && p->gamma < 1.0f)) return bad("gamma must be in (0, 1)");
     if (!(p->w_T > 0.0f)) return bad("w_T must be > 0");
-    if (p->reserved != 0) return bad("reserved must be 0");
+    if (p->resample != 0 && p->resample != 1) return bad("resample must be 0 or 1");
+    if (p->resample && !p->compensated) return bad("resample needs compensated = 1");
     const double* Se = p->Sigma_eps;
     if (!(Se[0] > 0 && Se[3] > 0 && Se[0] * Se[3] - Se[1] * Se[2] > 0 && std::fabs(Se[1] - Se[2]) <= 1e-12 * (Se[0] + Se[3])))
         return bad("Sigma_eps must be symmetric positive definite");
@@ -205,6 +206,7 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.uniform = (p->M == seg * P) ? 1 : 0;
     d.n_sub = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_sub : 1;
     d.ey = p->ey_index; d.crn = p->crn_disturbance ? 1 : 0; d.record = p->record_moments ? 1 : 0;
+    d.resample = p->resample ? 1 : 0;
     d.key0 = (uint32_t)(p->seed & 0xffffffffu); d.key1 = (uint32_t)(p->seed >> 32);
     for (int r = 0; r < 10; ++r) {  // Philox key schedule: k + r (0x9E3779B9, 0xBB67AE85)
         d.rk0[r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
@@ -448,6 +450,7 @@ int bssmppi_repair_grad(bssmppi_t h, const float* d_x0, const float* d_v, float*
     if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
     if (!d_x0 || !d_grad) return fail(h, BSSMPPI_EINVAL, "x0 and grad must be non-NULL");
     if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256");
+    if (h->prm.resample) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates persistent particles (resample = 0)");
     const float* v = d_v ? d_v : h->d_v;
     BSS_CUDA(h, bss::repair_launch(h->dp, d_x0, const_cast<float*>(v), h->d_ctr, h->d_repair_X, d_grad,
                                    d_J ? d_J : h->d_repair_J, 0, 0.0f, h->stream));
@@ -461,6 +464,7 @@ int bssmppi_repair(bssmppi_t h, const float* d_x0, float* d_v, int32_t iters, fl
     if (iters < 1 || iters > 1000) return fail(h, BSSMPPI_EINVAL, "iters must be in [1, 1000]");
     if (!(step >= 0.0f) || !std::isfinite(step)) return fail(h, BSSMPPI_EINVAL, "step must be finite and >= 0");
     if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256");
+    if (h->prm.resample) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates persistent particles (resample = 0)");
     BSS_CUDA(h, bss::repair_launch(h->dp, d_x0, d_v ? d_v : h->d_v, h->d_ctr, h->d_repair_X, nullptr, d_J, iters,
                                    step, h->stream));
     return BSSMPPI_OK;

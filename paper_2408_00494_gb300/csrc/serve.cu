@@ -560,6 +560,7 @@ int bssmppi_server_add_controller(bssmppi_server_t s, const bssmppi_params* p, i
     if (!s || !p || !ctrl_id) return srv_fail(s, BSSMPPI_EINVAL, "NULL argument");
     if (p->model != BSSMPPI_MODEL_BICYCLE6) return srv_fail(s, BSSMPPI_ENOTSUP, "the server runs the bicycle model");
     if (p->record_moments || !p->compensated) return srv_fail(s, BSSMPPI_ENOTSUP, "the server runs compensated solves without recorded moments");
+    if (p->resample) return srv_fail(s, BSSMPPI_ENOTSUP, "the server runs persistent particles (resample = 0)");
     DevParams d{};
     int P = 1;
     std::string why;

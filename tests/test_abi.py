@@ -58,6 +58,11 @@ def test_invalid_parameters_rejected_on_host():
     prm = bssmppi.make_params(p)
     prm.Sigma_w[0] = -1.0
     assert L.bssmppi_create(ctypes.byref(prm), None, ctypes.byref(ctypes.c_void_p())) == -1
+    for resample, compensated in ((2, 1), (1, 0)):  # re-sampling runs with compensated reductions only
+        prm = bssmppi.make_params(p)
+        prm.resample, prm.compensated = resample, compensated
+        assert L.bssmppi_create(ctypes.byref(prm), None, ctypes.byref(ctypes.c_void_p())) == -1
+        assert "resample" in bssmppi.last_error(None)
 
 
 def test_no_cpu_fallback_without_gpu():

@@ -61,7 +61,8 @@ def assert_close(a, b, rtol, atol, what):
     assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} outside tolerance, max err {err.max():.3e}"
 
 
-def check_solve(prob, x0, v, ctr=0, Sigma0=None):
+def check_solve(prob, x0, v, ctr=0, Sigma0=None, mean_atol=None):
+    """mean_atol(ref) may widen the absolute tolerance of the means per state component."""
     o = oracle.Oracle(prob)
     ref = o.solve(x0, v, ctr, Sigma0=Sigma0, want_cov=True)
     g = gpu_solve(prob, x0, v, ctr, Sigma0=Sigma0)
@@ -69,7 +70,7 @@ def check_solve(prob, x0, v, ctr=0, Sigma0=None):
     # control perturbations
     assert_close(g["eps"], ref["eps"], 0.0, 1e-6, "eps_eff")
     # moments of every step
-    assert_close(g["mean"], ref["mean"], 1e-4, 1e-5, "particle means")
+    assert_close(g["mean"], ref["mean"], 1e-4, 1e-5 if mean_atol is None else mean_atol(ref), "particle means")
     ref_var = np.diagonal(ref["cov"], axis1=2, axis2=3)
     for i in range(ref_var.shape[-1]):
         assert_close(g["var"][..., i], ref_var[..., i], 1e-4, 1e-5, f"particle variances of state {i}")
