@@ -20,6 +20,12 @@ _SRC = os.path.join(_HERE, "bssmppi_oracle.c")
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
+class OrcConstraint(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("backoff", ctypes.c_int), ("i", ctypes.c_int), ("j", ctypes.c_int),
+                ("p", ctypes.c_double), ("b", ctypes.c_double), ("a", ctypes.c_double * 6),
+                ("center", ctypes.c_double * 2), ("radius", ctypes.c_double)]
+
+
 class OrcProblem(ctypes.Structure):
     _fields_ = [
         ("K", ctypes.c_int), ("M", ctypes.c_int), ("T", ctypes.c_int), ("n_sub", ctypes.c_int),
@@ -37,6 +43,7 @@ class OrcProblem(ctypes.Structure):
         ("ey_index", ctypes.c_int),
         ("kappa", _dp), ("n_track", ctypes.c_int), ("track_len", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("crn_disturbance", ctypes.c_int), ("resample", ctypes.c_int),
+        ("n_con", ctypes.c_int), ("con", ctypes.POINTER(OrcConstraint)),
     ]
 
 
@@ -125,6 +132,23 @@ class Oracle:
         p.n_track = int(self._kappa.size)
         p.track_len = _f32(prob.track_len)
         p.seed = int(prob.seed) & 0xFFFFFFFFFFFFFFFF
+        cons = list(getattr(prob, "constraints", ()) or ())
+        self._con = (OrcConstraint * max(1, len(cons)))()
+        for q, c in enumerate(cons):
+            oc = self._con[q]
+            oc.kind = {"halfspace": 0, "disk": 1}[c["kind"]]
+            oc.backoff = {"gaussian": 0, "cantelli": 1}[c.get("backoff", "gaussian")]
+            oc.p = _f32(c["p"])
+            if oc.kind == 0:
+                for l in range(6):
+                    oc.a[l] = _f32(c["a"][l]) if l < len(c["a"]) else 0.0
+                oc.b = _f32(c["b"])
+            else:
+                oc.i, oc.j = int(c["i"]), int(c["j"])
+                oc.center[0], oc.center[1] = _f32(c["center"][0]), _f32(c["center"][1])
+                oc.radius = _f32(c["radius"])
+        p.n_con = len(cons)
+        p.con = ctypes.cast(self._con, ctypes.POINTER(OrcConstraint))
         self.p = p
         self.nx = nx
 

@@ -284,7 +284,45 @@ static double belief_h(const orc_problem* p, double nu, const double* mean, cons
     return b * b - mean[e] * mean[e];
 }
 
-/* Running cost, Eq. "CostFunction": (x - x_g)^T Q (x - x_g) + C_obs 1[|e_y| > w_T]. */
+/* c_i(x) of one constraint and its gradient eta = grad c_i(x) (Assumption 1). */
+static double constraint_value(const orc_constraint* c, const double* x, int nx, double* eta)
+{
+    for (int l = 0; l < nx; ++l) eta[l] = 0.0;
+    if (c->kind == 0) {
+        double v = -c->b;
+        for (int l = 0; l < nx; ++l) {
+            v += c->a[l] * x[l];
+            eta[l] = c->a[l];
+        }
+        return v;
+    }
+    double di = x[c->i] - c->center[0], dj = x[c->j] - c->center[1];
+    eta[c->i] = -2.0 * di;
+    eta[c->j] = -2.0 * dj;
+    return c->radius * c->radius - di * di - dj * dj;
+}
+
+/* General belief barrier, Eq. "DCBFchoice0" and Eq. "DCBFchoice": h = min_i h_i with
+ * h_i = -c_i(mean) - nu_i sqrt(eta_i^T Sigma eta_i), eta_i = grad c_i(mean), nu_i from Remark 1. */
+static double general_h(const orc_problem* p, const double* mean, const double* cov, int nx)
+{
+    double h = INFINITY;
+    for (int q = 0; q < p->n_con; ++q) {
+        const orc_constraint* c = p->con + q;
+        double eta[6];
+        double cv = constraint_value(c, mean, nx, eta);
+        double quad = 0.0;
+        for (int a = 0; a < nx; ++a)
+            for (int b = 0; b < nx; ++b) quad += eta[a] * cov[a * nx + b] * eta[b];
+        double nu = c->backoff == 0 ? orc_backoff_gaussian(c->p) : orc_backoff_cantelli(c->p);
+        double hi = -cv - nu * sqrt(fmax(quad, 0.0));
+        if (hi < h) h = hi;
+    }
+    return h;
+}
+
+/* Running cost, Eq. "CostFunction": (x - x_g)^T Q (x - x_g) + C_obs when the mean breaks a
+ * constraint (|e_y| > w_T for the racing barrier; c_i(mean) > 0 for some i for the general set). */
 static double state_cost(const orc_problem* p, const double* W, const double* xm, int nx)
 {
     double c = 0.0;
@@ -292,7 +330,16 @@ static double state_cost(const orc_problem* p, const double* W, const double* xm
         double d = xm[i] - p->x_goal[i];
         c += W[i] * d * d;
     }
-    if (fabs(xm[p->ey_index]) > p->w_T) c += p->C_obs;
+    if (p->n_con == 0) {
+        if (fabs(xm[p->ey_index]) > p->w_T) c += p->C_obs;
+    } else {
+        int broken = 0;
+        for (int q = 0; q < p->n_con; ++q) {
+            double eta[6];
+            if (constraint_value(p->con + q, xm, nx, eta) > 0.0) broken = 1;
+        }
+        if (broken) c += p->C_obs;
+    }
     return c;
 }
 
@@ -349,7 +396,7 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
             u[2 * k + 1] = clampd(v[2 * k + 1] + e1, p->u_min[1], p->u_max[1]);
         }
         /* Roll out: Algorithm 2 propagates the particles, then the augmented cost accumulates. */
-        hz[0] = belief_h(p, nu, xbar, Sig, nx);
+        hz[0] = p->n_con ? general_h(p, xbar, Sig, nx) : belief_h(p, nu, xbar, Sig, nx);
         double S = 0.0;
         for (int k = 0; k < T; ++k) {
             const double* uk = u + 2 * k;
@@ -393,7 +440,7 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
                     for (int n = 0; n < M; ++n) s += (X[n * nx + i] - mk[i]) * (X[n * nx + j] - mk[j]);
                     Sk[i * nx + j] = s / (M - 1);
                 }
-            hz[k + 1] = belief_h(p, nu, mk, Sk, nx);
+            hz[k + 1] = p->n_con ? general_h(p, mk, Sk, nx) : belief_h(p, nu, mk, Sk, nx);
             /* S += q(xbar_k) + ctrl_w v_k^T Sigma_eps^-1 u_k + C_safe(z_k), with h_{-1} = h_0. */
             double vSu = v[2 * k] * (Sinv[0] * uk[0] + Sinv[1] * uk[1])
                        + v[2 * k + 1] * (Sinv[2] * uk[0] + Sinv[3] * uk[1]);
@@ -411,8 +458,16 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
         if (out->margin) {
             double mg = INFINITY;
             for (int k = 0; k <= T; ++k) {
-                double d = fabs(fabs(xbar[(size_t)k * nx + p->ey_index]) - p->w_T);
-                if (d < mg) mg = d;
+                if (p->n_con == 0) {
+                    double d = fabs(fabs(xbar[(size_t)k * nx + p->ey_index]) - p->w_T);
+                    if (d < mg) mg = d;
+                } else {
+                    for (int q = 0; q < p->n_con; ++q) {
+                        double eta[6];
+                        double d = fabs(constraint_value(p->con + q, xbar + (size_t)k * nx, nx, eta));
+                        if (d < mg) mg = d;
+                    }
+                }
             }
             out->margin[m] = mg;
         }

@@ -28,6 +28,16 @@
 extern "C" {
 #endif
 
+/* One constraint c(x) < 0 of the feasible set (Assumption 1) with its chance level p
+ * (Pr(c(x) >= 0) <= p, Eq. "chance_constraint2") and back-off rule (Remark 1).
+ *   kind 0, half-space: c(x) = a^T x - b.
+ *   kind 1, disk obstacle in the plane of states (i, j): c(x) = r^2 - (x_i - o_0)^2 - (x_j - o_1)^2.
+ *   backoff 0: nu = sqrt(2) erfinv(1 - 2p) (Gaussian); 1: nu = sqrt((1 - p) / p) (Cantelli). */
+typedef struct orc_constraint {
+    int kind, backoff, i, j;
+    double p, b, a[6], center[2], radius;
+} orc_constraint;
+
 typedef struct orc_problem {
     int K, M, T, n_sub, model; /* model 0: dynamic bicycle (nx=6); 1: double integrator (nx=4) */
     double dt, mass, Iz, lf, lr, tire_B, tire_C, mu, g, vx_floor;
@@ -44,11 +54,14 @@ typedef struct orc_problem {
     int crn_disturbance;  /* 1: disturbance draws shared by all K samples */
     int resample;         /* 1: Algorithm 2 read literally: before every step k >= 1 the particles are
                              re-drawn from N(xbar_k, Sigma_k) (stream 4); 0: persistent particles */
+    int n_con;            /* 0: the racing barrier of Eq. "DCBF"; > 0: the general set, Eq. "DCBFchoice" */
+    const orc_constraint* con;
 } orc_problem;
 
 /* Per-solve outputs; any pointer may be NULL. Sizes: S[K], u[K*T*2] (clamped samples), w[K]
  * (normalised weights), v_plus[T*2], mean[K*(T+1)*nx], cov[K*(T+1)*nx*nx], margin[K]
- * (min over steps of ||mean e_y| - w_T|), h[K*(T+1)], diag[4] = {beta, eta, ESS, free energy
+ * (min over steps of ||mean e_y| - w_T|, or of |c_i(mean)| over the constraints of a general set),
+ * h[K*(T+1)], diag[4] = {beta, eta, ESS, free energy
  * beta - lambda ln(eta / K)}. */
 typedef struct orc_outputs {
     double *S, *u, *w, *v_plus, *mean, *cov, *margin, *h, *diag;

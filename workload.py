@@ -104,6 +104,7 @@ class Problem:
     seed: int = 0
     crn_disturbance: int = 0
     resample: int = 0                # 1: re-draw particles from N(mean, cov) before every step (Alg. 2 literal)
+    constraints: tuple = ()          # general constraint set (halfspace()/disk() entries); () = racing barrier
     compensated: int = 1
 
     @property
@@ -142,6 +143,17 @@ def double_integrator_problem(K, M, T, q_w=0.01, seed=0, **kw) -> Problem:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def halfspace(a, b, p, backoff="gaussian") -> dict:
+    """Constraint a^T x - b < 0 held with probability 1 - p."""
+    return {"kind": "halfspace", "a": tuple(float(x) for x in a), "b": float(b), "p": float(p), "backoff": backoff}
+
+
+def disk(i, j, center, radius, p, backoff="gaussian") -> dict:
+    """Disk obstacle in the plane of states (i, j): feasible outside, with probability 1 - p."""
+    return {"kind": "disk", "i": int(i), "j": int(j), "center": (float(center[0]), float(center[1])),
+            "radius": float(radius), "p": float(p), "backoff": backoff}
 
 
 def racing_x0(p: Problem) -> np.ndarray:
