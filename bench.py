@@ -447,23 +447,33 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     rep_ms = statistics.fmean(a.elapsed_time(b) for a, b in rep_ev)
 
-    # the literal reading of Algorithm 2 (particles re-drawn from N(mean, cov) before every step) on
-    # the same workload, same L2 flush
+    def time_variant(pv):
+        """Solve + shift of a problem variant on the same state and L2 flush (CUDA events)."""
+        cv = bssmppi.Controller(pv, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.warmup + args.steps):
+            flush.fill_(float(i))
+            if i >= args.warmup:
+                ev[i - args.warmup][0].record(stream)
+            bssmppi.solve(cv.h, x0)
+            bssmppi.shift(cv.h, None, 1)
+            if i >= args.warmup:
+                ev[i - args.warmup][1].record(stream)
+        torch.cuda.synchronize()
+        cv.close()
+        return statistics.fmean(a.elapsed_time(b) for a, b in ev)
+
+    # the literal reading of Algorithm 2 (particles re-drawn from N(mean, cov) before every step)
     p_rs = _problem(args.workload, rank)
     p_rs.resample = 1
-    ctl_rs = bssmppi.Controller(p_rs, stream=stream)
-    rs_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.warmup + args.steps):
-        flush.fill_(float(i))
-        if i >= args.warmup:
-            rs_ev[i - args.warmup][0].record(stream)
-        bssmppi.solve(ctl_rs.h, x0)
-        bssmppi.shift(ctl_rs.h, None, 1)
-        if i >= args.warmup:
-            rs_ev[i - args.warmup][1].record(stream)
-    torch.cuda.synchronize()
-    ctl_rs.close()
-    rs_ms = statistics.fmean(a.elapsed_time(b) for a, b in rs_ev)
+    rs_ms = time_variant(p_rs)
+    # the general constraint set: track edges as two half-spaces and a disk obstacle 6 m ahead
+    p_con = _problem(args.workload, rank)
+    x0_np = workload.racing_x0(p_con)
+    p_con.constraints = (workload.halfspace((0, 0, 0, 0, 1, 0), p_con.w_T, p_con.delta),
+                         workload.halfspace((0, 0, 0, 0, -1, 0), p_con.w_T, p_con.delta),
+                         workload.disk(5, 4, (float(x0_np[5]) + 6.0, 0.3), 1.0, 0.05, backoff="cantelli"))
+    con_ms = time_variant(p_con)
 
     # end to end through the C ABI with host buffers (H2D of the state and nominal, D2H of v+ and u0)
     x0_h = workload.racing_x0(p)
@@ -506,6 +516,9 @@ def run_ours(args, rank, world, local_rank):
         "resample_variant": {"ms_per_step": rs_ms, "particle_steps_per_s": units / (rs_ms * 1e-3),
                              "note": "Algorithm 2 read literally: full moments, Cholesky and re-draw of "
                                      "every particle before each step; solve + shift, same L2 flush"},
+        "constraint_set_variant": {"ms_per_step": con_ms, "particle_steps_per_s": units / (con_ms * 1e-3),
+                                   "note": "general set h = min_q h_q: two track-edge half-spaces and a disk "
+                                           "obstacle on (s, e_y), full covariance every step; solve + shift"},
         "shield_repair": {"iters": args.repair_iters, "step": args.repair_step, "ms_per_step": rep_ms,
                           "repair_ms": rep_ms - mean_ms, "solves_per_s": 1e3 / rep_ms,
                           "particle_steps_per_s": units / (rep_ms * 1e-3),

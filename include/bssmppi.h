@@ -110,6 +110,35 @@ typedef struct bssmppi_params {
                              available to the shield repair or the server (BSSMPPI_ENOTSUP there). */
 } bssmppi_params;
 
+/*
+ * General constraint set (Assumption 1 and Eqs. "chance_constraint2", "deterministic_chance_constraint",
+ * "DCBFchoice0", "DCBFchoice"). Each constraint c_q(x) < 0 is held with probability at least 1 - p_q.
+ * Its deterministic form backs off by nu_q sqrt(eta_q^T Sigma eta_q), with eta_q = grad c_q at the
+ * belief mean and nu_q from Remark 1. The barrier becomes h = min_q [-c_q(mean) - nu_q
+ * sqrt(eta_q^T Sigma eta_q)], with Sigma the full Monte-Carlo covariance. The collision penalty C_obs
+ * is charged when the mean breaks a constraint (some c_q(mean) > 0).
+ */
+#define BSSMPPI_MAX_CONSTRAINTS 8
+typedef enum bssmppi_constraint_kind {
+    BSSMPPI_CON_HALFSPACE = 0, /* c(x) = a^T x - b */
+    BSSMPPI_CON_DISK = 1       /* c(x) = r^2 - (x_i - center_0)^2 - (x_j - center_1)^2: an obstacle */
+} bssmppi_constraint_kind;
+typedef enum bssmppi_backoff {
+    BSSMPPI_BACKOFF_GAUSSIAN = 0, /* nu = sqrt(2) erfinv(1 - 2p), 0 < p < 0.5 */
+    BSSMPPI_BACKOFF_CANTELLI = 1  /* nu = sqrt((1 - p) / p), 0 < p < 1; holds for any distribution */
+} bssmppi_backoff;
+typedef struct bssmppi_constraint {
+    int32_t kind;         /* bssmppi_constraint_kind */
+    int32_t backoff;      /* bssmppi_backoff */
+    int32_t i, j;         /* DISK: the two (distinct) state components of the obstacle's plane */
+    float p;              /* chance level p_q of this constraint */
+    float b;              /* HALFSPACE: offset b */
+    float a[6];           /* HALFSPACE: normal a (entries past nx ignored) */
+    float center[2];      /* DISK: centre in the (x_i, x_j) plane */
+    float radius;         /* DISK: radius r > 0 */
+    int32_t reserved;     /* 0 */
+} bssmppi_constraint;
+
 typedef struct bssmppi_ctx* bssmppi_t;
 
 /* Library identification. bssmppi_params_size() lets bindings check their struct layout. */
@@ -153,6 +182,17 @@ int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, fl
  * d_v [T*2] device sequence, or NULL for the resident one. 0 <= n <= T. Asynchronous.
  */
 int bssmppi_shift(bssmppi_t h, float* d_v, int32_t n);
+
+/*
+ * Replaces the racing barrier of Eq. "DCBF" with the general constraint set `cons[0..n)` (host
+ * array, copied; n <= BSSMPPI_MAX_CONSTRAINTS); n = 0 restores the racing barrier. The back-off
+ * coefficients are computed here in double precision. For the bicycle, s is the absolute path
+ * coordinate of the track (no wrap at the lap). Needs compensated = 1. Waits for the handle's stream,
+ * then selects the full-belief kernel variant (all means and the whole covariance every step).
+ * Returns BSSMPPI_EINVAL for a bad kind, back-off, chance level, disk state pair or non-finite
+ * value, leaving the handle's set unchanged. The shield repair and the server do not use it.
+ */
+int bssmppi_set_constraints(bssmppi_t h, const bssmppi_constraint* cons, int32_t n);
 
 /* Free the handle and its device buffers after waiting for its stream. NULL is accepted. */
 int bssmppi_destroy(bssmppi_t h);

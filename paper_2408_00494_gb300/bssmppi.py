@@ -48,6 +48,16 @@ class Params(ctypes.Structure):
     ]
 
 
+class Constraint(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("backoff", ctypes.c_int32), ("i", ctypes.c_int32), ("j", ctypes.c_int32),
+                ("p", ctypes.c_float), ("b", ctypes.c_float), ("a", ctypes.c_float * 6),
+                ("center", ctypes.c_float * 2), ("radius", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+CON_HALFSPACE, CON_DISK = 0, 1
+BACKOFF_GAUSSIAN, BACKOFF_CANTELLI = 0, 1
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_controllers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("T_max", ctypes.c_int32),
                 ("slots", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32),
@@ -89,6 +99,7 @@ def load(build_if_missing: bool = True):
         "bssmppi_solve": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "bssmppi_solve_host": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "bssmppi_shift": (ctypes.c_int, [vp, vp, i32]),
+        "bssmppi_set_constraints": (ctypes.c_int, [vp, vp, i32]),
         "bssmppi_destroy": (ctypes.c_int, [vp]),
         "bssmppi_last_error": (ctypes.c_char_p, [vp]),
         "bssmppi_set_counter": (ctypes.c_int, [vp, u32]),
@@ -211,6 +222,31 @@ def solve(h, x0, Sigma0=None, v=None, u0=None):
 
 def solve_host(h, x0, Sigma0=None, v=None, u0=None):
     _check(load().bssmppi_solve_host(h, _hptr(x0), _hptr(Sigma0), _hptr(v), _hptr(u0)), h)
+
+
+def make_constraints(cons):
+    """ctypes array of bssmppi_constraint from {"kind": "halfspace" | "disk", ...} descriptions."""
+    arr = (Constraint * max(1, len(cons)))()
+    for q, c in enumerate(cons):
+        k = arr[q]
+        k.kind = {"halfspace": CON_HALFSPACE, "disk": CON_DISK}[c["kind"]]
+        k.backoff = {"gaussian": BACKOFF_GAUSSIAN, "cantelli": BACKOFF_CANTELLI}[c.get("backoff", "gaussian")]
+        k.p = float(c["p"])
+        if k.kind == CON_HALFSPACE:
+            for l, x in enumerate(c["a"]):
+                k.a[l] = float(x)
+            k.b = float(c["b"])
+        else:
+            k.i, k.j = int(c["i"]), int(c["j"])
+            k.center[0], k.center[1] = float(c["center"][0]), float(c["center"][1])
+            k.radius = float(c["radius"])
+    return arr
+
+
+def set_constraints(h, cons):
+    """Selects the general constraint set (an empty list restores the racing barrier)."""
+    cons = list(cons or ())
+    _check(load().bssmppi_set_constraints(h, ctypes.cast(make_constraints(cons), ctypes.c_void_p), len(cons)), h)
 
 
 def shift(h, v=None, n: int = 1):
@@ -337,6 +373,8 @@ class Controller:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.h = create(self.params, self.stream)
         self.nx = prob.nx
+        if getattr(prob, "constraints", ()):
+            set_constraints(self.h, prob.constraints)
 
     def close(self):
         if self.h is not None:

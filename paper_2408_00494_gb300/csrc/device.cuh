@@ -321,6 +321,94 @@ __device__ __forceinline__ float belief_barrier(const DevParams& P, float mean_e
     return b * b - mean_ey * mean_ey;
 }
 
+// General constraint set (Assumption 1): constraints c_q(x) < 0, each held with its own chance
+// level through the back-off nu_q (Remark 1, computed on the host). A kernel parameter of its own,
+// read with constant offsets only (the loops over q are unrolled).
+constexpr int kMaxCon = 8;
+struct ConSet {
+    int n;                  // 0: the racing barrier of Eq. "DCBF"; 1..kMaxCon: this set
+    int kind[kMaxCon];      // 0: half-space a^T x - b; 1: disk r^2 - |D (x - o)|^2 on two states
+    float nu[kMaxCon];      // back-off coefficient
+    float b[kMaxCon];       // half-space offset b; disk: r^2
+    float a[kMaxCon][6];    // half-space normal a; disk: the selector D (1 on its two states)
+    float o[kMaxCon][6];    // disk centre on its two states (0 elsewhere)
+};
+
+// c_q(m) and eta = grad c_q(m).
+template <int NX>
+__device__ __forceinline__ float constraint_value(const ConSet& cs, int q, const float (&m)[NX], float (&eta)[NX])
+{
+    float v;
+    if (cs.kind[q] == 0) {
+        v = -cs.b[q];
+#pragma unroll
+        for (int l = 0; l < NX; ++l) {
+            v = fmaf(cs.a[q][l], m[l], v);
+            eta[l] = cs.a[q][l];
+        }
+    } else {
+        v = cs.b[q];
+#pragma unroll
+        for (int l = 0; l < NX; ++l) {
+            const float d = cs.a[q][l] * (m[l] - cs.o[q][l]);
+            v = fmaf(-d, d, v);
+            eta[l] = -2.0f * d;
+        }
+    }
+    return v;
+}
+
+// Eq. "DCBFchoice0" and Eq. "DCBFchoice": h = min_q -c_q(m) - nu_q sqrt(eta_q^T Sigma eta_q), with the
+// covariance packed (lower triangle by rows).
+template <int NX>
+__device__ __forceinline__ float general_barrier(const ConSet& cs, const float (&m)[NX], const float (&C)[NX * (NX + 1) / 2])
+{
+    float h = INFINITY;
+#pragma unroll
+    for (int q = 0; q < kMaxCon; ++q) {
+        if (q >= cs.n) break;
+        float eta[NX];
+        const float cv = constraint_value<NX>(cs, q, m, eta);
+        float quad = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            float r = 0.5f * C[i * (i + 1) / 2 + i] * eta[i];
+#pragma unroll
+            for (int j = 0; j < i; ++j) r = fmaf(C[i * (i + 1) / 2 + j], eta[j], r);
+            quad = fmaf(2.0f * eta[i], r, quad);
+        }
+        h = fminf(h, -cv - cs.nu[q] * sqrtf(fmaxf(quad, 0.0f)));
+    }
+    return h;
+}
+
+// The collision indicator of Eq. "CostFunction" for the general set: some c_q(m) > 0.
+template <int NX>
+__device__ __forceinline__ bool any_constraint_broken(const ConSet& cs, const float (&m)[NX])
+{
+    bool broken = false;
+#pragma unroll
+    for (int q = 0; q < kMaxCon; ++q) {
+        if (q >= cs.n) break;
+        float eta[NX];
+        broken |= constraint_value<NX>(cs, q, m, eta) > 0.0f;
+    }
+    return broken;
+}
+
+// Quadratic part of the running cost, (m - x_g)^T diag(W) (m - x_g).
+template <int NX>
+__device__ __forceinline__ float quad_cost(const DevParams& P, const float* W, const float (&m)[NX])
+{
+    float c = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+        const float d = m[i] - P.xg[i];
+        c = fmaf(W[i] * d, d, c);
+    }
+    return c;
+}
+
 // Neumaier-compensated accumulation: sum + c carries the sum to about twice the working precision.
 struct CompSum {
     float s = 0.0f, c = 0.0f;

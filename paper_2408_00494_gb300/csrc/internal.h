@@ -8,6 +8,7 @@
 namespace bss {
 
 struct DevParams;
+struct ConSet;
 
 constexpr int kUpdThreads = 512;    // threads per weights/update block
 constexpr int kUpdMaxBlocks = 148;  // upper bound on weights/update blocks (scratch is sized by it)
@@ -31,10 +32,11 @@ struct TailIO {
     float* v_out;           // T*2: v+ (the resident nominal, read by every block first)
 };
 size_t rollout_smem_bytes(const DevParams& dp, int wpb);
-cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, RollLaunch& L);
+// full: the full-belief kernel variant (re-sampled particles and/or a general constraint set).
+cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L);
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
                            const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
-                           float* var, const TailIO& tail, cudaStream_t st);
+                           float* var, const TailIO& tail, const ConSet& cs, cudaStream_t st);
 cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, const float* w, float* xn, int64_t n,
                               cudaStream_t st);
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st);

@@ -250,9 +250,9 @@ __device__ __noinline__ void block_partial(const int K, const int T, const int s
 // log-sum-exp partial of its own samples (block_partial), and the last block to arrive (atomic
 // ticket) merges the partials in block order and writes v+ = v + N / eta, u0, the normalised weights,
 // the diagnostics and the counter (tail_merge). No block waits for another.
-template <int MODEL, int P, bool COMP, bool RS>
+template <int MODEL, int P, bool COMP, bool FULL>
 __global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const DevParams dp, const RollIO io,
-                                                                       const TailIO tail)
+                                                                       const TailIO tail, const ConSet cs)
 {
     extern __shared__ float smem[];
     __shared__ float fac_s[kTailMaxBlocks];
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const De
     float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * TN;
     const int n_groups = (dp.K + dp.spw - 1) / dp.spw;
     for (int group = blockIdx.x * wpb + warp; group < n_groups; group += gridDim.x * wpb)
-        rollout_group<MODEL, P, COMP, RS>(dp, io, kap_s, v_s, my_u, group, ctr);
+        rollout_group<MODEL, P, COMP, FULL>(dp, io, kap_s, v_s, my_u, group, ctr, &cs);
     __syncthreads();
 
     float* part = tail.part + (size_t)blockIdx.x * (3 + TN);
@@ -304,34 +304,34 @@ size_t rollout_smem_bytes(const DevParams& dp, int wpb)
     return floats * sizeof(float);
 }
 
-template <int MODEL, int P, bool COMP, bool RS>
-static cudaError_t launch_one(const DevParams& dp, const RollIO& io, const TailIO& tail, const RollLaunch& L,
-                              cudaStream_t st)
+template <int MODEL, int P, bool COMP, bool FULL>
+static cudaError_t launch_one(const DevParams& dp, const RollIO& io, const TailIO& tail, const ConSet& cs,
+                              const RollLaunch& L, cudaStream_t st)
 {
     if (L.grid > kTailMaxBlocks) return cudaErrorInvalidValue;
-    rollout_kernel<MODEL, P, COMP, RS><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io, tail);
+    rollout_kernel<MODEL, P, COMP, FULL><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io, tail, cs);
     return cudaGetLastError();
 }
 
-template <int MODEL, bool COMP, bool RS>
-static cudaError_t launch_model(const DevParams& dp, const RollIO& io, const TailIO& tail, int P, const RollLaunch& L,
-                                cudaStream_t st)
+template <int MODEL, bool COMP, bool FULL>
+static cudaError_t launch_model(const DevParams& dp, const RollIO& io, const TailIO& tail, const ConSet& cs, int P,
+                                const RollLaunch& L, cudaStream_t st)
 {
     switch (P) {
-    case 1: return launch_one<MODEL, 1, COMP, RS>(dp, io, tail, L, st);
-    case 2: return launch_one<MODEL, 2, COMP, RS>(dp, io, tail, L, st);
-    case 4: return launch_one<MODEL, 4, COMP, RS>(dp, io, tail, L, st);
-    case 8: return launch_one<MODEL, 8, COMP, RS>(dp, io, tail, L, st);
+    case 1: return launch_one<MODEL, 1, COMP, FULL>(dp, io, tail, cs, L, st);
+    case 2: return launch_one<MODEL, 2, COMP, FULL>(dp, io, tail, cs, L, st);
+    case 4: return launch_one<MODEL, 4, COMP, FULL>(dp, io, tail, cs, L, st);
+    case 8: return launch_one<MODEL, 8, COMP, FULL>(dp, io, tail, cs, L, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // Block shape: one block per SM with w warps, w chosen to minimise the makespan of an issue-bound
 // kernel, ceil(groups / (SMs w)) rounds of w warps each, among the w that fit on an SM.
-template <int MODEL, int P, bool COMP, bool RS>
+template <int MODEL, int P, bool COMP, bool FULL>
 static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
 {
-    auto kern = rollout_kernel<MODEL, P, COMP, RS>;
+    auto kern = rollout_kernel<MODEL, P, COMP, FULL>;
     int dev = 0, sms = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -371,45 +371,47 @@ static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
     return cudaSuccess;
 }
 
-template <int MODEL, bool COMP, bool RS>
+template <int MODEL, bool COMP, bool FULL>
 static cudaError_t plan_model(const DevParams& dp, int P, RollLaunch& L)
 {
     switch (P) {
-    case 1: return plan_one<MODEL, 1, COMP, RS>(dp, L);
-    case 2: return plan_one<MODEL, 2, COMP, RS>(dp, L);
-    case 4: return plan_one<MODEL, 4, COMP, RS>(dp, L);
-    case 8: return plan_one<MODEL, 8, COMP, RS>(dp, L);
+    case 1: return plan_one<MODEL, 1, COMP, FULL>(dp, L);
+    case 2: return plan_one<MODEL, 2, COMP, FULL>(dp, L);
+    case 4: return plan_one<MODEL, 4, COMP, FULL>(dp, L);
+    case 8: return plan_one<MODEL, 8, COMP, FULL>(dp, L);
     default: return cudaErrorInvalidValue;
     }
 }
 
-// Variants: persistent particles with compensated or naive reductions; re-sampled particles (always
-// with the compensated cost sums; the host rejects re-sampling with naive reductions).
-cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, RollLaunch& L)
+// Variants: the racing barrier on persistent particles, with compensated or naive reductions; and
+// the full-belief variant (re-sampled particles and/or the general constraint set), always with
+// the compensated sums (the host rejects it with naive reductions).
+cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L)
 {
-    if (dp.resample && !comp) return cudaErrorInvalidValue;
+    if (full && !comp) return cudaErrorInvalidValue;
     if (dp.nx == 6) {
-        if (dp.resample) return plan_model<0, true, true>(dp, P, L);
+        if (full) return plan_model<0, true, true>(dp, P, L);
         return comp ? plan_model<0, true, false>(dp, P, L) : plan_model<0, false, false>(dp, P, L);
     }
-    if (dp.resample) return plan_model<1, true, true>(dp, P, L);
+    if (full) return plan_model<1, true, true>(dp, P, L);
     return comp ? plan_model<1, true, false>(dp, P, L) : plan_model<1, false, false>(dp, P, L);
 }
 
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
                            const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
-                           float* var, const TailIO& tail, cudaStream_t st)
+                           float* var, const TailIO& tail, const ConSet& cs, cudaStream_t st)
 {
     RollIO io{x0, Sigma0, v, ctr, S, eps, mean, var};
-    if (dp.resample && !comp) return cudaErrorInvalidValue;
+    const bool full = dp.resample || cs.n > 0;
+    if (full && !comp) return cudaErrorInvalidValue;
     if (dp.nx == 6) {
-        if (dp.resample) return launch_model<0, true, true>(dp, io, tail, P, L, st);
-        return comp ? launch_model<0, true, false>(dp, io, tail, P, L, st)
-                    : launch_model<0, false, false>(dp, io, tail, P, L, st);
+        if (full) return launch_model<0, true, true>(dp, io, tail, cs, P, L, st);
+        return comp ? launch_model<0, true, false>(dp, io, tail, cs, P, L, st)
+                    : launch_model<0, false, false>(dp, io, tail, cs, P, L, st);
     }
-    if (dp.resample) return launch_model<1, true, true>(dp, io, tail, P, L, st);
-    return comp ? launch_model<1, true, false>(dp, io, tail, P, L, st)
-                : launch_model<1, false, false>(dp, io, tail, P, L, st);
+    if (full) return launch_model<1, true, true>(dp, io, tail, cs, P, L, st);
+    return comp ? launch_model<1, true, false>(dp, io, tail, cs, P, L, st)
+                : launch_model<1, false, false>(dp, io, tail, cs, P, L, st);
 }
 
 // Model step for n independent states, plus an optional additive disturbance (model checks and

@@ -234,13 +234,14 @@ constexpr int roll_max_threads()
 
 // One sample group (the spw samples of one warp): control sequence, rollout, moments, cost.
 // Returns the cost S of the lane's own sample (identical on every lane of its segment); my_u keeps
-// the segment's clamped control sequence u (T x 2) until the warp's next group. RS selects the
-// literal reading of Algorithm 2: full moments every step and the particles re-drawn from
-// N(mean, cov) before the next step.
-template <int MODEL, int P, bool COMP, bool RS = false>
+// the segment's clamped control sequence u (T x 2) until the warp's next group. FULL selects the
+// full-belief variant: every mean and the whole covariance each step, which the general constraint
+// set (cs->n > 0, Eq. "DCBFchoice") and the literal reading of Algorithm 2 (dp.resample: particles
+// re-drawn from N(mean, cov) before the next step) need; cs is read only by it.
+template <int MODEL, int P, bool COMP, bool FULL = false>
 __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO& io, const float* __restrict__ kap_s,
                                                const float* __restrict__ v_s, float* __restrict__ my_u, int group,
-                                               uint32_t ctr)
+                                               uint32_t ctr, const ConSet* cs = nullptr)
 {
     constexpr int NX = MODEL == 0 ? 6 : 4;
     constexpr int EY = MODEL == 0 ? 4 : 1;
@@ -306,7 +307,23 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
     float mean[NX], var[NX];
 #pragma unroll
     for (int i = 0; i < NX; ++i) mean[i] = x0[i];
-    float h_cur = belief_barrier(dp, mean[EY], var0_ey);
+    bool general = false;
+    float h_cur;
+    if constexpr (FULL) {
+        general = cs->n > 0;
+        if (general) {
+            float C0[NX * (NX + 1) / 2];
+#pragma unroll
+            for (int i = 0; i < NX; ++i)
+#pragma unroll
+                for (int j = 0; j <= i; ++j) C0[i * (i + 1) / 2 + j] = io.Sigma0 ? io.Sigma0[i * NX + j] : 0.0f;
+            h_cur = general_barrier<NX>(*cs, mean, C0);
+        } else {
+            h_cur = belief_barrier(dp, mean[EY], var0_ey);
+        }
+    } else {
+        h_cur = belief_barrier(dp, mean[EY], var0_ey);
+    }
     float h_prev = h_cur;
     const bool writer = active && ls == 0;
     if (dp.record && writer) {
@@ -325,7 +342,14 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         const float v0 = v_s[2 * t], v1 = v_s[2 * t + 1];
         const float ctrl = dp.ctrl_w * (v0 * fmaf(dp.Si00, u0, dp.Si01 * u1) + v1 * fmaf(dp.Si10, u0, dp.Si11 * u1));
         const float csafe = dp.Csafe * fmaxf(fmaf(dp.one_m_gamma, h_prev, -h_cur), 0.0f);
-        const float term = state_cost<NX>(dp, dp.Q, mean) + ctrl + csafe;
+        float q;
+        if constexpr (FULL) {
+            q = general ? quad_cost<NX>(dp, dp.Q, mean) + (any_constraint_broken<NX>(*cs, mean) ? dp.Cobs : 0.0f)
+                        : state_cost<NX>(dp, dp.Q, mean);
+        } else {
+            q = state_cost<NX>(dp, dp.Q, mean);
+        }
+        const float term = q + ctrl + csafe;
         if constexpr (COMP) S.add(term); else S_naive += term;
 
         // (a3, a4) propagate every particle: x <- f(x, u_t) + L_w z.
@@ -350,12 +374,20 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         }
 
         // (a5) belief moments of step t+1, (a6) barrier.
-        if constexpr (RS) {
+        float h_next = 0.0f;
+        if constexpr (FULL) {
             float C[NX * (NX + 1) / 2];
             belief_moments_full<NX, P>(dp, x, ls, seg, mean, C);
 #pragma unroll
             for (int i = 0; i < NX; ++i) var[i] = C[i * (i + 1) / 2 + i];
-            if (t + 1 < dp.T) {  // re-draw x^n_{t+1} ~ N(mean, cov) for the next step (stream 4)
+            if (general) {
+                float ma[NX];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) ma[i] = mean[i];
+                if constexpr (MODEL == 0) ma[5] += s0;
+                h_next = general_barrier<NX>(*cs, ma, C);
+            }
+            if (dp.resample && t + 1 < dp.T) {  // re-draw x^n_{t+1} ~ N(mean, cov) for the next step (stream 4)
                 cholesky_packed_psd<NX>(C);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
@@ -371,7 +403,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         }
         if constexpr (MODEL == 0) mean[5] += s0;
         h_prev = h_cur;
-        h_cur = belief_barrier(dp, mean[EY], var[EY]);
+        h_cur = general ? h_next : belief_barrier(dp, mean[EY], var[EY]);
         if (dp.record && writer) {
             const size_t base = ((size_t)k * (dp.T + 1) + t + 1) * NX;
 #pragma unroll
@@ -382,7 +414,14 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         }
     }
     // Terminal: phi(x_bar_T) + C_safe(z_T).
-    const float term = state_cost<NX>(dp, dp.Qf, mean) + dp.Csafe * fmaxf(fmaf(dp.one_m_gamma, h_prev, -h_cur), 0.0f);
+    float qT;
+    if constexpr (FULL) {
+        qT = general ? quad_cost<NX>(dp, dp.Qf, mean) + (any_constraint_broken<NX>(*cs, mean) ? dp.Cobs : 0.0f)
+                     : state_cost<NX>(dp, dp.Qf, mean);
+    } else {
+        qT = state_cost<NX>(dp, dp.Qf, mean);
+    }
+    const float term = qT + dp.Csafe * fmaxf(fmaf(dp.one_m_gamma, h_prev, -h_cur), 0.0f);
     float total;
     if constexpr (COMP) {
         S.add(term);

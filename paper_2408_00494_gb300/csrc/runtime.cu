@@ -14,6 +14,7 @@ struct bssmppi_ctx {
     bss::DevParams dp{};
     int P = 1;            // particles per lane (1, 2, 4 or 8)
     bss::RollLaunch roll; // persistent rollout launch shape
+    bss::ConSet cons{};   // general constraint set (n = 0: the racing barrier)
     int nx = 6;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -35,7 +36,7 @@ struct bssmppi_ctx {
     float* d_repair_X = nullptr;  // stored particle states of the repair rollout
     float* d_repair_J = nullptr;  // objective of the last repair_grad call
     float* h_stage = nullptr;   // pinned host staging: x0 | Sigma0 | v | u0
-    // per-phase timing ring: 4 events per recorded solve
+    // timing ring: 2 events per recorded solve
     cudaEvent_t* ev = nullptr;
     int ev_cap = 0, ev_count = 0;
     std::string err;
@@ -321,7 +322,7 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
         if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMemset(h->d_ticket, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(h->d_diag, 0, sizeof(float) * BSSMPPI_NDIAG);
-        if (e == cudaSuccess) e = bss::rollout_prepare(h->dp, h->P, p->compensated != 0, h->roll);
+        if (e == cudaSuccess) e = bss::rollout_prepare(h->dp, h->P, p->compensated != 0, h->dp.resample != 0, h->roll);
         if (e == cudaSuccess) e = bss::repair_prepare(h->dp);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = cuda_fail(h, e, "create");
@@ -348,7 +349,7 @@ int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* 
     // One launch: rollout, costs, and (in its tail) weights, update, u0, diagnostics, counter.
     bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, h->d_ctr, h->d_v};
     BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, h->d_v, h->d_ctr,
-                                    h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->stream));
+                                    h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, h->stream));
     if (ev) {
         BSS_CUDA(h, cudaEventRecord(ev[1], h->stream));
         ++h->ev_count;
@@ -383,6 +384,59 @@ int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, fl
     BSS_CUDA(h, cudaStreamSynchronize(h->stream));
     if (h_v) std::memcpy(h_v, sv, sizeof(float) * 2 * T);
     if (h_u0) std::memcpy(h_u0, su0, sizeof(float) * 2);
+    return BSSMPPI_OK;
+}
+
+int bssmppi_set_constraints(bssmppi_t h, const bssmppi_constraint* cons, int32_t n)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (n < 0 || n > BSSMPPI_MAX_CONSTRAINTS) return fail(h, BSSMPPI_EINVAL, "constraint count must be in [0, 8]");
+    if (n > 0 && !cons) return fail(h, BSSMPPI_EINVAL, "constraints are NULL");
+    if (n > 0 && !h->prm.compensated) return fail(h, BSSMPPI_EINVAL, "a constraint set needs compensated = 1");
+    bss::ConSet cs{};
+    cs.n = n;
+    for (int q = 0; q < n; ++q) {
+        const bssmppi_constraint& c = cons[q];
+        const double pq = c.p;
+        if (c.backoff == BSSMPPI_BACKOFF_GAUSSIAN) {
+            if (!(pq > 0.0 && pq < 0.5)) return fail(h, BSSMPPI_EINVAL, "Gaussian back-off needs 0 < p < 0.5");
+            cs.nu[q] = (float)(std::sqrt(2.0) * inverse_erf(1.0 - 2.0 * pq));
+        } else if (c.backoff == BSSMPPI_BACKOFF_CANTELLI) {
+            if (!(pq > 0.0 && pq < 1.0)) return fail(h, BSSMPPI_EINVAL, "Cantelli back-off needs 0 < p < 1");
+            cs.nu[q] = (float)std::sqrt((1.0 - pq) / pq);
+        } else {
+            return fail(h, BSSMPPI_EINVAL, "unknown back-off rule");
+        }
+        if (c.kind == BSSMPPI_CON_HALFSPACE) {
+            cs.kind[q] = 0;
+            cs.b[q] = c.b;
+            for (int l = 0; l < 6; ++l) {
+                if (!std::isfinite(c.a[l])) return fail(h, BSSMPPI_EINVAL, "half-space normal must be finite");
+                cs.a[q][l] = l < h->nx ? c.a[l] : 0.0f;
+            }
+            if (!std::isfinite(c.b)) return fail(h, BSSMPPI_EINVAL, "half-space offset must be finite");
+        } else if (c.kind == BSSMPPI_CON_DISK) {
+            if (c.i < 0 || c.i >= h->nx || c.j < 0 || c.j >= h->nx || c.i == c.j)
+                return fail(h, BSSMPPI_EINVAL, "disk states i, j must be distinct states");
+            if (!(c.radius > 0.0f) || !std::isfinite(c.radius) || !std::isfinite(c.center[0]) ||
+                !std::isfinite(c.center[1]))
+                return fail(h, BSSMPPI_EINVAL, "disk radius must be positive and its centre finite");
+            cs.kind[q] = 1;
+            cs.b[q] = c.radius * c.radius;
+            cs.a[q][c.i] = 1.0f;
+            cs.a[q][c.j] = 1.0f;
+            cs.o[q][c.i] = c.center[0];
+            cs.o[q][c.j] = c.center[1];
+        } else {
+            return fail(h, BSSMPPI_EINVAL, "unknown constraint kind");
+        }
+    }
+    bss::RollLaunch L;
+    const bool full = h->dp.resample != 0 || n > 0;
+    BSS_CUDA(h, cudaStreamSynchronize(h->stream));  // no solve may still read the old set's launch shape
+    BSS_CUDA(h, bss::rollout_prepare(h->dp, h->P, h->prm.compensated != 0, full, L));
+    h->roll = L;
+    h->cons = cs;
     return BSSMPPI_OK;
 }
 
@@ -451,6 +505,7 @@ int bssmppi_repair_grad(bssmppi_t h, const float* d_x0, const float* d_v, float*
     if (!d_x0 || !d_grad) return fail(h, BSSMPPI_EINVAL, "x0 and grad must be non-NULL");
     if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256");
     if (h->prm.resample) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates persistent particles (resample = 0)");
+    if (h->cons.n > 0) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates the racing barrier (no constraint set)");
     const float* v = d_v ? d_v : h->d_v;
     BSS_CUDA(h, bss::repair_launch(h->dp, d_x0, const_cast<float*>(v), h->d_ctr, h->d_repair_X, d_grad,
                                    d_J ? d_J : h->d_repair_J, 0, 0.0f, h->stream));
@@ -465,6 +520,7 @@ int bssmppi_repair(bssmppi_t h, const float* d_x0, float* d_v, int32_t iters, fl
     if (!(step >= 0.0f) || !std::isfinite(step)) return fail(h, BSSMPPI_EINVAL, "step must be finite and >= 0");
     if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256");
     if (h->prm.resample) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates persistent particles (resample = 0)");
+    if (h->cons.n > 0) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates the racing barrier (no constraint set)");
     BSS_CUDA(h, bss::repair_launch(h->dp, d_x0, d_v ? d_v : h->d_v, h->d_ctr, h->d_repair_X, nullptr, d_J, iters,
                                    step, h->stream));
     return BSSMPPI_OK;
