@@ -84,6 +84,8 @@ def lib():
                                   ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrcOutputs)]
         L.orc_optimal_control.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp,
                                           _dp, _dp, _dp]
+        L.orc_lse_partial.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+        L.orc_lse_merge.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
         L.orc_solve.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, _dp, ctypes.c_uint32,
                                 ctypes.POINTER(OrcOutputs)]
         L.orc_repair_objective.restype = ctypes.c_double
@@ -214,6 +216,26 @@ def optimal_control(S, u, lam):
     diag = np.zeros(4)
     lib().orc_optimal_control(K, T, float(lam), _ptr(S), _ptr(u), _ptr(w), _ptr(vp), _ptr(diag))
     return w, vp, diag
+
+
+def lse_partial(S, u, lam, k_range):
+    """Log-sum-exp partial {beta, eta, q, U[2T]} of the samples k_range = (k0, k1)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    T = u.shape[1]
+    part = np.zeros(3 + 2 * T)
+    lib().orc_lse_partial(int(k_range[0]), int(k_range[1]), T, float(lam), _ptr(S), _ptr(u), _ptr(part))
+    return part
+
+
+def lse_merge(parts, lam, K_total):
+    """Merge of G partials (rows of parts) into (v+ [T, 2], diag[4])."""
+    parts = np.ascontiguousarray(parts, dtype=np.float64)
+    G, n = parts.shape
+    T = (n - 3) // 2
+    vp, diag = np.zeros((T, 2)), np.zeros(4)
+    lib().orc_lse_merge(G, T, float(lam), int(K_total), _ptr(parts), _ptr(vp), _ptr(diag))
+    return vp, diag
 
 
 def philox(ctr, key):

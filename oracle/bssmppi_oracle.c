@@ -503,6 +503,45 @@ void orc_optimal_control(int K, int T, double lambda, const double* S, const dou
     free(om);
 }
 
+/* Eq. "Weights" and Eq. "MPPI update law" restricted to the samples [k_begin, k_end): the
+ * log-sum-exp partial {beta_g = min S, eta_g = sum omega, q_g = sum omega^2, U_g[2T] = sum omega u}
+ * with omega = exp(-(S - beta_g)/lambda) over that subset. */
+void orc_lse_partial(int k_begin, int k_end, int T, double lambda, const double* S, const double* u, double* part)
+{
+    double beta = INFINITY;
+    for (int m = k_begin; m < k_end; ++m) if (S[m] < beta) beta = S[m];
+    double eta = 0.0, q = 0.0;
+    for (int i = 0; i < 2 * T; ++i) part[3 + i] = 0.0;
+    for (int m = k_begin; m < k_end; ++m) {
+        double om = exp(-(S[m] - beta) / lambda);
+        eta += om;
+        q += om * om;
+        for (int i = 0; i < 2 * T; ++i) part[3 + i] += om * u[(size_t)m * 2 * T + i];
+    }
+    part[0] = beta; part[1] = eta; part[2] = q;
+}
+
+/* Merge of G partials (a disjoint cover of the samples): beta = min_g beta_g, each partial rescaled
+ * by f_g = exp(-(beta_g - beta)/lambda), eta = sum f_g eta_g, v+ = sum f_g U_g / eta; diag as in
+ * orc_optimal_control with K_total samples (ESS = eta^2 / sum f_g^2 q_g). */
+void orc_lse_merge(int G, int T, double lambda, int K_total, const double* parts, double* v_plus, double* diag)
+{
+    const int stride = 3 + 2 * T;
+    double beta = INFINITY;
+    for (int g = 0; g < G; ++g) if (parts[g * stride] < beta) beta = parts[g * stride];
+    double eta = 0.0, q = 0.0;
+    for (int i = 0; i < 2 * T; ++i) v_plus[i] = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double* pg = parts + (size_t)g * stride;
+        double f = exp(-(pg[0] - beta) / lambda);
+        eta += f * pg[1];
+        q += f * f * pg[2];
+        for (int i = 0; i < 2 * T; ++i) v_plus[i] += f * pg[3 + i];
+    }
+    for (int i = 0; i < 2 * T; ++i) v_plus[i] /= eta;
+    if (diag) { diag[0] = beta; diag[1] = eta; diag[2] = eta * eta / q; diag[3] = beta - lambda * log(eta / K_total); }
+}
+
 int orc_solve(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
               uint32_t solve_ctr, const orc_outputs* out)
 {

@@ -82,6 +82,11 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
 /* OptimalControl: weights and v+ = sum w u / sum w from costs S[K] and clamped samples u. */
 void orc_optimal_control(int K, int T, double lambda, const double* S, const double* u,
                          double* w, double* v_plus, double* diag);
+/* The weights/update split over disjoint sample subsets (one per GPU when K is sharded):
+ * part[3 + 2T] = {beta_g, eta_g, q_g = sum omega^2, U_g[2T] = sum omega u} of samples [k_begin, k_end),
+ * and the merge of G such partials into v+ and diag (K_total samples in all). */
+void orc_lse_partial(int k_begin, int k_end, int T, double lambda, const double* S, const double* u, double* part);
+void orc_lse_merge(int G, int T, double lambda, int K_total, const double* parts, double* v_plus, double* diag);
 /* Full solve = orc_rollout over all samples + orc_optimal_control. Returns 0 or -1 (bad args). */
 int orc_solve(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
               uint32_t solve_ctr, const orc_outputs* out);

@@ -233,3 +233,21 @@ def test_repair_adjoint_matches_central_differences(model):
         fd = (o.repair_objective(x0, v + eps * e, 3, grad=False)
               - o.repair_objective(x0, v - eps * e, 3, grad=False)) / (2 * eps)
         assert g[t, j] == pytest.approx(fd, rel=2e-5, abs=1e-6 * abs(J))
+
+
+@pytest.mark.parametrize("cuts", [(), (1,), (37, 38, 100), (5, 17, 64, 65, 90, 120)])
+def test_lse_partials_merge_to_the_full_update(cuts):
+    """Splitting the samples into disjoint groups, taking each group's log-sum-exp partial and
+    merging them reproduces the weights' normaliser and the update of the whole set (the exchange a
+    sample-sharded solve makes), including groups whose best cost is far above the global best."""
+    rng = np.random.default_rng(len(cuts))
+    K, T, lam = 128, 6, 0.1
+    S = rng.uniform(0.0, 50.0, K)
+    S[90:] += 1e4  # a group that the merge rescales by exp(-1e5) (underflows to 0 weight)
+    u = rng.normal(size=(K, T, 2))
+    edges = (0,) + tuple(cuts) + (K,)
+    parts = np.array([oracle.lse_partial(S, u, lam, (a, b)) for a, b in zip(edges[:-1], edges[1:])])
+    vp, diag = oracle.lse_merge(parts, lam, K)
+    w_ref, vp_ref, diag_ref = oracle.optimal_control(S, u, lam)
+    np.testing.assert_allclose(vp, vp_ref, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(diag, diag_ref, rtol=1e-12)
