@@ -194,6 +194,35 @@ int bssmppi_shift(bssmppi_t h, float* d_v, int32_t n);
  */
 int bssmppi_set_constraints(bssmppi_t h, const bssmppi_constraint* cons, int32_t n);
 
+/*
+ * Sample-sharded solve: G handles (typically one per GPU) split the K_total samples of one solve
+ * into disjoint ranges. All have the same parameters, seed, nominal, state and counter. Samples
+ * are independent until the weights (Eq. "Weights"), so each shard rolls out its own range and
+ * reduces it to a log-sum-exp partial of 3 + 2T floats {beta_g = min S, eta_g = sum omega,
+ * q_g = sum omega^2, N_g = sum omega eps_eff}, with omega = exp(-(S - beta_g)/lambda). One
+ * exchange of the partials (an all-gather of (3 + 2T) G floats) and a merge give every shard the
+ * whole solve's update: beta = min beta_g, f_g = exp(-(beta_g - beta)/lambda),
+ * v+ = v + sum f_g N_g / sum f_g eta_g (Eq. "MPPI update law").
+ *
+ * bssmppi_set_sample_range: this handle's K samples are samples [k_begin, k_begin + K) of K_total;
+ * their random streams are keyed by the global sample index, so the shards together draw exactly
+ * the numbers one handle with K_total samples would draw. Waits for the handle's stream.
+ * BSSMPPI_EINVAL unless 0 <= k_begin, k_begin + K <= K_total <= BSSMPPI_K_MAX.
+ *
+ * bssmppi_solve_partial: as bssmppi_solve, but writes the partial to d_partial (device, 3 + 2T
+ * floats) and leaves v, u0, the weights and the diagnostics unchanged; the counter advances.
+ * d_v (device, T*2, or NULL for the resident nominal) is the nominal the shard samples around.
+ * Asynchronous.
+ *
+ * bssmppi_merge_partials: merges G partials (device, G x (3 + 2T) floats; G <= 256) into the
+ * resident nominal (and d_v, device T*2, if not NULL), u0 (d_u0, or the handle's), the diagnostics
+ * (free energy with K_total samples) and the normalised weights of this handle's own samples
+ * (BSSMPPI_BUF_W), from the costs of its last bssmppi_solve_partial. Asynchronous.
+ */
+int bssmppi_set_sample_range(bssmppi_t h, int32_t k_begin, int32_t K_total);
+int bssmppi_solve_partial(bssmppi_t h, const float* d_x0, const float* d_Sigma0, const float* d_v, float* d_partial);
+int bssmppi_merge_partials(bssmppi_t h, const float* d_partials, int32_t G, float* d_v, float* d_u0);
+
 /* Free the handle and its device buffers after waiting for its stream. NULL is accepted. */
 int bssmppi_destroy(bssmppi_t h);
 

@@ -100,6 +100,9 @@ def load(build_if_missing: bool = True):
         "bssmppi_solve_host": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "bssmppi_shift": (ctypes.c_int, [vp, vp, i32]),
         "bssmppi_set_constraints": (ctypes.c_int, [vp, vp, i32]),
+        "bssmppi_set_sample_range": (ctypes.c_int, [vp, i32, i32]),
+        "bssmppi_solve_partial": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "bssmppi_merge_partials": (ctypes.c_int, [vp, vp, i32, vp, vp]),
         "bssmppi_destroy": (ctypes.c_int, [vp]),
         "bssmppi_last_error": (ctypes.c_char_p, [vp]),
         "bssmppi_set_counter": (ctypes.c_int, [vp, u32]),
@@ -247,6 +250,36 @@ def set_constraints(h, cons):
     """Selects the general constraint set (an empty list restores the racing barrier)."""
     cons = list(cons or ())
     _check(load().bssmppi_set_constraints(h, ctypes.cast(make_constraints(cons), ctypes.c_void_p), len(cons)), h)
+
+
+def set_sample_range(h, k_begin: int, K_total: int):
+    _check(load().bssmppi_set_sample_range(h, int(k_begin), int(K_total)), h)
+
+
+def solve_partial(h, x0, Sigma0, v, partial):
+    _check(load().bssmppi_solve_partial(h, _ptr(x0), _ptr(Sigma0), _ptr(v), _ptr(partial)), h)
+
+
+def merge_partials(h, partials, v=None, u0=None):
+    G = partials.shape[0] if partials.dim() > 1 else 1
+    _check(load().bssmppi_merge_partials(h, _ptr(partials), int(G), _ptr(v), _ptr(u0)), h)
+
+
+def sharded_solve(h, x0, T, Sigma0=None, v=None, u0=None, group=None):
+    """One solve whose samples are split over the ranks of a torch.distributed group (each rank's
+    handle covers its range, set with set_sample_range): partial, one all-gather of the partials,
+    merge. Every rank ends with the whole solve's update in its resident nominal (and v, u0)."""
+    import torch
+    import torch.distributed as dist
+    part = torch.empty(3 + 2 * T, dtype=torch.float32, device=x0.device)
+    solve_partial(h, x0, Sigma0, v, part)
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    if world > 1:
+        parts = torch.empty(world, 3 + 2 * T, dtype=torch.float32, device=x0.device)
+        dist.all_gather_into_tensor(parts, part, group=group)
+    else:
+        parts = part.view(1, -1)
+    merge_partials(h, parts, v, u0)
 
 
 def shift(h, v=None, n: int = 1):

@@ -20,6 +20,8 @@ struct DevParams {
     int ey, crn, record, n_track_mask;
     int mean_mask;    // bit i: the cost needs the belief mean of state i (always all when recording)
     int resample;     // 1: particles re-drawn from N(mean, cov) before every step k >= 1 (Algorithm 2 literal)
+    int k_off;        // global index of the handle's first sample (a shard of a larger K); 0 otherwise
+    int K_norm;       // samples of the whole (possibly sharded) solve: K unless sharded
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];       // Philox round keys k + r W (the key schedule, precomputed)
     float dt, h, inv_m, inv_Iz, lf, lr, tB, tC, Df, Dr, vx_floor;

@@ -28,8 +28,10 @@ struct TailIO {
     float* w;               // K normalised weights (out)
     float* u0;              // 2 (out) or nullptr
     float* diag;            // 4 (out) or nullptr
-    uint32_t* ctr_out;      // the solve counter, incremented by the last block
+    uint32_t* ctr_out;      // the solve counter, incremented by the last block (nullptr: left alone)
     float* v_out;           // T*2: v+ (the resident nominal, read by every block first)
+    float* part_out;        // nullptr: apply the update; else write the merged log-sum-exp partial
+                            // (3 + 2T floats: beta, eta, sum omega^2, N) there and leave v, u0, w, diag
 };
 size_t rollout_smem_bytes(const DevParams& dp, int wpb);
 // full: the full-belief kernel variant (re-sampled particles and/or a general constraint set).
@@ -37,6 +39,10 @@ cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, bool full, Ro
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
                            const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
                            float* var, const TailIO& tail, const ConSet& cs, cudaStream_t st);
+// Merge of G log-sum-exp partials (G x (3 + 2T) floats, each {beta, eta, q, N}) into v+ = v + N / eta,
+// u0, the diagnostics (K_norm samples in all) and the normalised weights of the K local costs S.
+cudaError_t merge_partials_launch(const DevParams& dp, int G, const float* parts, bool comp, const float* S,
+                                  const TailIO& tail, cudaStream_t st);
 cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* u, const float* w, float* xn, int64_t n,
                               cudaStream_t st);
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st);

@@ -9,23 +9,27 @@
 
 namespace bss {
 
-// The last block's merge of the block partials (block order; out of line so that its registers
-// do not weigh on the rollout loop). red: max(2T, threads) floats of shared scratch; fac_s, red_e,
-// red_q: one float per block.
+// Merge of G log-sum-exp partials {beta_g, eta_g, q_g, N_g[2T]} (stride 3 + 2T from `part`) in
+// order: the rollout's last block merges its blocks' partials, the merge kernel those of several
+// sample shards. Writes v+ = v + N / eta, u0, the weights of the K local costs S, the diagnostics
+// (K_norm samples in all) and the counter, or, with tail.part_out set, only the merged partial and
+// the counter. Out of line so that its registers do not weigh on the rollout loop. red: max(2T,
+// threads) floats of shared scratch; fac_s, red_e, red_q: G floats each (G <= kTailMaxBlocks).
 constexpr int kTailBatch = 8;  // independent L2 loads a thread keeps in flight in the merge
 
 template <bool COMP>
-__device__ __noinline__ void tail_merge(const int K, const int T, const float lambda, const float inv_lambda,
-                                        const float* S, const TailIO tail, const float* v_s, float* red,
-                                        float* fac_s, float* red_e, float* red_q, float* bc_s)
+__device__ __noinline__ void tail_merge(const int G, const float* part, const int K, const float K_norm, const int T,
+                                        const float lambda, const float inv_lambda, const float* S,
+                                        const TailIO tail, const float* v_s, float* red, float* fac_s, float* red_e,
+                                        float* red_q, float* bc_s)
 {
-    const int G = gridDim.x, tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid / kWarp, lane = tid & (kWarp - 1), wpb = nthr / kWarp;
     const int TN = 2 * T;
     const size_t stride = 3 + TN;
     // beta = min over blocks, then every block's factor exp(-(beta_b - beta)/lambda)
     float b = INFINITY;
-    for (int g = tid; g < G; g += nthr) b = fminf(b, __ldcg(tail.part + g * stride));
+    for (int g = tid; g < G; g += nthr) b = fminf(b, __ldcg(part + g * stride));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) b = fminf(b, __shfl_xor_sync(0xffffffffu, b, off));
     if (lane == 0) red[warp] = b;
@@ -38,11 +42,11 @@ __device__ __noinline__ void tail_merge(const int K, const int T, const float la
     __syncthreads();
     const float beta = bc_s[0];
     for (int g = tid; g < G; g += nthr) {
-        const float bg = __ldcg(tail.part + g * stride);
+        const float bg = __ldcg(part + g * stride);
         const float f = (bg < INFINITY) ? expf((beta - bg) * inv_lambda) : 0.0f;
         fac_s[g] = f;
-        red_e[g] = __ldcg(tail.part + g * stride + 1) * f;
-        red_q[g] = __ldcg(tail.part + g * stride + 2) * f * f;
+        red_e[g] = __ldcg(part + g * stride + 1) * f;
+        red_q[g] = __ldcg(part + g * stride + 2) * f * f;
     }
     __syncthreads();
     if (warp == 0) {  // eta and sum of squares: lane l adds blocks l, l+32, ... then a fixed tree
@@ -81,7 +85,7 @@ __device__ __noinline__ void tail_merge(const int K, const int T, const float la
 #pragma unroll
             for (int j = 0; j < kTailBatch; ++j) {
                 const int g = g0 + j * NG;
-                x[j] = g < G ? __ldcg(tail.part + g * stride + 3 + i) * fac_s[g] : 0.0f;
+                x[j] = g < G ? __ldcg(part + g * stride + 3 + i) * fac_s[g] : 0.0f;
             }
 #pragma unroll
             for (int j = 0; j < kTailBatch; ++j) {
@@ -98,9 +102,24 @@ __device__ __noinline__ void tail_merge(const int K, const int T, const float la
         for (int grp = 0; grp < NG; ++grp) {
             if constexpr (COMP) n.add(red[grp * TN + i]); else n_n += red[grp * TN + i];
         }
-        const float vn = v_s[i] + (COMP ? n.value() : n_n) / eta;
+        const float N = COMP ? n.value() : n_n;
+        if (tail.part_out != nullptr) {  // a shard's partial: the update waits for the other shards
+            tail.part_out[3 + i] = N;
+            continue;
+        }
+        const float vn = v_s[i] + N / eta;
         tail.v_out[i] = vn;
         if (tail.u0 != nullptr && i < 2) tail.u0[i] = vn;
+    }
+    if (tail.part_out != nullptr) {
+        if (tid == 0) {
+            tail.part_out[0] = beta;
+            tail.part_out[1] = eta;
+            tail.part_out[2] = sumsq;
+            if (tail.ctr_out != nullptr) *tail.ctr_out += 1u;
+            if (tail.ticket != nullptr) *tail.ticket = 0u;
+        }
+        return;
     }
     for (int k0 = tid; k0 < K; k0 += kTailBatch * nthr) {
         float s[kTailBatch];
@@ -116,11 +135,43 @@ __device__ __noinline__ void tail_merge(const int K, const int T, const float la
             tail.diag[0] = beta;
             tail.diag[1] = eta;
             tail.diag[2] = eta * eta / sumsq;
-            tail.diag[3] = beta - lambda * logf(eta / (float)K);
+            tail.diag[3] = beta - lambda * logf(eta / K_norm);
         }
-        *tail.ctr_out += 1u;
-        *tail.ticket = 0u;
+        if (tail.ctr_out != nullptr) *tail.ctr_out += 1u;
+        if (tail.ticket != nullptr) *tail.ticket = 0u;
     }
+}
+
+// One block merges the partials of G sample shards (the exchange of a sample-sharded solve).
+template <bool COMP>
+__global__ void __launch_bounds__(512) merge_partials_kernel(const int G, const float* parts, const int K,
+                                                             const float K_norm, const int T, const float lambda,
+                                                             const float inv_lambda, const float* S, const TailIO tail)
+{
+    extern __shared__ float smem[];
+    __shared__ float fac_s[kTailMaxBlocks];
+    __shared__ float red_e[kTailMaxBlocks], red_q[kTailMaxBlocks];
+    __shared__ float bc_s[3];
+    const int TN = 2 * T;
+    float* v_s = smem;
+    float* red = smem + TN;
+    for (int i = threadIdx.x; i < TN; i += blockDim.x) v_s[i] = tail.v_out[i];
+    __syncthreads();
+    tail_merge<COMP>(G, parts, K, K_norm, T, lambda, inv_lambda, S, tail, v_s, red, fac_s, red_e, red_q, bc_s);
+}
+
+cudaError_t merge_partials_launch(const DevParams& dp, int G, const float* parts, bool comp, const float* S,
+                                  const TailIO& tail, cudaStream_t st)
+{
+    if (G < 1 || G > kTailMaxBlocks) return cudaErrorInvalidValue;
+    const int threads = 512;
+    const size_t smem = sizeof(float) * (2 * (size_t)dp.T + std::max<size_t>(2 * (size_t)dp.T, threads));
+    const float Kn = (float)dp.K_norm;
+    if (comp)
+        merge_partials_kernel<true><<<1, threads, smem, st>>>(G, parts, dp.K, Kn, dp.T, dp.lambda, dp.inv_lambda, S, tail);
+    else
+        merge_partials_kernel<false><<<1, threads, smem, st>>>(G, parts, dp.K, Kn, dp.T, dp.lambda, dp.inv_lambda, S, tail);
+    return cudaGetLastError();
 }
 
 // A block's partial of the weights/update over the samples it rolled out, read back from S and
@@ -292,7 +343,8 @@ __global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const De
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    tail_merge<COMP>(dp.K, dp.T, dp.lambda, dp.inv_lambda, io.S, tail, v_s, red, fac_s, red_e, red_q, bc_s);
+    tail_merge<COMP>(gridDim.x, tail.part, dp.K, (float)dp.K_norm, dp.T, dp.lambda, dp.inv_lambda, io.S, tail, v_s,
+                     red, fac_s, red_e, red_q, bc_s);
 }
 
 size_t rollout_smem_bytes(const DevParams& dp, int wpb)

@@ -251,12 +251,13 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
     const int k = group * dp.spw + lane / seg;
     const bool active = k < dp.K;
     const int kc = active ? k : dp.K - 1;  // inactive segments shadow a valid sample, write nothing
-    const uint32_t kk = dp.crn ? 0u : (uint32_t)kc;
+    const uint32_t kg = (uint32_t)(kc + dp.k_off);  // global sample index: the random streams' key
+    const uint32_t kk = dp.crn ? 0u : kg;
 
     // (a1, a2) control noise eps ~ N(0, Sigma_eps) and clamped samples u = clamp(v + eps); the
     // lanes of the segment split the horizon. eps_eff = u - v feeds the update.
     for (int t = ls; t < dp.T; t += seg) {
-        const uint4 w = draw_words(dp, (uint32_t)t, 0u, 0u, (uint32_t)kc, kStreamControl, ctr);
+        const uint4 w = draw_words(dp, (uint32_t)t, 0u, 0u, kg, kStreamControl, ctr);
         const float2 z = box_muller(w.x, w.y);
         const float e0 = dp.Le00 * z.x;
         const float e1 = fmaf(dp.Le10, z.x, dp.Le11 * z.y);

@@ -208,6 +208,8 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.n_sub = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_sub : 1;
     d.ey = p->ey_index; d.crn = p->crn_disturbance ? 1 : 0; d.record = p->record_moments ? 1 : 0;
     d.resample = p->resample ? 1 : 0;
+    d.k_off = 0;
+    d.K_norm = p->K;
     d.key0 = (uint32_t)(p->seed & 0xffffffffu); d.key1 = (uint32_t)(p->seed >> 32);
     for (int r = 0; r < 10; ++r) {  // Philox key schedule: k + r (0x9E3779B9, 0xBB67AE85)
         d.rk0[r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
@@ -347,7 +349,7 @@ int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* 
     cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 2 * h->ev_count : nullptr;
     if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], h->stream));
     // One launch: rollout, costs, and (in its tail) weights, update, u0, diagnostics, counter.
-    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, h->d_ctr, h->d_v};
+    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, h->d_ctr, h->d_v, nullptr};
     BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, h->d_v, h->d_ctr,
                                     h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, h->stream));
     if (ev) {
@@ -384,6 +386,41 @@ int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, fl
     BSS_CUDA(h, cudaStreamSynchronize(h->stream));
     if (h_v) std::memcpy(h_v, sv, sizeof(float) * 2 * T);
     if (h_u0) std::memcpy(h_u0, su0, sizeof(float) * 2);
+    return BSSMPPI_OK;
+}
+
+int bssmppi_set_sample_range(bssmppi_t h, int32_t k_begin, int32_t K_total)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (k_begin < 0 || K_total < h->prm.K || K_total > BSSMPPI_K_MAX || k_begin > K_total - h->prm.K)
+        return fail(h, BSSMPPI_EINVAL, "need 0 <= k_begin and k_begin + K <= K_total <= BSSMPPI_K_MAX");
+    BSS_CUDA(h, cudaStreamSynchronize(h->stream));  // solves in flight keep the old range
+    h->dp.k_off = k_begin;
+    h->dp.K_norm = K_total;
+    return BSSMPPI_OK;
+}
+
+int bssmppi_solve_partial(bssmppi_t h, const float* d_x0, const float* d_Sigma0, const float* d_v, float* d_partial)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!d_x0 || !d_partial) return fail(h, BSSMPPI_EINVAL, "x0 and partial must be non-NULL");
+    const size_t vbytes = sizeof(float) * 2 * h->prm.T;
+    if (d_v) BSS_CUDA(h, cudaMemcpyAsync(h->d_v, d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, nullptr, nullptr, h->d_ctr, h->d_v, d_partial};
+    BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, h->d_v, h->d_ctr,
+                                    h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, h->stream));
+    return BSSMPPI_OK;
+}
+
+int bssmppi_merge_partials(bssmppi_t h, const float* d_partials, int32_t G, float* d_v, float* d_u0)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!d_partials) return fail(h, BSSMPPI_EINVAL, "partials are NULL");
+    if (G < 1 || G > bss::kTailMaxBlocks) return fail(h, BSSMPPI_EINVAL, "G must be in [1, 256]");
+    bss::TailIO tail{nullptr, nullptr, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, nullptr, h->d_v, nullptr};
+    BSS_CUDA(h, bss::merge_partials_launch(h->dp, G, d_partials, h->prm.compensated != 0, h->d_S, tail, h->stream));
+    const size_t vbytes = sizeof(float) * 2 * h->prm.T;
+    if (d_v) BSS_CUDA(h, cudaMemcpyAsync(d_v, h->d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
     return BSSMPPI_OK;
 }
 
