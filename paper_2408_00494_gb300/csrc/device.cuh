@@ -22,6 +22,7 @@ struct DevParams {
     int resample;     // 1: particles re-drawn from N(mean, cov) before every step k >= 1 (Algorithm 2 literal)
     int k_off;        // global index of the handle's first sample (a shard of a larger K); 0 otherwise
     int K_norm;       // samples of the whole (possibly sharded) solve: K unless sharded
+    int lw_diag;      // 1: Sigma_w is diagonal, so its Cholesky factor is (the disturbance needs nx products)
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];       // Philox round keys k + r W (the key schedule, precomputed)
     float dt, h, inv_m, inv_Iz, lf, lr, tB, tC, Df, Dr, vx_floor;
@@ -112,6 +113,14 @@ __device__ __forceinline__ void draw_normals(const DevParams& P, uint32_t step, 
     }
 }
 
+// x += L z with L diagonal (its diagonal entries at the packed positions i (i + 3) / 2).
+template <int NX>
+__device__ __forceinline__ void add_diagonal(const float* L, const float (&z)[NX], float (&x)[NX])
+{
+#pragma unroll
+    for (int i = 0; i < NX; ++i) x[i] = fmaf(L[i * (i + 3) / 2], z[i], x[i]);
+}
+
 // x += L z with L packed lower-triangular by rows.
 template <int NX>
 __device__ __forceinline__ void add_correlated(const float* L, const float (&z)[NX], float (&x)[NX])
@@ -134,6 +143,31 @@ __device__ __forceinline__ void add_correlated(const float* L, const float (&z)[
 struct Control {
     float steer, accel, sin_steer, cos_steer;
 };
+
+// sin x and cos x from their Taylor series through x^11 and x^12 (coefficients 1/n!); for |x| <= pi/4
+// the truncation error is below 1e-12, far under FP32 rounding. Outside that range (a spinning
+// vehicle) the library's sincosf.
+__device__ __forceinline__ void sincos_series(float x, float* s, float* c)
+{
+    if (fabsf(x) <= 0.78539816f) {
+        const float x2 = x * x;
+        float ps = -2.5052108e-8f;          // -1/11!
+        ps = fmaf(ps, x2, 2.7557319e-6f);   //  1/9!
+        ps = fmaf(ps, x2, -1.9841270e-4f);  // -1/7!
+        ps = fmaf(ps, x2, 8.3333333e-3f);   //  1/5!
+        ps = fmaf(ps, x2, -1.6666667e-1f);  // -1/3!
+        *s = fmaf(ps * x2, x, x);
+        float pc = 2.0876757e-9f;           //  1/12!
+        pc = fmaf(pc, x2, -2.7557319e-7f);  // -1/10!
+        pc = fmaf(pc, x2, 2.4801587e-5f);   //  1/8!
+        pc = fmaf(pc, x2, -1.3888889e-3f);  // -1/6!
+        pc = fmaf(pc, x2, 4.1666667e-2f);   //  1/4!
+        pc = fmaf(pc, x2, -0.5f);           // -1/2!
+        *c = fmaf(pc, x2, 1.0f);
+    } else {
+        sincosf(x, s, c);
+    }
+}
 
 __device__ __forceinline__ float track_curvature(const DevParams& P, const float* __restrict__ kap, float s)
 {
@@ -159,7 +193,7 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const float*
     const float Fr = P.Dr * __sinf(P.tC * atanf(P.tB * alpha_r));
     const float kap_s = track_curvature(P, kap, s0 + x[5]);
     float sp, cp;
-    sincosf(ep, &sp, &cp);  // e_psi is small and multiplies v_x: keep the ulp-accurate version
+    sincos_series(ep, &sp, &cp);  // e_psi multiplies v_x: an ulp-level sine, not the hardware one
     const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
     const float dvx = u.accel - Ff * u.sin_steer * P.inv_m + vy * r;
     const float dvy = (Ff * u.cos_steer + Fr) * P.inv_m - vx * r;

@@ -229,7 +229,7 @@ __device__ __forceinline__ void cholesky_psd(const float* A, float (&L)[NX][NX])
 template <int P>
 constexpr int roll_max_threads()
 {
-    return P <= 2 ? 1024 : (P == 4 ? 768 : 512);
+    return P == 1 ? 1024 : (P == 2 ? 896 : (P == 4 ? 768 : 512));
 }
 
 // One sample group (the spw samples of one warp): control sequence, rollout, moments, cost.
@@ -371,7 +371,8 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         for (int p = 0; p < P; ++p) {
             float z[NX];
             draw_normals<NX>(dp, (uint32_t)t, (uint32_t)(ls + seg * p), kk, kStreamDisturbance, ctr, z);
-            add_correlated<NX>(dp.Lw, z, x[p]);
+            if (dp.lw_diag) add_diagonal<NX>(dp.Lw, z, x[p]);
+            else add_correlated<NX>(dp.Lw, z, x[p]);
         }
 
         // (a5) belief moments of step t+1, (a6) barrier.

@@ -228,8 +228,12 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.Si00 = (float)(Se[3] / det); d.Si01 = (float)(-Se[1] / det);
     d.Si10 = (float)(-Se[2] / det); d.Si11 = (float)(Se[0] / det);
     for (int i = 0; i < 21; ++i) d.Lw[i] = 0.0f;
+    d.lw_diag = 1;
     for (int i = 0; i < nx; ++i)
-        for (int j = 0; j <= i; ++j) d.Lw[i * (i + 1) / 2 + j] = (float)Lw[i * nx + j];
+        for (int j = 0; j <= i; ++j) {
+            d.Lw[i * (i + 1) / 2 + j] = (float)Lw[i * nx + j];
+            if (j < i && d.Lw[i * (i + 1) / 2 + j] != 0.0f) d.lw_diag = 0;
+        }
     d.lambda = p->lambda;
     d.inv_lambda = 1.0f / p->lambda;
     d.nu = (float)(std::sqrt(2.0) * inverse_erf(1.0 - 2.0 * (double)p->delta));
