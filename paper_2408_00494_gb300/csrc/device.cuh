@@ -59,13 +59,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // The same ten rounds with the key schedule taken from precomputed round keys (kernel parameters),
-// which saves the two key additions of every round.
+// which saves the two key additions of every round. Each 32x32 -> 64-bit product is written as one
+// widening multiply, so its high and low halves come from a single instruction.
 __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk0, const uint32_t* rk1)
 {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         c = make_uint4(hi1 ^ c.y ^ rk0[round], lo1, hi0 ^ c.w ^ rk1[round], lo0);
     }
     return c;
@@ -144,21 +147,19 @@ struct Control {
     float steer, accel, sin_steer, cos_steer;
 };
 
-// sin x and cos x from their Taylor series through x^11 and x^12 (coefficients 1/n!); for |x| <= pi/4
-// the truncation error is below 1e-12, far under FP32 rounding. Outside that range (a spinning
-// vehicle) the library's sincosf.
+// sin x and cos x from their Taylor series through x^9 and x^10 (coefficients 1/n!); for |x| <= pi/4
+// the truncation errors are below |x|^11/11! < 2e-9 and |x|^12/12! < 2e-10, under FP32 rounding.
+// Outside that range (a spinning vehicle) the library's sincosf.
 __device__ __forceinline__ void sincos_series(float x, float* s, float* c)
 {
     if (fabsf(x) <= 0.78539816f) {
         const float x2 = x * x;
-        float ps = -2.5052108e-8f;          // -1/11!
-        ps = fmaf(ps, x2, 2.7557319e-6f);   //  1/9!
+        float ps = 2.7557319e-6f;           //  1/9!
         ps = fmaf(ps, x2, -1.9841270e-4f);  // -1/7!
         ps = fmaf(ps, x2, 8.3333333e-3f);   //  1/5!
         ps = fmaf(ps, x2, -1.6666667e-1f);  // -1/3!
         *s = fmaf(ps * x2, x, x);
-        float pc = 2.0876757e-9f;           //  1/12!
-        pc = fmaf(pc, x2, -2.7557319e-7f);  // -1/10!
+        float pc = -2.7557319e-7f;          // -1/10!
         pc = fmaf(pc, x2, 2.4801587e-5f);   //  1/8!
         pc = fmaf(pc, x2, -1.3888889e-3f);  // -1/6!
         pc = fmaf(pc, x2, 4.1666667e-2f);   //  1/4!
