@@ -22,7 +22,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 class OrcConstraint(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("backoff", ctypes.c_int), ("i", ctypes.c_int), ("j", ctypes.c_int),
-                ("p", ctypes.c_double), ("b", ctypes.c_double), ("a", ctypes.c_double * 6),
+                ("p", ctypes.c_double), ("b", ctypes.c_double), ("a", ctypes.c_double * 8),
                 ("center", ctypes.c_double * 2), ("radius", ctypes.c_double)]
 
 
@@ -34,12 +34,14 @@ class OrcProblem(ctypes.Structure):
         ("lf", ctypes.c_double), ("lr", ctypes.c_double), ("tire_B", ctypes.c_double),
         ("tire_C", ctypes.c_double), ("mu", ctypes.c_double), ("g", ctypes.c_double),
         ("vx_floor", ctypes.c_double),
+        ("wheel_radius", ctypes.c_double), ("wheel_inertia", ctypes.c_double), ("mu_x", ctypes.c_double),
+        ("tau_max", ctypes.c_double), ("slip_floor", ctypes.c_double),
         ("u_min", ctypes.c_double * 2), ("u_max", ctypes.c_double * 2),
-        ("Sigma_eps", ctypes.c_double * 4), ("Sigma_w", ctypes.c_double * 36),
+        ("Sigma_eps", ctypes.c_double * 4), ("Sigma_w", ctypes.c_double * 64),
         ("lam", ctypes.c_double), ("delta", ctypes.c_double), ("gamma", ctypes.c_double),
         ("ctrl_w", ctypes.c_double), ("C_safe", ctypes.c_double), ("C_obs", ctypes.c_double),
         ("w_T", ctypes.c_double),
-        ("x_goal", ctypes.c_double * 6), ("Q", ctypes.c_double * 6), ("Qf", ctypes.c_double * 6),
+        ("x_goal", ctypes.c_double * 8), ("Q", ctypes.c_double * 8), ("Qf", ctypes.c_double * 8),
         ("ey_index", ctypes.c_int),
         ("kappa", _dp), ("n_track", ctypes.c_int), ("track_len", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("crn_disturbance", ctypes.c_int), ("resample", ctypes.c_int),
@@ -112,6 +114,7 @@ class Oracle:
         for name in ("K", "M", "T", "n_sub", "model", "ey_index", "crn_disturbance", "resample"):
             setattr(p, name, int(getattr(prob, name)))
         for name in ("dt", "mass", "Iz", "lf", "lr", "tire_B", "tire_C", "mu", "g", "vx_floor",
+                     "wheel_radius", "wheel_inertia", "mu_x", "tau_max", "slip_floor",
                      "delta", "gamma", "ctrl_w", "C_safe", "C_obs", "w_T"):
             setattr(p, name, _f32(getattr(prob, name)))
         p.lam = _f32(prob.lam)
@@ -125,7 +128,7 @@ class Oracle:
         sw = np.asarray(prob.Sigma_w, dtype=np.float64).reshape(nx, nx)
         for i in range(nx * nx):
             p.Sigma_w[i] = sw.flat[i]
-        for i in range(6):
+        for i in range(min(8, len(prob.x_goal))):
             p.x_goal[i] = _f32(prob.x_goal[i])
             p.Q[i] = _f32(prob.Q[i])
             p.Qf[i] = _f32(prob.Qf[i])
@@ -142,7 +145,7 @@ class Oracle:
             oc.backoff = {"gaussian": 0, "cantelli": 1}[c.get("backoff", "gaussian")]
             oc.p = _f32(c["p"])
             if oc.kind == 0:
-                for l in range(6):
+                for l in range(8):
                     oc.a[l] = _f32(c["a"][l]) if l < len(c["a"]) else 0.0
                 oc.b = _f32(c["b"])
             else:

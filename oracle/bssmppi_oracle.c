@@ -80,7 +80,7 @@ double orc_backoff_gaussian(double p)
 
 double orc_backoff_cantelli(double p) { return sqrt((1.0 - p) / p); }
 
-int orc_nx(const orc_problem* p) { return p->model == 0 ? 6 : 4; }
+int orc_nx(const orc_problem* p) { return p->model == 0 ? 6 : (p->model == 2 ? 8 : 4); }
 
 /* Cholesky factor L (lower, row-major n x n) of a symmetric PSD matrix; a zero pivot gives a
  * zero column (a component with no noise). */
@@ -196,9 +196,59 @@ static void bicycle_rhs_vjp(const orc_problem* p, const double* x, const double*
     gu[0] += gsteer; gu[1] += gacc;
 }
 
+/* Single-track model with wheel speeds and combined slip (Sec. V-A's plant: state
+ * [v_x, v_y, r, omega_F, omega_R, e_psi, e_y, s], input [steer, throttle]). Lateral slip angles as in
+ * the bicycle model; longitudinal slip kappa = (R omega - v_w) / max(|v_w|, slip_floor) with v_w the
+ * wheel's forward speed; one magic-formula curve on the combined slip s = sqrt(kappa^2 + alpha^2),
+ * g = sin(C atan(B s)), split along the slip direction and scaled by the friction ellipse's axes:
+ * F_x = mu_x F_z g kappa / s, F_y = mu F_z g alpha / s (so (F_x / mu_x F_z)^2 + (F_y / mu F_z)^2 = g^2 <= 1).
+ * Rear-wheel drive torque tau_max * throttle; static axle loads. */
+static void wheels8_rhs(const orc_problem* p, const double* x, const double* u, double* dx)
+{
+    double vx = x[0], vy = x[1], r = x[2], wf = x[3], wr = x[4], epsi = x[5], ey = x[6], s = x[7];
+    double steer = u[0], thr = u[1];
+    double vxh = fmax(vx, p->vx_floor);
+    double alpha_f = steer - atan2(vy + p->lf * r, vxh);
+    double alpha_r = -atan2(vy - p->lr * r, vxh);
+    double vwf = vx * cos(steer) + (vy + p->lf * r) * sin(steer);
+    double vwr = vx;
+    double kf = (p->wheel_radius * wf - vwf) / fmax(fabs(vwf), p->slip_floor);
+    double kr = (p->wheel_radius * wr - vwr) / fmax(fabs(vwr), p->slip_floor);
+    double L = p->lf + p->lr;
+    double Fz[2] = {p->mass * p->g * p->lr / L, p->mass * p->g * p->lf / L};
+    double kap[2] = {kf, kr}, alp[2] = {alpha_f, alpha_r}, Fx[2], Fy[2];
+    for (int w = 0; w < 2; ++w) {
+        double sl = sqrt(kap[w] * kap[w] + alp[w] * alp[w]);
+        /* g(s) / s, which tends to C B as s -> 0 */
+        double ratio = sl > 1e-12 ? sin(p->tire_C * atan(p->tire_B * sl)) / sl : p->tire_C * p->tire_B;
+        Fx[w] = p->mu_x * Fz[w] * ratio * kap[w];
+        Fy[w] = p->mu * Fz[w] * ratio * alp[w];
+    }
+    double FXf = Fx[0] * cos(steer) - Fy[0] * sin(steer);
+    double FYf = Fx[0] * sin(steer) + Fy[0] * cos(steer);
+    double kp = orc_track_kappa(p, s);
+    double sdot = (vx * cos(epsi) - vy * sin(epsi)) / (1.0 - kp * ey);
+    dx[0] = (FXf + Fx[1]) / p->mass + vy * r;
+    dx[1] = (FYf + Fy[1]) / p->mass - vx * r;
+    dx[2] = (p->lf * FYf - p->lr * Fy[1]) / p->Iz;
+    dx[3] = -p->wheel_radius * Fx[0] / p->wheel_inertia;
+    dx[4] = (p->tau_max * thr - p->wheel_radius * Fx[1]) / p->wheel_inertia;
+    dx[5] = r - kp * sdot;
+    dx[6] = vx * sin(epsi) + vy * cos(epsi);
+    dx[7] = sdot;
+}
+
 void orc_model_step(const orc_problem* p, const double* x, const double* u, double* x_next)
 {
-    if (p->model == 0) {
+    if (p->model == 2) {
+        double h = p->dt / p->n_sub, xs[8], dx[8];
+        memcpy(xs, x, sizeof xs);
+        for (int j = 0; j < p->n_sub; ++j) {
+            wheels8_rhs(p, xs, u, dx);
+            for (int i = 0; i < 8; ++i) xs[i] += h * dx[i];
+        }
+        memcpy(x_next, xs, sizeof xs);
+    } else if (p->model == 0) {
         double h = p->dt / p->n_sub, xs[6], dx[6];
         memcpy(xs, x, sizeof xs);
         for (int j = 0; j < p->n_sub; ++j) {
@@ -309,7 +359,7 @@ static double general_h(const orc_problem* p, const double* mean, const double* 
     double h = INFINITY;
     for (int q = 0; q < p->n_con; ++q) {
         const orc_constraint* c = p->con + q;
-        double eta[6];
+        double eta[8];
         double cv = constraint_value(c, mean, nx, eta);
         double quad = 0.0;
         for (int a = 0; a < nx; ++a)
@@ -335,7 +385,7 @@ static double state_cost(const orc_problem* p, const double* W, const double* xm
     } else {
         int broken = 0;
         for (int q = 0; q < p->n_con; ++q) {
-            double eta[6];
+            double eta[8];
             if (constraint_value(p->con + q, xm, nx, eta) > 0.0) broken = 1;
         }
         if (broken) c += p->C_obs;
@@ -357,7 +407,7 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
 {
     const int nx = orc_nx(p), M = p->M, T = p->T;
     if (M < 2 || T < 1 || k_begin < 0 || k_end > p->K || k_begin > k_end) return -1;
-    double L_eps[4], L_w[36], L_0[36], Sinv[4];
+    double L_eps[4], L_w[64], L_0[64], Sinv[4];
     cholesky_psd(2, p->Sigma_eps, L_eps);
     cholesky_psd(nx, p->Sigma_w, L_w);
     if (Sigma0) cholesky_psd(nx, Sigma0, L_0);
@@ -380,7 +430,7 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
         for (int n = 0; n < M; ++n) {
             for (int i = 0; i < nx; ++i) X[n * nx + i] = x0[i];
             if (Sigma0) {
-                double xi[6];
+                double xi[8];
                 draw_normals(p, nx, 0, (uint32_t)n, kk, 3, solve_ctr, xi);
                 for (int i = 0; i < nx; ++i)
                     for (int j = 0; j <= i; ++j) X[n * nx + i] += L_0[i * nx + j] * xi[j];
@@ -404,11 +454,11 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
                 /* Algorithm 2, first line of its loop: x^n_k ~ N(xbar_k, Sigma_k), drawn as
                  * xbar_k + L_k xi^n with L_k the (PSD) Cholesky factor of the Monte-Carlo covariance
                  * of step k and xi^n from stream 4. At k = 0 the initial particles above are the draw. */
-                double Lk[36];
+                double Lk[64];
                 cholesky_psd(nx, Sig + (size_t)k * nx * nx, Lk);
                 const double* mk = xbar + (size_t)k * nx;
                 for (int n = 0; n < M; ++n) {
-                    double xi[6];
+                    double xi[8];
                     draw_normals(p, nx, (uint32_t)k, (uint32_t)n, kk, 4, solve_ctr, xi);
                     for (int i = 0; i < nx; ++i) {
                         double x = mk[i];
@@ -418,7 +468,7 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
                 }
             }
             for (int n = 0; n < M; ++n) {
-                double xn[6], w[6], z[6];
+                double xn[8], w[8], z[8];
                 orc_model_step(p, X + n * nx, uk, xn);
                 draw_normals(p, nx, (uint32_t)k, (uint32_t)n, kk, 1, solve_ctr, z);
                 for (int i = 0; i < nx; ++i) {
@@ -463,7 +513,7 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
                     if (d < mg) mg = d;
                 } else {
                     for (int q = 0; q < p->n_con; ++q) {
-                        double eta[6];
+                        double eta[8];
                         double d = fabs(constraint_value(p->con + q, xbar + (size_t)k * nx, nx, eta));
                         if (d < mg) mg = d;
                     }

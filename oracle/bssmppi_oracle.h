@@ -35,17 +35,19 @@ extern "C" {
  *   backoff 0: nu = sqrt(2) erfinv(1 - 2p) (Gaussian); 1: nu = sqrt((1 - p) / p) (Cantelli). */
 typedef struct orc_constraint {
     int kind, backoff, i, j;
-    double p, b, a[6], center[2], radius;
+    double p, b, a[8], center[2], radius;
 } orc_constraint;
 
 typedef struct orc_problem {
-    int K, M, T, n_sub, model; /* model 0: dynamic bicycle (nx=6); 1: double integrator (nx=4) */
+    int K, M, T, n_sub, model; /* model 0: dynamic bicycle (nx=6); 1: double integrator (nx=4);
+                                  2: single-track model with wheel speeds and combined slip (nx=8) */
     double dt, mass, Iz, lf, lr, tire_B, tire_C, mu, g, vx_floor;
+    double wheel_radius, wheel_inertia, mu_x, tau_max, slip_floor; /* model 2 only */
     double u_min[2], u_max[2];
     double Sigma_eps[4];  /* 2x2 row-major, SPD */
-    double Sigma_w[36];   /* nx x nx row-major (leading dimension nx), PSD */
+    double Sigma_w[64];   /* nx x nx row-major (leading dimension nx), PSD */
     double lambda, delta, gamma, ctrl_w, C_safe, C_obs, w_T;
-    double x_goal[6], Q[6], Qf[6];
+    double x_goal[8], Q[8], Qf[8];
     int ey_index;         /* component bounded by |x_i| <= w_T (e_y) */
     const double* kappa;  /* curvature table, n_track entries over [0, track_len) */
     int n_track;

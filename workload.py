@@ -27,6 +27,7 @@ import numpy as np
 NU = 2
 MODEL_BICYCLE6 = 0
 MODEL_DOUBLE_INT4 = 1
+MODEL_WHEELS8 = 2
 
 
 def make_track(seed: int, radius: float = 60.0, n_s: int = 4096, n_theta: int = 1 << 16,
@@ -84,6 +85,11 @@ class Problem:
     mu: float = 1.0
     g: float = 9.81
     vx_floor: float = 1.0
+    wheel_radius: float = 0.3        # wheel-speed model (model 2) only
+    wheel_inertia: float = 1.0
+    mu_x: float = 1.0
+    tau_max: float = 0.0
+    slip_floor: float = 2.0
     u_min: tuple = (-0.4, -3.0)
     u_max: tuple = (0.4, 3.0)
     Sigma_eps: np.ndarray = None     # 2x2 control-noise covariance
@@ -109,7 +115,7 @@ class Problem:
 
     @property
     def nx(self) -> int:
-        return 6 if self.model == MODEL_BICYCLE6 else 4
+        return {MODEL_BICYCLE6: 6, MODEL_DOUBLE_INT4: 4, MODEL_WHEELS8: 8}[self.model]
 
 
 def _diag(std):
@@ -123,6 +129,24 @@ def racing_problem(K, M, T, track_seed, noise_scale=1.0, lam=1.0, seed=0, **kw) 
     p = Problem(K=K, M=M, T=T, lam=lam, ctrl_w=lam, kappa=kappa, track_len=length, seed=seed)
     p.Sigma_eps = _diag([0.05, 0.5])
     p.Sigma_w = _diag(np.array([0.02, 0.02, 0.01, 0.002, 0.02, 0.0]) * noise_scale)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def wheels_problem(K, M, T, track_seed=2, noise_scale=1.0, lam=1.0, seed=0, **kw) -> Problem:
+    """The single-track model with wheel speeds and combined slip at AutoRally scale (a 22 kg,
+    1 m vehicle) on a seeded track of radius 25 m, goal speed 6 m/s, half-width 2 m. The paper does
+    not publish the model's parameters; these are chosen to be plausible for such a vehicle."""
+    kappa, length = make_track(track_seed, radius=25.0, amp_max=0.5)
+    p = Problem(K=K, M=M, T=T, model=MODEL_WHEELS8, n_sub=10, lam=lam, ctrl_w=lam, kappa=kappa, track_len=length,
+                seed=seed, mass=22.0, Iz=1.1, lf=0.34, lr=0.23, tire_B=8.0, tire_C=1.6, mu=0.9, mu_x=1.0,
+                wheel_radius=0.095, wheel_inertia=0.05, tau_max=8.0, slip_floor=2.0,
+                u_min=(-0.35, -1.0), u_max=(0.35, 1.0), w_T=2.0, ey_index=6,
+                x_goal=(6.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0), Q=(1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.1, 0.0),
+                Qf=(1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.1, 0.0))
+    p.Sigma_eps = _diag([0.05, 0.3])
+    p.Sigma_w = _diag(np.array([0.02, 0.02, 0.01, 0.05, 0.05, 0.002, 0.02, 0.0]) * noise_scale)
     for k, v in kw.items():
         setattr(p, k, v)
     return p
@@ -157,15 +181,24 @@ def disk(i, j, center, radius, p, backoff="gaussian") -> dict:
 
 
 def racing_x0(p: Problem) -> np.ndarray:
-    """Start on the centre line at the goal speed."""
+    """Start on the centre line at the goal speed (wheels rolling freely for the wheel-speed model)."""
     x = np.zeros(p.nx, dtype=np.float32)
-    x[0] = p.x_goal[0] if p.model == MODEL_BICYCLE6 else 0.0
+    if p.model in (MODEL_BICYCLE6, MODEL_WHEELS8):
+        x[0] = p.x_goal[0]
+    if p.model == MODEL_WHEELS8:
+        x[3] = x[4] = p.x_goal[0] / p.wheel_radius
     return x
 
 
 def random_state(p: Problem, seed: int) -> np.ndarray:
     """A seeded plausible state near the centre line (for parity cases away from the start)."""
     rng = np.random.default_rng(seed)
+    if p.model == MODEL_WHEELS8:
+        vx = rng.uniform(4.0, 7.0)
+        x = np.array([vx, rng.normal(0, 0.1), rng.normal(0, 0.1), vx / p.wheel_radius * (1 + rng.normal(0, 0.02)),
+                      vx / p.wheel_radius * (1 + rng.normal(0, 0.02)), rng.normal(0, 0.05), rng.uniform(-1.0, 1.0),
+                      rng.uniform(0, p.track_len)])
+        return x.astype(np.float32)
     if p.model == MODEL_BICYCLE6:
         x = np.array([rng.uniform(7.0, 12.0), rng.normal(0, 0.3), rng.normal(0, 0.2),
                       rng.normal(0, 0.05), rng.uniform(-2.0, 2.0), rng.uniform(0, p.track_len)])
