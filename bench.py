@@ -447,15 +447,16 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     rep_ms = statistics.fmean(a.elapsed_time(b) for a, b in rep_ev)
 
-    def time_variant(pv):
-        """Solve + shift of a problem variant on the same state and L2 flush (CUDA events)."""
+    def time_variant(pv, xv=None):
+        """Solve + shift of a problem variant from state xv (default: the benchmark's), same L2 flush."""
+        xv = x0 if xv is None else xv
         cv = bssmppi.Controller(pv, stream=stream)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for i in range(args.warmup + args.steps):
             flush.fill_(float(i))
             if i >= args.warmup:
                 ev[i - args.warmup][0].record(stream)
-            bssmppi.solve(cv.h, x0)
+            bssmppi.solve(cv.h, xv)
             bssmppi.shift(cv.h, None, 1)
             if i >= args.warmup:
                 ev[i - args.warmup][1].record(stream)
@@ -474,6 +475,9 @@ def run_ours(args, rank, world, local_rank):
                          workload.halfspace((0, 0, 0, 0, -1, 0), p_con.w_T, p_con.delta),
                          workload.disk(5, 4, (float(x0_np[5]) + 6.0, 0.3), 1.0, 0.05, backoff="cantelli"))
     con_ms = time_variant(p_con)
+    # the 8-state single-track model with wheel speeds and combined slip (n_sub = 10), same sizes
+    p_w8 = workload.wheels_problem(p.K, p.M, p.T, seed=int(p.seed))
+    w8_ms = time_variant(p_w8, torch.as_tensor(workload.racing_x0(p_w8), device=dev))
 
     # end to end through the C ABI with host buffers (H2D of the state and nominal, D2H of v+ and u0)
     x0_h = workload.racing_x0(p)
@@ -516,6 +520,9 @@ def run_ours(args, rank, world, local_rank):
         "resample_variant": {"ms_per_step": rs_ms, "particle_steps_per_s": units / (rs_ms * 1e-3),
                              "note": "Algorithm 2 read literally: full moments, Cholesky and re-draw of "
                                      "every particle before each step; solve + shift, same L2 flush"},
+        "wheels8_variant": {"ms_per_step": w8_ms, "particle_steps_per_s": units / (w8_ms * 1e-3),
+                            "note": "8-state single-track model with wheel speeds and friction-ellipse "
+                                    "combined slip, n_sub = 10, AutoRally scale; solve + shift"},
         "constraint_set_variant": {"ms_per_step": con_ms, "particle_steps_per_s": units / (con_ms * 1e-3),
                                    "note": "general set h = min_q h_q: two track-edge half-spaces and a disk "
                                            "obstacle on (s, e_y), full covariance every step; solve + shift"},

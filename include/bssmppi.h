@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define BSSMPPI_ABI_VERSION 1u
+#define BSSMPPI_ABI_VERSION 2u
 #define BSSMPPI_NU 2          /* controls: [steer delta (rad), acceleration (m/s^2)] */
 #define BSSMPPI_NX_MAX 6
 #define BSSMPPI_K_MAX (1 << 20)
@@ -59,7 +59,10 @@ typedef enum bssmppi_status {
 
 typedef enum bssmppi_model {
     BSSMPPI_MODEL_BICYCLE6 = 0,  /* dynamic single-track vehicle, x = [v_x, v_y, r, e_psi, e_y, s] */
-    BSSMPPI_MODEL_DOUBLE_INT4 = 1 /* planar double integrator, x = [p_x, p_y, v_x, v_y] (test model) */
+    BSSMPPI_MODEL_DOUBLE_INT4 = 1, /* planar double integrator, x = [p_x, p_y, v_x, v_y] (test model) */
+    BSSMPPI_MODEL_WHEELS8 = 2     /* single-track vehicle with wheel speeds and friction-ellipse combined
+                                     slip (Sec. V-A's plant), x = [v_x, v_y, r, omega_F, omega_R, e_psi,
+                                     e_y, s], u = [steer, throttle]; M <= 128 */
 } bssmppi_model;
 
 /* Which internal buffer of the last solve bssmppi_read() copies. */
@@ -85,6 +88,9 @@ typedef struct bssmppi_params {
     int32_t model;        /* bssmppi_model */
     int32_t ey_index;     /* state component bounded by |x_i| <= w_T (4 = e_y for the bicycle) */
     float dt, mass, Iz, lf, lr, tire_B, tire_C, mu, g, vx_floor; /* model constants (SI units) */
+    /* wheel-speed model only: wheel radius R, axle wheel inertia I_w, longitudinal friction mu_x (mu is the
+       lateral one), rear drive torque at full throttle, and the speed floor of the slip denominators */
+    float wheel_radius, wheel_inertia, mu_x, tau_max, slip_floor;
     float u_min[2], u_max[2];  /* control bounds; sampled controls are clamped to them */
     float lambda;         /* temperature, > 0 */
     float delta;          /* per-boundary chance level, 0 < delta < 0.5; nu = sqrt(2) erfinv(1 - 2 delta) */
@@ -93,12 +99,12 @@ typedef struct bssmppi_params {
     float C_safe;         /* weight C of the safe-condition violation cost */
     float C_obs;          /* collision penalty added when |mean e_y| > w_T */
     float w_T;            /* track half-width */
-    float x_goal[6], Q[6], Qf[6]; /* quadratic running and terminal cost (diagonal weights) */
+    float x_goal[8], Q[8], Qf[8]; /* quadratic running and terminal cost (diagonal weights; first nx used) */
     float track_len;      /* length of the closed centre line (m), > 0 */
     int32_t n_track;      /* curvature table size, a power of two in 2..BSSMPPI_NTRACK_MAX */
     const float* track_kappa; /* host pointer to n_track curvature samples kappa(i * track_len / n_track); copied */
     double Sigma_eps[4];  /* 2x2 SPD control-noise covariance */
-    double Sigma_w[36];   /* nx x nx PSD disturbance covariance (leading dimension nx) */
+    double Sigma_w[64];   /* nx x nx PSD disturbance covariance (leading dimension nx) */
     uint64_t seed;        /* Philox key */
     int32_t crn_disturbance; /* 1: disturbance draws shared by all K samples (common random numbers) */
     int32_t compensated;  /* 1: Welford/Chan moments and Kahan sums; 0: naive sums (precision study) */
@@ -133,7 +139,7 @@ typedef struct bssmppi_constraint {
     int32_t i, j;         /* DISK: the two (distinct) state components of the obstacle's plane */
     float p;              /* chance level p_q of this constraint */
     float b;              /* HALFSPACE: offset b */
-    float a[6];           /* HALFSPACE: normal a (entries past nx ignored) */
+    float a[8];           /* HALFSPACE: normal a (entries past nx ignored) */
     float center[2];      /* DISK: centre in the (x_i, x_j) plane */
     float radius;         /* DISK: radius r > 0 */
     int32_t reserved;     /* 0 */

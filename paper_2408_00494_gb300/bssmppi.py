@@ -35,13 +35,15 @@ class Params(ctypes.Structure):
         ("dt", ctypes.c_float), ("mass", ctypes.c_float), ("Iz", ctypes.c_float), ("lf", ctypes.c_float),
         ("lr", ctypes.c_float), ("tire_B", ctypes.c_float), ("tire_C", ctypes.c_float), ("mu", ctypes.c_float),
         ("g", ctypes.c_float), ("vx_floor", ctypes.c_float),
+        ("wheel_radius", ctypes.c_float), ("wheel_inertia", ctypes.c_float), ("mu_x", ctypes.c_float),
+        ("tau_max", ctypes.c_float), ("slip_floor", ctypes.c_float),
         ("u_min", ctypes.c_float * 2), ("u_max", ctypes.c_float * 2),
         ("lam", ctypes.c_float), ("delta", ctypes.c_float), ("gamma", ctypes.c_float), ("ctrl_w", ctypes.c_float),
         ("C_safe", ctypes.c_float), ("C_obs", ctypes.c_float), ("w_T", ctypes.c_float),
-        ("x_goal", ctypes.c_float * 6), ("Q", ctypes.c_float * 6), ("Qf", ctypes.c_float * 6),
+        ("x_goal", ctypes.c_float * 8), ("Q", ctypes.c_float * 8), ("Qf", ctypes.c_float * 8),
         ("track_len", ctypes.c_float), ("n_track", ctypes.c_int32),
         ("track_kappa", ctypes.POINTER(ctypes.c_float)),
-        ("Sigma_eps", ctypes.c_double * 4), ("Sigma_w", ctypes.c_double * 36),
+        ("Sigma_eps", ctypes.c_double * 4), ("Sigma_w", ctypes.c_double * 64),
         ("seed", ctypes.c_uint64),
         ("crn_disturbance", ctypes.c_int32), ("compensated", ctypes.c_int32),
         ("record_moments", ctypes.c_int32), ("resample", ctypes.c_int32),
@@ -50,7 +52,7 @@ class Params(ctypes.Structure):
 
 class Constraint(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("backoff", ctypes.c_int32), ("i", ctypes.c_int32), ("j", ctypes.c_int32),
-                ("p", ctypes.c_float), ("b", ctypes.c_float), ("a", ctypes.c_float * 6),
+                ("p", ctypes.c_float), ("b", ctypes.c_float), ("a", ctypes.c_float * 8),
                 ("center", ctypes.c_float * 2), ("radius", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
@@ -176,11 +178,14 @@ def make_params(prob, record_moments: bool = False, compensated: bool | None = N
     for name in ("dt", "mass", "Iz", "lf", "lr", "tire_B", "tire_C", "mu", "g", "vx_floor", "delta", "gamma",
                  "ctrl_w", "C_safe", "C_obs", "w_T"):
         setattr(p, name, float(getattr(prob, name)))
+    for name, default in (("wheel_radius", 0.3), ("wheel_inertia", 1.0), ("mu_x", 1.0), ("tau_max", 0.0),
+                          ("slip_floor", 2.0)):
+        setattr(p, name, float(getattr(prob, name, default)))
     p.lam = float(prob.lam)
     for i in range(2):
         p.u_min[i] = float(prob.u_min[i])
         p.u_max[i] = float(prob.u_max[i])
-    for i in range(6):
+    for i in range(min(8, len(prob.x_goal))):
         p.x_goal[i] = float(prob.x_goal[i])
         p.Q[i] = float(prob.Q[i])
         p.Qf[i] = float(prob.Qf[i])

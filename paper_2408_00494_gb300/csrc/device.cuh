@@ -8,7 +8,11 @@
 namespace bss {
 
 constexpr int kWarp = 32;
-constexpr int kNxMax = 6;
+constexpr int kNxMax = 8;
+// States of each model (0: bicycle, 1: double integrator, 2: wheel speeds) and the index of the
+// path coordinate s (-1: none).
+__host__ __device__ constexpr int model_nx(int model) { return model == 0 ? 6 : (model == 2 ? 8 : 4); }
+__host__ __device__ constexpr int model_s_index(int model) { return model == 0 ? 5 : (model == 2 ? 7 : -1); }
 
 // Everything a solve's kernels need, derived on the host at create time and passed by value
 // (kernel parameter space), so several controllers can run concurrently without global state.
@@ -29,9 +33,12 @@ struct DevParams {
     float umin0, umin1, umax0, umax1;
     float Le00, Le10, Le11;          // Cholesky factor of Sigma_eps
     float Si00, Si01, Si10, Si11;    // Sigma_eps^-1
-    float Lw[21];                    // Cholesky factor of Sigma_w, packed lower triangle by rows
+    float Lw[36];                    // Cholesky factor of Sigma_w, packed lower triangle by rows
     float lambda, inv_lambda, nu, one_m_gamma, ctrl_w, Csafe, Cobs, wT;
-    float xg[6], Q[6], Qf[6];
+    float xg[8], Q[8], Qf[8];
+    // wheel-speed model: mu_x F_z per axle, wheel radius, 1 / wheel inertia, full-throttle drive
+    // torque, slip-denominator speed floor, and C B (the slope of the tyre curve at zero slip)
+    float Dxf, Dxr, Rw, inv_Iw, tau_max, slip_floor, CB;
     float track_scale;               // n_track / track_len
     float Mf, invM, invM1;           // M, 1/M, 1/(M-1)
     const float* kappa;              // device curvature table, n_track + 1 entries (last = first)
@@ -113,6 +120,10 @@ __device__ __forceinline__ void draw_normals(const DevParams& P, uint32_t step, 
         const uint4 w1 = draw_words(P, step, 1u, particle, sample, stream, ctr);
         const float2 g2 = box_muller(w1.x, w1.y);
         z[4] = g2.x; z[5] = g2.y;
+        if constexpr (NX > 6) {
+            const float2 g3 = box_muller(w1.z, w1.w);
+            z[6] = g3.x; z[7] = g3.y;
+        }
     }
 }
 
@@ -207,6 +218,57 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const float*
     x[3] = fmaf(P.h, dep, ep);
     x[4] = fmaf(P.h, dey, ey);
     x[5] = fmaf(P.h, sdot, x[5]);
+}
+
+// Single-track model with wheel speeds and combined slip, x = [v_x, v_y, r, omega_F, omega_R, e_psi,
+// e_y, s - s0], u = [steer, throttle]. Lateral slip angles as in the bicycle model; longitudinal slip
+// kappa = (R omega - v_w) / max(|v_w|, slip_floor), v_w the wheel's forward speed; one tyre curve
+// g = sin(C atan(B s)) on the combined slip s = sqrt(kappa^2 + alpha^2), split along the slip
+// direction and scaled by the friction ellipse's axes: F_x = mu_x F_z g kappa / s,
+// F_y = mu F_z g alpha / s. Rear-wheel drive torque tau_max * throttle; static axle loads.
+__device__ __forceinline__ float tyre_ratio(const DevParams& P, float sl)
+{
+    // g(s) / s, which tends to C B at zero slip; |C atan(B s)| < C pi / 2 < pi keeps the hardware
+    // sine inside its accurate range
+    return sl > 1e-6f ? __fdividef(__sinf(P.tC * atanf(P.tB * sl)), sl) : P.CB;
+}
+
+__device__ __forceinline__ void wheels_substep(const DevParams& P, const float* __restrict__ kap, float s0,
+                                               const Control& u, float (&x)[8])
+{
+    const float vx = x[0], vy = x[1], r = x[2], wf = x[3], wr = x[4], ep = x[5], ey = x[6];
+    const float inv_vx = __fdividef(1.0f, fmaxf(vx, P.vx_floor));
+    const float yf = vy + P.lf * r;
+    const float alpha_f = u.steer - atanf(yf * inv_vx);
+    const float alpha_r = -atanf((vy - P.lr * r) * inv_vx);
+    const float vwf = fmaf(vx, u.cos_steer, yf * u.sin_steer);
+    const float kf = __fdividef(fmaf(P.Rw, wf, -vwf), fmaxf(fabsf(vwf), P.slip_floor));
+    const float kr = __fdividef(fmaf(P.Rw, wr, -vx), fmaxf(fabsf(vx), P.slip_floor));
+    const float gf = tyre_ratio(P, sqrtf(fmaf(kf, kf, alpha_f * alpha_f)));
+    const float gr = tyre_ratio(P, sqrtf(fmaf(kr, kr, alpha_r * alpha_r)));
+    const float Fxf = P.Dxf * gf * kf, Fyf = P.Df * gf * alpha_f;
+    const float Fxr = P.Dxr * gr * kr, Fyr = P.Dr * gr * alpha_r;
+    const float FXf = fmaf(Fxf, u.cos_steer, -Fyf * u.sin_steer);
+    const float FYf = fmaf(Fxf, u.sin_steer, Fyf * u.cos_steer);
+    const float kap_s = track_curvature(P, kap, s0 + x[7]);
+    float sp, cp;
+    sincos_series(ep, &sp, &cp);
+    const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
+    const float dvx = fmaf(FXf + Fxr, P.inv_m, vy * r);
+    const float dvy = fmaf(FYf + Fyr, P.inv_m, -vx * r);
+    const float dr = (P.lf * FYf - P.lr * Fyr) * P.inv_Iz;
+    const float dwf = -P.Rw * Fxf * P.inv_Iw;
+    const float dwr = fmaf(P.tau_max, u.accel, -P.Rw * Fxr) * P.inv_Iw;
+    const float dep = r - kap_s * sdot;
+    const float dey = vx * sp + vy * cp;
+    x[0] = fmaf(P.h, dvx, vx);
+    x[1] = fmaf(P.h, dvy, vy);
+    x[2] = fmaf(P.h, dr, r);
+    x[3] = fmaf(P.h, dwf, wf);
+    x[4] = fmaf(P.h, dwr, wr);
+    x[5] = fmaf(P.h, dep, ep);
+    x[6] = fmaf(P.h, dey, ey);
+    x[7] = fmaf(P.h, sdot, x[7]);
 }
 
 // Tape of one bicycle substep: the transcendental results its adjoint needs
@@ -331,6 +393,8 @@ __device__ __forceinline__ void model_step(const DevParams& P, const float* __re
 {
     if constexpr (MODEL == 0) {
         for (int j = 0; j < P.n_sub; ++j) bicycle_substep(P, kap, s0, u, x);
+    } else if constexpr (MODEL == 2) {
+        for (int j = 0; j < P.n_sub; ++j) wheels_substep(P, kap, s0, u, x);
     } else {
         double_integrator_step(P, u, x);
     }
@@ -367,8 +431,8 @@ struct ConSet {
     int kind[kMaxCon];      // 0: half-space a^T x - b; 1: disk r^2 - |D (x - o)|^2 on two states
     float nu[kMaxCon];      // back-off coefficient
     float b[kMaxCon];       // half-space offset b; disk: r^2
-    float a[kMaxCon][6];    // half-space normal a; disk: the selector D (1 on its two states)
-    float o[kMaxCon][6];    // disk centre on its two states (0 elsewhere)
+    float a[kMaxCon][kNxMax];  // half-space normal a; disk: the selector D (1 on its two states)
+    float o[kMaxCon][kNxMax];  // disk centre on its two states (0 elsewhere)
 };
 
 // c_q(m) and eta = grad c_q(m).

@@ -302,7 +302,7 @@ __device__ __noinline__ void block_partial(const int K, const int T, const int s
 // ticket) merges the partials in block order and writes v+ = v + N / eta, u0, the normalised weights,
 // the diagnostics and the counter (tail_merge). No block waits for another.
 template <int MODEL, int P, bool COMP, bool FULL>
-__global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const DevParams dp, const RollIO io,
+__global__ void __launch_bounds__(roll_max_threads<MODEL, P>()) rollout_kernel(const DevParams dp, const RollIO io,
                                                                        const TailIO tail, const ConSet cs)
 {
     extern __shared__ float smem[];
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(roll_max_threads<P>()) rollout_kernel(const De
     float* u_s = v_s + TN;
     float* red = u_s + (size_t)wpb * dp.spw * TN;  // tail scratch: max(TN, threads) floats
 
-    if constexpr (MODEL == 0) {
+    if constexpr (MODEL != 1) {
         for (int i = threadIdx.x; i <= ntab; i += blockDim.x) kap_s[i] = dp.kappa[i];
     }
     for (int i = threadIdx.x; i < TN; i += blockDim.x) v_s[i] = io.v[i];
@@ -373,7 +373,9 @@ static cudaError_t launch_model(const DevParams& dp, const RollIO& io, const Tai
     case 1: return launch_one<MODEL, 1, COMP, FULL>(dp, io, tail, cs, L, st);
     case 2: return launch_one<MODEL, 2, COMP, FULL>(dp, io, tail, cs, L, st);
     case 4: return launch_one<MODEL, 4, COMP, FULL>(dp, io, tail, cs, L, st);
-    case 8: return launch_one<MODEL, 8, COMP, FULL>(dp, io, tail, cs, L, st);
+    case 8:
+        if constexpr (MODEL != 2) return launch_one<MODEL, 8, COMP, FULL>(dp, io, tail, cs, L, st);
+        else return cudaErrorInvalidValue;  // the wheel-speed model takes M <= 128
     default: return cudaErrorInvalidValue;
     }
 }
@@ -393,7 +395,7 @@ static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
     e = cudaFuncGetAttributes(&attr, kern);
     if (e != cudaSuccess) return e;
     sms = std::min(sms, kTailMaxBlocks);
-    const int max_w = roll_max_threads<P>() / kWarp;
+    const int max_w = roll_max_threads<MODEL, P>() / kWarp;
     const size_t optin_dynamic = (size_t)optin > attr.sharedSizeBytes ? (size_t)optin - attr.sharedSizeBytes : 0;
     const size_t smem_cap = std::min(rollout_smem_bytes(dp, max_w), optin_dynamic);
     if (rollout_smem_bytes(dp, 1) > smem_cap) return cudaErrorInvalidValue;  // one warp's share does not fit
@@ -430,7 +432,9 @@ static cudaError_t plan_model(const DevParams& dp, int P, RollLaunch& L)
     case 1: return plan_one<MODEL, 1, COMP, FULL>(dp, L);
     case 2: return plan_one<MODEL, 2, COMP, FULL>(dp, L);
     case 4: return plan_one<MODEL, 4, COMP, FULL>(dp, L);
-    case 8: return plan_one<MODEL, 8, COMP, FULL>(dp, L);
+    case 8:
+        if constexpr (MODEL != 2) return plan_one<MODEL, 8, COMP, FULL>(dp, L);
+        else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }
@@ -441,6 +445,10 @@ static cudaError_t plan_model(const DevParams& dp, int P, RollLaunch& L)
 cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L)
 {
     if (full && !comp) return cudaErrorInvalidValue;
+    if (dp.nx == 8) {
+        if (full) return plan_model<2, true, true>(dp, P, L);
+        return comp ? plan_model<2, true, false>(dp, P, L) : plan_model<2, false, false>(dp, P, L);
+    }
     if (dp.nx == 6) {
         if (full) return plan_model<0, true, true>(dp, P, L);
         return comp ? plan_model<0, true, false>(dp, P, L) : plan_model<0, false, false>(dp, P, L);
@@ -456,6 +464,11 @@ cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaun
     RollIO io{x0, Sigma0, v, ctr, S, eps, mean, var};
     const bool full = dp.resample || cs.n > 0;
     if (full && !comp) return cudaErrorInvalidValue;
+    if (dp.nx == 8) {
+        if (full) return launch_model<2, true, true>(dp, io, tail, cs, P, L, st);
+        return comp ? launch_model<2, true, false>(dp, io, tail, cs, P, L, st)
+                    : launch_model<2, false, false>(dp, io, tail, cs, P, L, st);
+    }
     if (dp.nx == 6) {
         if (full) return launch_model<0, true, true>(dp, io, tail, cs, P, L, st);
         return comp ? launch_model<0, true, false>(dp, io, tail, cs, P, L, st)
@@ -472,7 +485,8 @@ template <int MODEL>
 __global__ void model_step_kernel(const DevParams dp, const float* __restrict__ xin, const float* __restrict__ uin,
                                   const float* __restrict__ win, float* __restrict__ xout, int64_t n)
 {
-    constexpr int NX = MODEL == 0 ? 6 : 4;
+    constexpr int NX = model_nx(MODEL);
+    constexpr int SI = model_s_index(MODEL);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float x[NX];
@@ -483,12 +497,12 @@ __global__ void model_step_kernel(const DevParams dp, const float* __restrict__ 
     c.accel = uin[2 * i + 1];
     sincosf(c.steer, &c.sin_steer, &c.cos_steer);
     float s0 = 0.0f;
-    if constexpr (MODEL == 0) {
-        s0 = x[5];
-        x[5] = 0.0f;
+    if constexpr (SI >= 0) {
+        s0 = x[SI];
+        x[SI] = 0.0f;
     }
     model_step<MODEL, NX>(dp, dp.kappa, s0, c, x);
-    if constexpr (MODEL == 0) x[5] += s0;
+    if constexpr (SI >= 0) x[SI] += s0;
 #pragma unroll
     for (int j = 0; j < NX; ++j) xout[i * NX + j] = x[j] + (win != nullptr ? win[i * NX + j] : 0.0f);
 }
@@ -500,6 +514,7 @@ cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* 
     const int threads = 128;
     const dim3 grid((unsigned)((n + threads - 1) / threads));
     if (dp.nx == 6) model_step_kernel<0><<<grid, threads, 0, st>>>(dp, x, u, w, xn, n);
+    else if (dp.nx == 8) model_step_kernel<2><<<grid, threads, 0, st>>>(dp, x, u, w, xn, n);
     else model_step_kernel<1><<<grid, threads, 0, st>>>(dp, x, u, w, xn, n);
     return cudaGetLastError();
 }

@@ -225,10 +225,13 @@ __device__ __forceinline__ void cholesky_psd(const float* A, float (&L)[NX][NX])
     }
 }
 
-// Largest block each particle count is compiled for (bounds the registers ptxas may use).
-template <int P>
-constexpr int roll_max_threads()
+// Largest block each model and particle count is compiled for (bounds the registers ptxas may use:
+// 65536 / threads per thread). The 8-state wheel-speed model holds 8 states per particle and needs
+// more registers per thread, so its blocks are smaller.
+template <int MODEL, int P>
+__host__ __device__ constexpr int roll_max_threads()
 {
+    if constexpr (MODEL == 2) return P == 1 ? 640 : (P == 2 ? 512 : 384);
     return P == 1 ? 1024 : (P == 2 ? 896 : (P == 4 ? 768 : 512));
 }
 
@@ -243,8 +246,9 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
                                                const float* __restrict__ v_s, float* __restrict__ my_u, int group,
                                                uint32_t ctr, const ConSet* cs = nullptr)
 {
-    constexpr int NX = MODEL == 0 ? 6 : 4;
-    constexpr int EY = MODEL == 0 ? 4 : 1;
+    constexpr int NX = model_nx(MODEL);
+    constexpr int EY = MODEL == 0 ? 4 : (MODEL == 2 ? 6 : 1);
+    constexpr int SI = model_s_index(MODEL);  // path coordinate, carried relative to its start (or -1)
     const int lane = threadIdx.x & (kWarp - 1);
     const int seg = dp.seg;
     const int ls = lane & (seg - 1);
@@ -274,12 +278,12 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
     float x0[NX];
 #pragma unroll
     for (int i = 0; i < NX; ++i) x0[i] = io.x0[i];
-    const float s0 = (MODEL == 0) ? x0[5] : 0.0f;
+    const float s0 = (SI >= 0) ? x0[SI] : 0.0f;
     float x[P][NX];
 #pragma unroll
     for (int p = 0; p < P; ++p)
 #pragma unroll
-        for (int i = 0; i < NX; ++i) x[p][i] = (MODEL == 0 && i == 5) ? 0.0f : x0[i];
+        for (int i = 0; i < NX; ++i) x[p][i] = (i == SI) ? 0.0f : x0[i];
     float var0_ey = 0.0f;
     float var0[NX];
 #pragma unroll
@@ -357,11 +361,16 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         Control c;
         c.steer = u0;
         c.accel = u1;
-        if constexpr (MODEL == 0) sincosf(u0, &c.sin_steer, &c.cos_steer);
+        if constexpr (MODEL != 1) sincosf(u0, &c.sin_steer, &c.cos_steer);
         if constexpr (MODEL == 0) {
             for (int j = 0; j < dp.n_sub; ++j) {
 #pragma unroll
                 for (int p = 0; p < P; ++p) bicycle_substep(dp, kap_s, s0, c, x[p]);
+            }
+        } else if constexpr (MODEL == 2) {
+            for (int j = 0; j < dp.n_sub; ++j) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) wheels_substep(dp, kap_s, s0, c, x[p]);
             }
         } else {
 #pragma unroll
@@ -386,7 +395,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
                 float ma[NX];
 #pragma unroll
                 for (int i = 0; i < NX; ++i) ma[i] = mean[i];
-                if constexpr (MODEL == 0) ma[5] += s0;
+                if constexpr (SI >= 0) ma[SI] += s0;
                 h_next = general_barrier<NX>(*cs, ma, C);
             }
             if (dp.resample && t + 1 < dp.T) {  // re-draw x^n_{t+1} ~ N(mean, cov) for the next step (stream 4)
@@ -403,7 +412,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         } else {
             belief_moments<NX, EY, P, COMP>(dp, x, ls, seg, dp.record != 0, mean, var);
         }
-        if constexpr (MODEL == 0) mean[5] += s0;
+        if constexpr (SI >= 0) mean[SI] += s0;
         h_prev = h_cur;
         h_cur = general ? h_next : belief_barrier(dp, mean[EY], var[EY]);
         if (dp.record && writer) {

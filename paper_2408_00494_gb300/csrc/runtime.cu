@@ -15,7 +15,7 @@ struct bssmppi_ctx {
     int P = 1;            // particles per lane (1, 2, 4 or 8)
     bss::RollLaunch roll; // persistent rollout launch shape
     bss::ConSet cons{};   // general constraint set (n = 0: the racing barrier)
-    int nx = 6;
+    int nx = 6;           // 4, 6 or 8 states
     cudaStream_t stream = nullptr;
     int device = 0;
     float* d_kappa = nullptr;
@@ -124,12 +124,18 @@ int validate(const bssmppi_params* p, std::string& why)
     if (p->K < 1 || p->K > BSSMPPI_K_MAX) return bad("K out of range [1, 2^20]");
     if (p->M < 2 || p->M > BSSMPPI_M_MAX) return bad("M out of range [2, 256] (an unbiased variance needs M >= 2)");
     if (p->T < 1 || p->T > BSSMPPI_T_MAX) return bad("T out of range [1, 256]");
-    if (p->model != BSSMPPI_MODEL_BICYCLE6 && p->model != BSSMPPI_MODEL_DOUBLE_INT4) return bad("unknown model");
+    if (p->model != BSSMPPI_MODEL_BICYCLE6 && p->model != BSSMPPI_MODEL_DOUBLE_INT4 && p->model != BSSMPPI_MODEL_WHEELS8)
+        return bad("unknown model");
     if (p->model == BSSMPPI_MODEL_BICYCLE6 && p->ey_index != 4) return bad("bicycle model constrains e_y: ey_index must be 4");
+    if (p->model == BSSMPPI_MODEL_WHEELS8 && p->ey_index != 6) return bad("wheel-speed model constrains e_y: ey_index must be 6");
+    if (p->model == BSSMPPI_MODEL_WHEELS8 && p->M > 128) return bad("the wheel-speed model takes M <= 128");
+    if (p->model == BSSMPPI_MODEL_WHEELS8 &&
+        !(p->wheel_radius > 0 && p->wheel_inertia > 0 && p->mu_x > 0 && p->tau_max >= 0 && p->slip_floor > 0))
+        return bad("wheel constants must be > 0 (tau_max >= 0)");
     if (p->model == BSSMPPI_MODEL_DOUBLE_INT4 && p->ey_index != 1) return bad("double integrator constrains p_y: ey_index must be 1");
     if (p->n_sub < 1 || p->n_sub > 64) return bad("n_sub out of range [1, 64]");
     if (!(p->dt > 0.0f)) return bad("dt must be > 0");
-    if (p->model == BSSMPPI_MODEL_BICYCLE6) {
+    if (p->model != BSSMPPI_MODEL_DOUBLE_INT4) {
         if (!(p->mass > 0 && p->Iz > 0 && p->lf > 0 && p->lr > 0 && p->g > 0 && p->vx_floor > 0)) return bad("model constants must be > 0");
         if (!p->track_kappa) return bad("track_kappa is NULL");
         if (!is_pow2(p->n_track) || p->n_track < 2 || p->n_track > BSSMPPI_NTRACK_MAX) return bad("n_track must be a power of two in [2, 16384]");
@@ -186,8 +192,8 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
 {
     int rc = validate(p, why);
     if (rc != BSSMPPI_OK) return rc;
-    const int nx = p->model == BSSMPPI_MODEL_BICYCLE6 ? 6 : 4;
-    double Lw[36], Le[4];
+    const int nx = p->model == BSSMPPI_MODEL_BICYCLE6 ? 6 : (p->model == BSSMPPI_MODEL_WHEELS8 ? 8 : 4);
+    double Lw[64], Le[4];
     if (!cholesky_psd(nx, p->Sigma_w, Lw)) {
         why = "Sigma_w must be symmetric positive semidefinite";
         return BSSMPPI_EINVAL;
@@ -205,7 +211,7 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.K = p->K; d.M = p->M; d.T = p->T; d.nx = nx;
     d.seg = seg; d.spw = 32 / seg;
     d.uniform = (p->M == seg * P) ? 1 : 0;
-    d.n_sub = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_sub : 1;
+    d.n_sub = p->model == BSSMPPI_MODEL_DOUBLE_INT4 ? 1 : p->n_sub;
     d.ey = p->ey_index; d.crn = p->crn_disturbance ? 1 : 0; d.record = p->record_moments ? 1 : 0;
     d.resample = p->resample ? 1 : 0;
     d.k_off = 0;
@@ -221,13 +227,23 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.Df = (float)((double)p->mu * p->mass * p->g * p->lr / ((double)p->lf + p->lr));
     d.Dr = (float)((double)p->mu * p->mass * p->g * p->lf / ((double)p->lf + p->lr));
     d.vx_floor = p->vx_floor;
+    if (p->model == BSSMPPI_MODEL_WHEELS8) {
+        const double L = (double)p->lf + p->lr;
+        d.Dxf = (float)((double)p->mu_x * p->mass * p->g * p->lr / L);
+        d.Dxr = (float)((double)p->mu_x * p->mass * p->g * p->lf / L);
+        d.Rw = p->wheel_radius;
+        d.inv_Iw = 1.0f / p->wheel_inertia;
+        d.tau_max = p->tau_max;
+        d.slip_floor = p->slip_floor;
+        d.CB = p->tire_C * p->tire_B;
+    }
     d.umin0 = p->u_min[0]; d.umin1 = p->u_min[1]; d.umax0 = p->u_max[0]; d.umax1 = p->u_max[1];
     d.Le00 = (float)Le[0]; d.Le10 = (float)Le[2]; d.Le11 = (float)Le[3];
     const double* Se = p->Sigma_eps;
     const double det = Se[0] * Se[3] - Se[1] * Se[2];
     d.Si00 = (float)(Se[3] / det); d.Si01 = (float)(-Se[1] / det);
     d.Si10 = (float)(-Se[2] / det); d.Si11 = (float)(Se[0] / det);
-    for (int i = 0; i < 21; ++i) d.Lw[i] = 0.0f;
+    for (int i = 0; i < 36; ++i) d.Lw[i] = 0.0f;
     d.lw_diag = 1;
     for (int i = 0; i < nx; ++i)
         for (int j = 0; j <= i; ++j) {
@@ -240,15 +256,16 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.one_m_gamma = 1.0f - p->gamma;
     d.ctrl_w = p->ctrl_w; d.Csafe = p->C_safe; d.Cobs = p->C_obs; d.wT = p->w_T;
     d.mean_mask = 0;
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 8; ++i) {
         d.xg[i] = p->x_goal[i];
         d.Q[i] = i < nx ? p->Q[i] : 0.0f;
         d.Qf[i] = i < nx ? p->Qf[i] : 0.0f;
         if (i < nx && (d.Q[i] != 0.0f || d.Qf[i] != 0.0f || i == p->ey_index || p->record_moments)) d.mean_mask |= 1 << i;
     }
-    const int ntab = p->model == BSSMPPI_MODEL_BICYCLE6 ? p->n_track : 2;
+    const bool track = p->model != BSSMPPI_MODEL_DOUBLE_INT4;
+    const int ntab = track ? p->n_track : 2;
     d.n_track_mask = ntab - 1;
-    d.track_scale = p->model == BSSMPPI_MODEL_BICYCLE6 ? (float)((double)ntab / p->track_len) : 0.0f;
+    d.track_scale = track ? (float)((double)ntab / p->track_len) : 0.0f;
     d.Mf = (float)p->M; d.invM = 1.0f / (float)p->M; d.invM1 = 1.0f / (float)(p->M - 1);
     return BSSMPPI_OK;
 }
@@ -295,18 +312,19 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     if (rc == BSSMPPI_OK && p->record_moments) rc = alloc(h, &h->d_mean, K * (T + 1) * nx);
     if (rc == BSSMPPI_OK && p->record_moments) rc = alloc(h, &h->d_var, K * (T + 1) * nx);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_v, T * 2);
-    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_x0, 6);
-    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_Sigma0, 36);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_x0, 8);
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_Sigma0, 64);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_u0, 2);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_diag, BSSMPPI_NDIAG);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ctr, 1);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_partial, (size_t)G * T * 2);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ticket, 1);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_tail_part, (size_t)bss::kTailMaxBlocks * (3 + 2 * T));
-    if (rc == BSSMPPI_OK && p->M <= 256) rc = alloc(h, &h->d_repair_X, bss::repair_scratch_floats(h->dp));
+    const bool repairable = p->M <= 256 && p->model != BSSMPPI_MODEL_WHEELS8;  // the repair has no 8-state adjoint
+    if (rc == BSSMPPI_OK && repairable) rc = alloc(h, &h->d_repair_X, bss::repair_scratch_floats(h->dp));
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_repair_J, 1);
     if (rc == BSSMPPI_OK) {
-        e = cudaMallocHost(reinterpret_cast<void**>(&h->h_stage), sizeof(float) * (6 + 36 + 2 * T + 2));
+        e = cudaMallocHost(reinterpret_cast<void**>(&h->h_stage), sizeof(float) * (8 + 64 + 2 * T + 2));
         if (e != cudaSuccess) {
             h->h_stage = nullptr;
             rc = fail(h, BSSMPPI_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
@@ -315,7 +333,7 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     if (rc == BSSMPPI_OK) {
         std::string step;
         e = cudaSuccess;
-        if (p->model == BSSMPPI_MODEL_BICYCLE6) {
+        if (p->model != BSSMPPI_MODEL_DOUBLE_INT4) {  // the track models read the curvature table
             float* tab = new float[ntab + 1];
             std::memcpy(tab, p->track_kappa, sizeof(float) * ntab);
             tab[ntab] = tab[0];
@@ -329,7 +347,7 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
         if (e == cudaSuccess) e = cudaMemset(h->d_ticket, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(h->d_diag, 0, sizeof(float) * BSSMPPI_NDIAG);
         if (e == cudaSuccess) e = bss::rollout_prepare(h->dp, h->P, p->compensated != 0, h->dp.resample != 0, h->roll);
-        if (e == cudaSuccess) e = bss::repair_prepare(h->dp);
+        if (e == cudaSuccess && repairable) e = bss::repair_prepare(h->dp);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = cuda_fail(h, e, "create");
     }
@@ -370,8 +388,8 @@ int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, fl
     if (!h_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
     const int nx = h->nx, T = h->prm.T;
     float* sx0 = h->h_stage;
-    float* sS0 = sx0 + 6;
-    float* sv = sS0 + 36;
+    float* sS0 = sx0 + 8;
+    float* sv = sS0 + 64;
     float* su0 = sv + 2 * T;
     std::memcpy(sx0, h_x0, sizeof(float) * nx);
     BSS_CUDA(h, cudaMemcpyAsync(h->d_x0, sx0, sizeof(float) * nx, cudaMemcpyHostToDevice, h->stream));
@@ -451,7 +469,7 @@ int bssmppi_set_constraints(bssmppi_t h, const bssmppi_constraint* cons, int32_t
         if (c.kind == BSSMPPI_CON_HALFSPACE) {
             cs.kind[q] = 0;
             cs.b[q] = c.b;
-            for (int l = 0; l < 6; ++l) {
+            for (int l = 0; l < 8; ++l) {
                 if (!std::isfinite(c.a[l])) return fail(h, BSSMPPI_EINVAL, "half-space normal must be finite");
                 cs.a[q][l] = l < h->nx ? c.a[l] : 0.0f;
             }
@@ -544,7 +562,7 @@ int bssmppi_repair_grad(bssmppi_t h, const float* d_x0, const float* d_v, float*
 {
     if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
     if (!d_x0 || !d_grad) return fail(h, BSSMPPI_EINVAL, "x0 and grad must be non-NULL");
-    if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256");
+    if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256 and the bicycle or linear model");
     if (h->prm.resample) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates persistent particles (resample = 0)");
     if (h->cons.n > 0) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates the racing barrier (no constraint set)");
     const float* v = d_v ? d_v : h->d_v;
@@ -559,7 +577,7 @@ int bssmppi_repair(bssmppi_t h, const float* d_x0, float* d_v, int32_t iters, fl
     if (!d_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
     if (iters < 1 || iters > 1000) return fail(h, BSSMPPI_EINVAL, "iters must be in [1, 1000]");
     if (!(step >= 0.0f) || !std::isfinite(step)) return fail(h, BSSMPPI_EINVAL, "step must be finite and >= 0");
-    if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256");
+    if (!h->d_repair_X) return fail(h, BSSMPPI_ENOTSUP, "repair needs M <= 256 and the bicycle or linear model");
     if (h->prm.resample) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates persistent particles (resample = 0)");
     if (h->cons.n > 0) return fail(h, BSSMPPI_ENOTSUP, "repair differentiates the racing barrier (no constraint set)");
     BSS_CUDA(h, bss::repair_launch(h->dp, d_x0, d_v ? d_v : h->d_v, h->d_ctr, h->d_repair_X, nullptr, d_J, iters,

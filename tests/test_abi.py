@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_params_layout_and_version():
     L = bssmppi.load()
-    assert L.bssmppi_abi_version() == 1
+    assert L.bssmppi_abi_version() == 2
     assert L.bssmppi_params_size() == ctypes.sizeof(bssmppi.Params)
 
 
