@@ -59,7 +59,7 @@ struct ServeResult {
 };
 
 template <int P>
-__global__ void __launch_bounds__(kServeWarps * kWarp, 6) serve_rollout_kernel(ServeHeader* hdr, const ServeReq* reqs,
+__global__ void __launch_bounds__(kServeWarps * kWarp, 4) serve_rollout_kernel(ServeHeader* hdr, const ServeReq* reqs,
                                                                           const DevParams* ctrl_dp, float* arena,
                                                                           const float* ctrl_v, const uint32_t* ctrl_ctr,
                                                                           int cls, int T_max)
