@@ -11,7 +11,9 @@
  *     c2 = sample index k (0 for every sample when disturbance draws are shared)
  *     c3 = (stream << 28) | (solve counter & 0x0fffffff);
  *     streams: 0 control noise, 1 state disturbance, 3 initial particles, 4 per-step re-draws of
- *     the particles (only when the problem asks for Algorithm 2's re-sampling).
+ *     the particles (only when the problem asks for Algorithm 2's re-sampling). For 6 states the
+ *     disturbance pairs particles n and n + H, H = 2^ceil(log2 M) / 2, on one counter whose word 1
+ *     is the lower index (see draw_disturbance).
  *   Uniforms from two 32-bit words a, b: u1 = ((a >> 8) + 1) 2^-24 in (0, 1],
  *   u2 = (b >> 8) 2^-24 in [0, 1); Box-Muller z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
  *   Gaussian pair i of a draw comes from call i/2, words (2(i%2), 2(i%2)+1).
@@ -324,6 +326,30 @@ static void draw_normals(const orc_problem* p, int n_out, uint32_t t, uint32_t n
     }
 }
 
+/* The state disturbance of particle n at step t. For 6 states, particles n and n + H with
+ * H = 2^ceil(log2 M) / 2 share one counter (word 1 = n mod H, the lower index): calls 0-2 give six
+ * Gaussian pairs, pairs 0-2 to the lower particle and pairs 3-5 to the upper one, so no word is
+ * drawn unused. Other state counts draw per particle (4 or 8 normals use whole calls). */
+static void draw_disturbance(const orc_problem* p, int nx, uint32_t t, uint32_t n, uint32_t kk, uint32_t solve_ctr,
+                             double* z)
+{
+    if (nx != 6) {
+        draw_normals(p, nx, t, n, kk, 1, solve_ctr, z);
+        return;
+    }
+    uint32_t pw = 1;
+    while (pw < (uint32_t)p->M) pw <<= 1;
+    const uint32_t H = pw / 2;
+    const uint32_t half = n >= H ? 1u : 0u, q = n - half * H;
+    double pairs[12];
+    for (int i = 0; i < 6; ++i) {
+        uint32_t w[4];
+        philox_words(p, t | ((uint32_t)(i / 2) << 16), q, kk, 1, solve_ctr, w);
+        orc_gaussian_pair(w[2 * (i % 2)], w[2 * (i % 2) + 1], pairs + 2 * i);
+    }
+    for (int i = 0; i < 6; ++i) z[i] = pairs[6 * half + i];
+}
+
 /* Belief barrier, Eq. "DCBF": h = (w_T - nu sigma_y)^2 - mean_ey^2 with sigma_y^2 the (e_y, e_y)
  * entry of the covariance (eta = gradient of the boundary constraint = unit vector on e_y). */
 static double belief_h(const orc_problem* p, double nu, const double* mean, const double* cov, int nx)
@@ -470,7 +496,7 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
             for (int n = 0; n < M; ++n) {
                 double xn[8], w[8], z[8];
                 orc_model_step(p, X + n * nx, uk, xn);
-                draw_normals(p, nx, (uint32_t)k, (uint32_t)n, kk, 1, solve_ctr, z);
+                draw_disturbance(p, nx, (uint32_t)k, (uint32_t)n, kk, solve_ctr, z);
                 for (int i = 0; i < nx; ++i) {
                     w[i] = 0.0;
                     for (int j = 0; j <= i; ++j) w[i] += L_w[i * nx + j] * z[j];
@@ -638,7 +664,7 @@ double orc_repair_objective(const orc_problem* p, const double* x0, const double
             const double* xc = X + ((size_t)t * M + n) * nx;
             double* xo = X + ((size_t)(t + 1) * M + n) * nx;
             orc_model_step(p, xc, v + 2 * t, xn);
-            draw_normals(p, nx, (uint32_t)t, (uint32_t)n, 0u, 1, solve_ctr, z);
+            draw_disturbance(p, nx, (uint32_t)t, (uint32_t)n, 0u, solve_ctr, z);
             for (int i = 0; i < nx; ++i) {
                 double w = 0.0;
                 for (int j = 0; j <= i; ++j) w += L_w[i * nx + j] * z[j];

@@ -41,6 +41,19 @@ def normals(n_out, t, n, k, stream, ctr, seed):
     return z[:n_out]
 
 
+def disturbance(nx, t, n, k, ctr, seed, M):
+    """Disturbance normals of particle n: for 6 states the particles n and n + H (H = half the
+    smallest power of two >= M) share a counter keyed by the lower index and split its six pairs."""
+    if nx != 6:
+        return normals(nx, t, n, k, 1, ctr, seed)
+    H = 1
+    while 2 * H < M:
+        H *= 2
+    upper = n >= H
+    twelve = normals(12, t, n - H if upper else n, k, 1, ctr, seed)
+    return twelve[6:] if upper else twelve[:6]
+
+
 def chol(A):
     n = len(A)
     L = [[0.0] * n for _ in range(n)]
@@ -123,7 +136,7 @@ def solve(P, x0, v, ctr):
         for t in range(T):
             for n in range(M):
                 xn = f_model(P, X[n], U[t])
-                z = normals(nx, t, n, kk, 1, ctr, P["seed"])
+                z = disturbance(nx, t, n, kk, ctr, P["seed"], M)
                 X[n] = [xn[i] + sum(Lw[i][j] * z[j] for j in range(i + 1)) for i in range(nx)]
             mean = [sum(X[n][i] for n in range(M)) / M for i in range(nx)]
             cov = [[sum((X[n][i] - mean[i]) * (X[n][j] - mean[j]) for n in range(M)) / (M - 1)
