@@ -27,6 +27,7 @@ struct DevParams {
     int k_off;        // global index of the handle's first sample (a shard of a larger K); 0 otherwise
     int K_norm;       // samples of the whole (possibly sharded) solve: K unless sharded
     int lw_diag;      // 1: Sigma_w is diagonal, so its Cholesky factor is (the disturbance needs nx products)
+    int dist_half;    // H = 2^ceil(log2 M) / 2: particles n and n + H share a disturbance counter (6 states)
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];       // Philox round keys k + r W (the key schedule, precomputed)
     float dt, h, inv_m, inv_Iz, lf, lr, tB, tC, Df, Dr, vx_floor;
@@ -125,6 +126,50 @@ __device__ __forceinline__ void draw_normals(const DevParams& P, uint32_t step, 
             z[6] = g3.x; z[7] = g3.y;
         }
     }
+}
+
+// State disturbance of one particle n at a step (stream 1). For 6 states, particles n and n + H
+// (H = dist_half) share the counter whose word 1 is the lower index: its calls 0-2 give six Gaussian
+// pairs, pairs 0-2 to the lower particle and 3-5 to the upper one, so no word goes unused. Other
+// state counts draw per particle.
+template <int NX>
+__device__ __forceinline__ void draw_disturbance(const DevParams& P, uint32_t step, uint32_t particle, uint32_t sample,
+                                                 uint32_t ctr, float (&z)[NX])
+{
+    if constexpr (NX == 6) {
+        const bool upper = particle >= (uint32_t)P.dist_half;
+        const uint32_t q = upper ? particle - (uint32_t)P.dist_half : particle;
+        const uint4 wa = draw_words(P, step, upper ? 1u : 0u, q, sample, kStreamDisturbance, ctr);
+        const uint4 wb = draw_words(P, step, upper ? 2u : 1u, q, sample, kStreamDisturbance, ctr);
+        const float2 g0 = upper ? box_muller(wa.z, wa.w) : box_muller(wa.x, wa.y);
+        const float2 g1 = upper ? box_muller(wb.x, wb.y) : box_muller(wa.z, wa.w);
+        const float2 g2 = upper ? box_muller(wb.z, wb.w) : box_muller(wb.x, wb.y);
+        z[0] = g0.x; z[1] = g0.y; z[2] = g1.x; z[3] = g1.y; z[4] = g2.x; z[5] = g2.y;
+    } else {
+        draw_normals<NX>(P, step, particle, sample, kStreamDisturbance, ctr, z);
+    }
+}
+
+// The disturbances of both particles of one 6-state pair (lower index q, upper q + H) from their
+// shared counter: three calls instead of four.
+__device__ __forceinline__ void draw_disturbance_pair(const DevParams& P, uint32_t step, uint32_t q, uint32_t sample,
+                                                      uint32_t ctr, float (&lo)[6], float (&hi)[6])
+{
+    const uint4 w0 = draw_words(P, step, 0u, q, sample, kStreamDisturbance, ctr);
+    const uint4 w1 = draw_words(P, step, 1u, q, sample, kStreamDisturbance, ctr);
+    const uint4 w2 = draw_words(P, step, 2u, q, sample, kStreamDisturbance, ctr);
+    float2 g = box_muller(w0.x, w0.y);
+    lo[0] = g.x; lo[1] = g.y;
+    g = box_muller(w0.z, w0.w);
+    lo[2] = g.x; lo[3] = g.y;
+    g = box_muller(w1.x, w1.y);
+    lo[4] = g.x; lo[5] = g.y;
+    g = box_muller(w1.z, w1.w);
+    hi[0] = g.x; hi[1] = g.y;
+    g = box_muller(w2.x, w2.y);
+    hi[2] = g.x; hi[3] = g.y;
+    g = box_muller(w2.z, w2.w);
+    hi[4] = g.x; hi[5] = g.y;
 }
 
 // x += L z with L diagonal (its diagonal entries at the packed positions i (i + 3) / 2).

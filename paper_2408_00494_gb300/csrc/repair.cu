@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
                 model_step<MODEL, NX>(dp, kap_s, s0, c, x);
             }
             float z[NX];
-            draw_normals<NX>(dp, (uint32_t)t, (uint32_t)n, 0u, kStreamDisturbance, ctr, z);
+            draw_disturbance<NX>(dp, (uint32_t)t, (uint32_t)n, 0u, ctr, z);
             add_correlated<NX>(dp.Lw, z, x);
             if (valid) {
 #pragma unroll

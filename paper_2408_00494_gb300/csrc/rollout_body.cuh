@@ -376,12 +376,28 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
 #pragma unroll
             for (int p = 0; p < P; ++p) double_integrator_step(dp, c, x[p]);
         }
+        if constexpr (NX == 6 && P >= 2) {
+            // particles p and p + P/2 of this lane are n and n + H (H = seg P / 2): one counter
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            float z[NX];
-            draw_normals<NX>(dp, (uint32_t)t, (uint32_t)(ls + seg * p), kk, kStreamDisturbance, ctr, z);
-            if (dp.lw_diag) add_diagonal<NX>(dp.Lw, z, x[p]);
-            else add_correlated<NX>(dp.Lw, z, x[p]);
+            for (int p = 0; p < P / 2; ++p) {
+                float zl[NX], zh[NX];
+                draw_disturbance_pair(dp, (uint32_t)t, (uint32_t)(ls + seg * p), kk, ctr, zl, zh);
+                if (dp.lw_diag) {
+                    add_diagonal<NX>(dp.Lw, zl, x[p]);
+                    add_diagonal<NX>(dp.Lw, zh, x[p + P / 2]);
+                } else {
+                    add_correlated<NX>(dp.Lw, zl, x[p]);
+                    add_correlated<NX>(dp.Lw, zh, x[p + P / 2]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float z[NX];
+                draw_disturbance<NX>(dp, (uint32_t)t, (uint32_t)(ls + seg * p), kk, ctr, z);
+                if (dp.lw_diag) add_diagonal<NX>(dp.Lw, z, x[p]);
+                else add_correlated<NX>(dp.Lw, z, x[p]);
+            }
         }
 
         // (a5) belief moments of step t+1, (a6) barrier.

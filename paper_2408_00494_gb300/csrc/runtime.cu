@@ -210,6 +210,7 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     while (P < ppl) P <<= 1;
     d.K = p->K; d.M = p->M; d.T = p->T; d.nx = nx;
     d.seg = seg; d.spw = 32 / seg;
+    d.dist_half = seg * P / 2;  // = 2^ceil(log2 M) / 2 for every M (seg P is the next power of two)
     d.uniform = (p->M == seg * P) ? 1 : 0;
     d.n_sub = p->model == BSSMPPI_MODEL_DOUBLE_INT4 ? 1 : p->n_sub;
     d.ey = p->ey_index; d.crn = p->crn_disturbance ? 1 : 0; d.record = p->record_moments ? 1 : 0;

@@ -41,7 +41,7 @@ constexpr int kServeSpwMax = 16;   // samples per warp when M = 2
 struct ServeReq {
     int ctrl, K, M, T;
     int seg, spw, uniform, cls;
-    int group_begin, n_groups, pad0, pad1;
+    int group_begin, n_groups, dist_half, pad1;  // dist_half: particles n and n + H share a counter
     float x0[6];
     float pad2[2];
     unsigned long long off_eps, off_S, off_w;  // float offsets into the slot arena
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kServeWarps * kWarp, 4) serve_rollout_kernel(S
         __syncwarp();
         if (lane == 0) {
             dps->K = rq.K; dps->M = rq.M; dps->T = rq.T;
-            dps->seg = rq.seg; dps->spw = rq.spw; dps->uniform = rq.uniform;
+            dps->seg = rq.seg; dps->spw = rq.spw; dps->uniform = rq.uniform; dps->dist_half = rq.dist_half;
             dps->Mf = (float)rq.M; dps->invM = 1.0f / (float)rq.M; dps->invM1 = 1.0f / (float)(rq.M - 1);
         }
         __syncwarp();
@@ -325,6 +325,7 @@ void fill_descriptors(bssmppi_server* s, Slot& sl)
         int P = 1;
         while (P < ppl) P <<= 1;
         q.seg = seg; q.spw = 32 / seg; q.uniform = (p.M == seg * P) ? 1 : 0;
+        q.dist_half = seg * P / 2;
         q.cls = class_of(p.M);
         q.n_groups = (p.K + q.spw - 1) / q.spw;
         if (hdr->cls_count[q.cls] == 0) hdr->cls_begin[q.cls] = i;
