@@ -58,7 +58,7 @@ def algorithmic_flops_per_particle_step(prob) -> float:
         model = 4 * 2 + 2 * 2  # exact ZOH step: 4 + 2 fmas
         nx = 4
     pairs = (nx + 1) // 2
-    philox_calls = (pairs + 1) // 2
+    philox_calls = pairs / 2              # nx Gaussians need nx uniform words: a call gives four
     philox = philox_calls * 10 * 10       # 10 rounds x (2 wide multiplies = 4, 2 three-way xors = 4, 2 key adds)
     box_muller = pairs * (2 + 8 + 1 + 4 + 16 + 2)
     disturbance = nx * (nx + 1) // 2 * 2 + nx  # L_w z (fmas) and x += w
