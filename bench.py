@@ -35,7 +35,7 @@ import workload  # noqa: E402
 METRIC = "particle-steps/s (K*M*T per solve)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one rollout_kernel launch, from one
 # ncu capture of the current kernel on each workload (None where none was taken).
-ROLLOUT_DRAM_BYTES = {"racing_K4096_M64_T40": None}
+ROLLOUT_DRAM_BYTES = {"racing_K4096_M64_T40": 132096}
 # Device facts used for the ALU roofline (GB300: 152 SMs, 128 FP32 lanes per SM, max SM clock).
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
@@ -515,7 +515,8 @@ def run_ours(args, rank, world, local_rank):
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 (fma) x 2070 MHz max SM clock",
                      "flops_per_particle_step": algorithmic_flops_per_particle_step(p)},
         "e2e": {"value": whole_job_throughput(units, mean_e2e_ms, world), "unit": "particle-steps/s",
-                "h2d_bytes_per_step": 4 * (p.nx + 2 * p.T), "d2h_bytes_per_step": 4 * (2 * p.T + 2)},
+                "h2d_bytes_per_step": 4 * (8 + 2 * p.T), "d2h_bytes_per_step": 4 * (2 * p.T + 2),
+                "copies_per_step": "one H2D (x0 padded to 8 floats | v) and one D2H (v+ | u0)"},
         "gpu_launches": 2 * args.steps,  # per step: the solve kernel and the shift kernel
         "resample_variant": {"ms_per_step": rs_ms, "particle_steps_per_s": units / (rs_ms * 1e-3),
                              "note": "Algorithm 2 read literally: full moments, Cholesky and re-draw of "

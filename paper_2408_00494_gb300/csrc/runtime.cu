@@ -25,8 +25,9 @@ struct bssmppi_ctx {
     float* d_mean = nullptr;
     float* d_var = nullptr;
     float* d_v = nullptr;
-    float* d_x0 = nullptr;      // staging for the host-buffer solve
-    float* d_Sigma0 = nullptr;
+    float* d_in = nullptr;      // device staging of the host-buffer solve: x0 (8) | v (2T) | Sigma0 (64)
+    float* d_x0 = nullptr;      // = d_in
+    float* d_Sigma0 = nullptr;  // = d_in + 8 + 2T
     float* d_u0 = nullptr;
     float* d_diag = nullptr;
     uint32_t* d_ctr = nullptr;
@@ -35,7 +36,7 @@ struct bssmppi_ctx {
     unsigned int* d_ticket = nullptr;
     float* d_repair_X = nullptr;  // stored particle states of the repair rollout
     float* d_repair_J = nullptr;  // objective of the last repair_grad call
-    float* h_stage = nullptr;   // pinned host staging: x0 | Sigma0 | v | u0
+    float* h_stage = nullptr;   // pinned host staging: x0 (8) | v (2T) | Sigma0 (64) || v+ (2T) | u0 (2)
     // timing ring: 2 events per recorded solve
     cudaEvent_t* ev = nullptr;
     int ev_cap = 0, ev_count = 0;
@@ -170,8 +171,9 @@ int alloc(bssmppi_ctx* h, T** ptr, size_t count)
 
 void release(bssmppi_ctx* h)
 {
-    void* ptrs[] = {h->d_kappa, h->d_S, h->d_w, h->d_eps, h->d_mean, h->d_var, h->d_v, h->d_x0, h->d_Sigma0,
-                    h->d_u0, h->d_diag, h->d_ctr, h->d_partial, h->d_ticket, h->d_repair_X, h->d_repair_J,
+    // d_x0 and d_Sigma0 live in d_in, d_u0 in d_v
+    void* ptrs[] = {h->d_kappa, h->d_S, h->d_w, h->d_eps, h->d_mean, h->d_var, h->d_v, h->d_in,
+                    h->d_diag, h->d_ctr, h->d_partial, h->d_ticket, h->d_repair_X, h->d_repair_J,
                     h->d_tail_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -312,10 +314,14 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_eps, K * T * 2);
     if (rc == BSSMPPI_OK && p->record_moments) rc = alloc(h, &h->d_mean, K * (T + 1) * nx);
     if (rc == BSSMPPI_OK && p->record_moments) rc = alloc(h, &h->d_var, K * (T + 1) * nx);
-    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_v, T * 2);
-    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_x0, 8);
-    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_Sigma0, 64);
-    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_u0, 2);
+    // the resident nominal and u0 side by side, so a host solve reads both back with one copy
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_v, T * 2 + 2);
+    if (rc == BSSMPPI_OK) h->d_u0 = h->d_v + 2 * T;
+    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_in, 8 + 2 * T + 64);
+    if (rc == BSSMPPI_OK) {
+        h->d_x0 = h->d_in;
+        h->d_Sigma0 = h->d_in + 8 + 2 * T;
+    }
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_diag, BSSMPPI_NDIAG);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ctr, 1);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_partial, (size_t)G * T * 2);
@@ -325,7 +331,7 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     if (rc == BSSMPPI_OK && repairable) rc = alloc(h, &h->d_repair_X, bss::repair_scratch_floats(h->dp));
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_repair_J, 1);
     if (rc == BSSMPPI_OK) {
-        e = cudaMallocHost(reinterpret_cast<void**>(&h->h_stage), sizeof(float) * (8 + 64 + 2 * T + 2));
+        e = cudaMallocHost(reinterpret_cast<void**>(&h->h_stage), sizeof(float) * (8 + 2 * T + 64 + 2 * T + 2));
         if (e != cudaSuccess) {
             h->h_stage = nullptr;
             rc = fail(h, BSSMPPI_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
@@ -363,22 +369,35 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     return BSSMPPI_OK;
 }
 
+namespace {
+
+// One solve launch: the rollout reads the nominal from v_in; the tail writes v+ to the resident
+// nominal and the first control to u0.
+int launch_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, const float* v_in, float* u0)
+{
+    cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 2 * h->ev_count : nullptr;
+    if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], h->stream));
+    // One launch: rollout, costs, and (in its tail) weights, update, u0, diagnostics, counter.
+    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, u0, h->d_diag, h->d_ctr, h->d_v, nullptr};
+    BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, v_in, h->d_ctr,
+                                    h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, h->stream));
+    if (ev) {
+        BSS_CUDA(h, cudaEventRecord(ev[1], h->stream));
+        ++h->ev_count;
+    }
+    return BSSMPPI_OK;
+}
+
+}  // namespace
+
 int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* d_v, float* d_u0)
 {
     if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
     if (!d_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
     const size_t vbytes = sizeof(float) * 2 * h->prm.T;
     if (d_v) BSS_CUDA(h, cudaMemcpyAsync(h->d_v, d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
-    cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 2 * h->ev_count : nullptr;
-    if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], h->stream));
-    // One launch: rollout, costs, and (in its tail) weights, update, u0, diagnostics, counter.
-    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, h->d_ctr, h->d_v, nullptr};
-    BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, h->d_v, h->d_ctr,
-                                    h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, h->stream));
-    if (ev) {
-        BSS_CUDA(h, cudaEventRecord(ev[1], h->stream));
-        ++h->ev_count;
-    }
+    const int rc = launch_solve(h, d_x0, d_Sigma0, h->d_v, d_u0 ? d_u0 : h->d_u0);
+    if (rc != BSSMPPI_OK) return rc;
     if (d_v) BSS_CUDA(h, cudaMemcpyAsync(d_v, h->d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
     return BSSMPPI_OK;
 }
@@ -388,27 +407,23 @@ int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, fl
     if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
     if (!h_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
     const int nx = h->nx, T = h->prm.T;
+    // inputs in one pinned block, copied with one H2D: x0 (8) | v (2T) | Sigma0 (64)
     float* sx0 = h->h_stage;
-    float* sS0 = sx0 + 8;
-    float* sv = sS0 + 64;
-    float* su0 = sv + 2 * T;
+    float* sv = sx0 + 8;
+    float* sS0 = sv + 2 * T;
+    float* sout = sS0 + 64;  // v+ (2T) | u0 (2), read back with one D2H
     std::memcpy(sx0, h_x0, sizeof(float) * nx);
-    BSS_CUDA(h, cudaMemcpyAsync(h->d_x0, sx0, sizeof(float) * nx, cudaMemcpyHostToDevice, h->stream));
-    if (h_Sigma0) {
-        std::memcpy(sS0, h_Sigma0, sizeof(float) * nx * nx);
-        BSS_CUDA(h, cudaMemcpyAsync(h->d_Sigma0, sS0, sizeof(float) * nx * nx, cudaMemcpyHostToDevice, h->stream));
-    }
-    if (h_v) {
-        std::memcpy(sv, h_v, sizeof(float) * 2 * T);
-        BSS_CUDA(h, cudaMemcpyAsync(h->d_v, sv, sizeof(float) * 2 * T, cudaMemcpyHostToDevice, h->stream));
-    }
-    int rc = bssmppi_solve(h, h->d_x0, h_Sigma0 ? h->d_Sigma0 : nullptr, nullptr, h->d_u0);
+    if (h_v) std::memcpy(sv, h_v, sizeof(float) * 2 * T);
+    if (h_Sigma0) std::memcpy(sS0, h_Sigma0, sizeof(float) * nx * nx);
+    const size_t n_in = h_Sigma0 ? (size_t)(8 + 2 * T + nx * nx) : (h_v ? (size_t)(8 + 2 * T) : (size_t)nx);
+    BSS_CUDA(h, cudaMemcpyAsync(h->d_in, sx0, sizeof(float) * n_in, cudaMemcpyHostToDevice, h->stream));
+    const int rc = launch_solve(h, h->d_x0, h_Sigma0 ? h->d_Sigma0 : nullptr, h_v ? h->d_in + 8 : h->d_v, h->d_u0);
     if (rc != BSSMPPI_OK) return rc;
-    if (h_v) BSS_CUDA(h, cudaMemcpyAsync(sv, h->d_v, sizeof(float) * 2 * T, cudaMemcpyDeviceToHost, h->stream));
-    if (h_u0) BSS_CUDA(h, cudaMemcpyAsync(su0, h->d_u0, sizeof(float) * 2, cudaMemcpyDeviceToHost, h->stream));
+    if (h_v || h_u0)
+        BSS_CUDA(h, cudaMemcpyAsync(sout, h->d_v, sizeof(float) * (2 * T + 2), cudaMemcpyDeviceToHost, h->stream));
     BSS_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (h_v) std::memcpy(h_v, sv, sizeof(float) * 2 * T);
-    if (h_u0) std::memcpy(h_u0, su0, sizeof(float) * 2);
+    if (h_v) std::memcpy(h_v, sout, sizeof(float) * 2 * T);
+    if (h_u0) std::memcpy(h_u0, sout + 2 * T, sizeof(float) * 2);
     return BSSMPPI_OK;
 }
 

@@ -260,16 +260,30 @@ def test_shift_matches_definition():
     c.close()
 
 
-def test_solve_host_matches_device_path():
-    p = workload.config0()
+@pytest.mark.parametrize("case", ["plain", "sigma0", "resident", "wheels8"])
+def test_solve_host_matches_device_path(case):
+    """The host-buffer solve (one H2D of x0 | v | Sigma0, one D2H of v+ | u0) gives bit for bit the
+    device-buffer solve's v+ and u0."""
+    p = workload.wheels_problem(96, 16, 12) if case == "wheels8" else workload.config0()
     x0, v = workload.random_state(p, 13), workload.random_nominal(p, 13)
-    g = gpu_solve(p, x0, v, ctr=7, record=False)
+    Sig0 = None
+    if case in ("sigma0", "wheels8"):
+        Sig0 = (np.eye(p.nx) * 0.01).astype(np.float32)
+        Sig0[0, 1] = Sig0[1, 0] = 0.002
+    g = gpu_solve(p, x0, v, ctr=7, Sigma0=Sig0, record=False)
     c = bssmppi.Controller(p)
-    bssmppi.set_counter(c.h, 7)
-    vh = v.copy()
-    u0 = np.zeros(2, np.float32)
-    bssmppi.solve_host(c.h, x0.astype(np.float32), None, vh, u0)
-    c.close()
+    try:
+        bssmppi.set_counter(c.h, 7)
+        u0 = np.zeros(2, np.float32)
+        if case == "resident":
+            bssmppi.set_nominal(c.h, _dev(v))
+            bssmppi.solve_host(c.h, x0.astype(np.float32), None, None, u0)
+            vh = c.buffer(bssmppi.BUF_V).cpu().numpy()
+        else:
+            vh = v.copy()
+            bssmppi.solve_host(c.h, x0.astype(np.float32), Sig0, vh, u0)
+    finally:
+        c.close()
     assert np.array_equal(vh.astype(np.float64), g["v_plus"])
     assert np.array_equal(u0.astype(np.float64), g["u0"])
 
