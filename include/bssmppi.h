@@ -162,8 +162,8 @@ size_t bssmppi_params_size(void);
 int bssmppi_create(const bssmppi_params* params, void* cuda_stream, bssmppi_t* out);
 
 /*
- * One BSS-MPPI solve (Algorithm 1, one iteration of its outer loop, lines from the state estimate
- * to OptimalControl, with Algorithm 2 for the mean and covariance propagation):
+ * One BSS-MPPI solve (one iteration of Algorithm 1's outer loop, from the state estimate through
+ * OptimalControl, with Algorithm 2 for the mean and covariance propagation), as one kernel launch:
  *   d_x0     [nx]      state estimate x_bar_0 (device).
  *   d_Sigma0 [nx*nx]   covariance Sigma_{x_0} of the estimate, or NULL for a known state. When given,
  *                      the particles start at x_bar_0 + L_0 xi with L_0 its Cholesky factor.
@@ -176,9 +176,10 @@ int bssmppi_create(const bssmppi_params* params, void* cuda_stream, bssmppi_t* o
 int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* d_v, float* d_u0);
 
 /*
- * The same solve with host buffers: copies h_x0 (and h_Sigma0 if non-NULL) and h_v (NULL = resident)
- * to the device, solves, copies v+ back into h_v (if non-NULL) and the first control into h_u0 (if
- * non-NULL), and waits for the stream. Synchronous; the host pointers may be pageable.
+ * The same solve with host buffers: stages h_x0, h_v (NULL = resident) and h_Sigma0 (if non-NULL)
+ * in the handle's pinned buffer and copies them to the device in one transfer, solves, reads v+ and
+ * the first control back in one transfer into h_v and h_u0 (each if non-NULL), and waits for the
+ * stream. Synchronous; the host pointers may be pageable.
  */
 int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, float* h_v, float* h_u0);
 

@@ -477,7 +477,7 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
         for (int k = 0; k < T; ++k) {
             const double* uk = u + 2 * k;
             if (p->resample && k > 0) {
-                /* Algorithm 2, first line of its loop: x^n_k ~ N(xbar_k, Sigma_k), drawn as
+                /* Algorithm 2's sampling of the particles, x^n_k ~ N(xbar_k, Sigma_k), drawn as
                  * xbar_k + L_k xi^n with L_k the (PSD) Cholesky factor of the Monte-Carlo covariance
                  * of step k and xi^n from stream 4. At k = 0 the initial particles above are the draw. */
                 double Lk[64];

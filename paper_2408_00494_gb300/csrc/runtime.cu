@@ -31,7 +31,6 @@ struct bssmppi_ctx {
     float* d_u0 = nullptr;
     float* d_diag = nullptr;
     uint32_t* d_ctr = nullptr;
-    float* d_partial = nullptr;
     float* d_tail_part = nullptr;  // block partials of the rollout's fused weights/update tail
     unsigned int* d_ticket = nullptr;
     float* d_repair_X = nullptr;  // stored particle states of the repair rollout
@@ -173,7 +172,7 @@ void release(bssmppi_ctx* h)
 {
     // d_x0 and d_Sigma0 live in d_in, d_u0 in d_v
     void* ptrs[] = {h->d_kappa, h->d_S, h->d_w, h->d_eps, h->d_mean, h->d_var, h->d_v, h->d_in,
-                    h->d_diag, h->d_ctr, h->d_partial, h->d_ticket, h->d_repair_X, h->d_repair_J,
+                    h->d_diag, h->d_ctr, h->d_ticket, h->d_repair_X, h->d_repair_J,
                     h->d_tail_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -306,7 +305,6 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     const int ntab = dp.n_track_mask + 1;
 
     const size_t K = p->K, T = p->T;
-    const int G = bss::update_blocks(p->K);
     rc = BSSMPPI_OK;
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_kappa, ntab + 1);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_S, K);
@@ -324,7 +322,6 @@ int bssmppi_create(const bssmppi_params* p, void* cuda_stream, bssmppi_t* out)
     }
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_diag, BSSMPPI_NDIAG);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ctr, 1);
-    if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_partial, (size_t)G * T * 2);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_ticket, 1);
     if (rc == BSSMPPI_OK) rc = alloc(h, &h->d_tail_part, (size_t)bss::kTailMaxBlocks * (3 + 2 * T));
     const bool repairable = p->M <= 256 && p->model != BSSMPPI_MODEL_WHEELS8;  // the repair has no 8-state adjoint

@@ -3,7 +3,9 @@
 //   v+_t = v_t + sum_k (omega_k / eta) eps_eff_{k,t}   (= sum_k omega_k u_k / eta, since the
 //   normalised weights sum to one), then u0 = v+_0 and the solve counter advances.
 //
-// One launch of G blocks. Every block first reduces beta and eta over all K costs (identical, bit
+// The standalone weights/update step behind bssmppi_update_noalloc (a solve computes the same
+// quantities in its rollout kernel's tail). One launch of G blocks. Every block first reduces beta
+// and eta over all K costs (identical, bit
 // for bit, in every block: same data, same order), then block b forms the weighted sum of its
 // chunk of samples for all T*2 outputs, reading eps_eff coalesced (thread = output, thread groups
 // stride over samples). Partial sums go to scratch; the last block to finish (atomic ticket) adds
