@@ -236,8 +236,22 @@ __device__ __forceinline__ float track_curvature(const DevParams& P, const float
     return fmaf(f, k1 - k0, k0);
 }
 
+// The heading's sine and cosine carried across the substeps of one step: seeded from the series at
+// the step's first substep, then rotated by each substep's increment d = h e_psi' (|d| << 1:
+// sin d and cos d from three-term series, errors below |d|^7/7! and |d|^6/6!).
+__device__ __forceinline__ void rotate_heading(float d, float& sp, float& cp)
+{
+    const float d2 = d * d;
+    const float cd = fmaf(d2, fmaf(d2, 4.1666667e-2f, -0.5f), 1.0f);                       // 1 - d^2/2 + d^4/24
+    const float sd = fmaf(d * d2, fmaf(d2, 8.3333333e-3f, -1.6666667e-1f), d);           // d - d^3/6 + d^5/120
+    const float s = fmaf(sp, cd, cp * sd);
+    cp = fmaf(cp, cd, -sp * sd);
+    sp = s;
+}
+
+// One explicit-Euler substep; (sp, cp) = (sin e_psi, cos e_psi) on entry and on exit.
 __device__ __forceinline__ void bicycle_substep(const DevParams& P, const float* __restrict__ kap, float s0,
-                                                const Control& u, float (&x)[6])
+                                                const Control& u, float (&x)[6], float& sp, float& cp)
 {
     const float vx = x[0], vy = x[1], r = x[2], ep = x[3], ey = x[4];
     // v_x >= vx_floor >= 1 and 1 - kappa e_y is near 1, so the fast (2-ulp) quotients are safe.
@@ -249,8 +263,6 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const float*
     const float Ff = P.Df * __sinf(P.tC * atanf(P.tB * alpha_f));
     const float Fr = P.Dr * __sinf(P.tC * atanf(P.tB * alpha_r));
     const float kap_s = track_curvature(P, kap, s0 + x[5]);
-    float sp, cp;
-    sincos_series(ep, &sp, &cp);  // e_psi multiplies v_x: an ulp-level sine, not the hardware one
     const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
     const float dvx = u.accel - Ff * u.sin_steer * P.inv_m + vy * r;
     const float dvy = (Ff * u.cos_steer + Fr) * P.inv_m - vx * r;
@@ -263,6 +275,7 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const float*
     x[3] = fmaf(P.h, dep, ep);
     x[4] = fmaf(P.h, dey, ey);
     x[5] = fmaf(P.h, sdot, x[5]);
+    rotate_heading(P.h * dep, sp, cp);
 }
 
 // Single-track model with wheel speeds and combined slip, x = [v_x, v_y, r, omega_F, omega_R, e_psi,
@@ -279,7 +292,7 @@ __device__ __forceinline__ float tyre_ratio(const DevParams& P, float sl)
 }
 
 __device__ __forceinline__ void wheels_substep(const DevParams& P, const float* __restrict__ kap, float s0,
-                                               const Control& u, float (&x)[8])
+                                               const Control& u, float (&x)[8], float& sp, float& cp)
 {
     const float vx = x[0], vy = x[1], r = x[2], wf = x[3], wr = x[4], ep = x[5], ey = x[6];
     const float inv_vx = __fdividef(1.0f, fmaxf(vx, P.vx_floor));
@@ -296,8 +309,6 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const float* 
     const float FXf = fmaf(Fxf, u.cos_steer, -Fyf * u.sin_steer);
     const float FYf = fmaf(Fxf, u.sin_steer, Fyf * u.cos_steer);
     const float kap_s = track_curvature(P, kap, s0 + x[7]);
-    float sp, cp;
-    sincos_series(ep, &sp, &cp);
     const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
     const float dvx = fmaf(FXf + Fxr, P.inv_m, vy * r);
     const float dvy = fmaf(FYf + Fyr, P.inv_m, -vx * r);
@@ -314,6 +325,7 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const float* 
     x[5] = fmaf(P.h, dep, ep);
     x[6] = fmaf(P.h, dey, ey);
     x[7] = fmaf(P.h, sdot, x[7]);
+    rotate_heading(P.h * dep, sp, cp);
 }
 
 // Tape of one bicycle substep: the transcendental results its adjoint needs
@@ -437,9 +449,13 @@ __device__ __forceinline__ void model_step(const DevParams& P, const float* __re
                                            const Control& u, float (&x)[NX])
 {
     if constexpr (MODEL == 0) {
-        for (int j = 0; j < P.n_sub; ++j) bicycle_substep(P, kap, s0, u, x);
+        float sp, cp;
+        sincos_series(x[3], &sp, &cp);
+        for (int j = 0; j < P.n_sub; ++j) bicycle_substep(P, kap, s0, u, x, sp, cp);
     } else if constexpr (MODEL == 2) {
-        for (int j = 0; j < P.n_sub; ++j) wheels_substep(P, kap, s0, u, x);
+        float sp, cp;
+        sincos_series(x[5], &sp, &cp);
+        for (int j = 0; j < P.n_sub; ++j) wheels_substep(P, kap, s0, u, x, sp, cp);
     } else {
         double_integrator_step(P, u, x);
     }

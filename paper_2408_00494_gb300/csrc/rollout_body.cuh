@@ -362,15 +362,18 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         c.steer = u0;
         c.accel = u1;
         if constexpr (MODEL != 1) sincosf(u0, &c.sin_steer, &c.cos_steer);
-        if constexpr (MODEL == 0) {
+        if constexpr (MODEL != 1) {
+            // the heading's sine and cosine: series at the step's start, rotated through the substeps
+            constexpr int HI = MODEL == 0 ? 3 : 5;
+            float hs[P], hc[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) sincos_series(x[p][HI], &hs[p], &hc[p]);
             for (int j = 0; j < dp.n_sub; ++j) {
 #pragma unroll
-                for (int p = 0; p < P; ++p) bicycle_substep(dp, kap_s, s0, c, x[p]);
-            }
-        } else if constexpr (MODEL == 2) {
-            for (int j = 0; j < dp.n_sub; ++j) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) wheels_substep(dp, kap_s, s0, c, x[p]);
+                for (int p = 0; p < P; ++p) {
+                    if constexpr (MODEL == 0) bicycle_substep(dp, kap_s, s0, c, x[p], hs[p], hc[p]);
+                    else wheels_substep(dp, kap_s, s0, c, x[p], hs[p], hc[p]);
+                }
             }
         } else {
 #pragma unroll
