@@ -96,3 +96,25 @@ def test_empty_set_restores_racing_barrier_and_bad_sets_are_rejected():
             bssmppi.repair_grad(c.h, torch.as_tensor(x0, device="cuda"), None, torch.zeros(p.T, 2, device="cuda"))
     finally:
         c.close()
+
+
+def test_switching_barriers_matches_fresh_handles():
+    """One handle switched racing -> constraint set -> racing -> constraint set gives, solve by
+    solve, the costs of fresh handles built for each configuration (same counter)."""
+    p = workload.config0()
+    x0, v = workload.random_state(p, 9), workload.random_nominal(p, 9)
+    cons = _racing_cons(p, x0)
+    expect = {}
+    for name, cs in (("racing", ()), ("set", cons)):
+        q = workload.Problem(**{**p.__dict__, "constraints": cs})
+        expect[name] = gpu_solve(q, x0, v, ctr=12, record=False)["S"]
+    c = bssmppi.Controller(p)
+    try:
+        for name in ("racing", "set", "racing", "set"):
+            bssmppi.set_constraints(c.h, cons if name == "set" else [])
+            bssmppi.set_counter(c.h, 12)
+            bssmppi.solve(c.h, torch.as_tensor(x0, device="cuda"), None, torch.as_tensor(v, device="cuda"))
+            S = c.buffer(bssmppi.BUF_S).cpu().numpy().astype(np.float64)
+            np.testing.assert_array_equal(S, expect[name])
+    finally:
+        c.close()

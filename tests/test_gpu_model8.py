@@ -38,9 +38,9 @@ def test_model_step_matches_oracle():
     assert_close(g, ref, 2e-5, 2e-5, "wheel-speed model step")
 
 
-@pytest.mark.parametrize("M", [16, 64, 128])
-def test_solve_matches_oracle(M):
-    p = workload.wheels_problem(192, M, 20)
+@pytest.mark.parametrize("M,K,crn", [(16, 192, 0), (64, 192, 0), (128, 192, 0), (16, 193, 1), (5, 77, 0)])
+def test_solve_matches_oracle(M, K, crn):
+    p = workload.wheels_problem(K, M, 20, crn_disturbance=crn)
     x0, v = workload.random_state(p, 70 + M), workload.random_nominal(p, 70 + M, scale=(0.1, 0.5))
     check_solve(p, x0, v, ctr=4)
 

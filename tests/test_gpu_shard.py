@@ -61,10 +61,16 @@ def _sharded(p, x0, v, ctr, sizes):
             c.close()
 
 
-@pytest.mark.parametrize("sizes", [(128, 128), (100, 123, 33), (1, 255)])
-def test_shards_merge_to_the_single_handle_solve(sizes):
+@pytest.mark.parametrize("sizes,variant", [((128, 128), "racing"), ((100, 123, 33), "racing"), ((1, 255), "racing"),
+                                           ((96, 160), "constraints"), ((200, 56), "resample")])
+def test_shards_merge_to_the_single_handle_solve(sizes, variant):
     p = workload.config0()
     p.K = sum(sizes)
+    if variant == "resample":
+        p.resample = 1
+    if variant == "constraints":
+        p.constraints = (workload.halfspace((0, 0, 0, 0, 1, 0), 2.5, 0.05),
+                         workload.disk(5, 4, (40.0, 0.5), 1.0, 0.1, backoff="cantelli"))
     x0, v = workload.random_state(p, 61), workload.random_nominal(p, 61)
     full = _full(p, x0, v, ctr=5)
     shards = _sharded(p, x0, v, 5, sizes)
