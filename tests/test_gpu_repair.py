@@ -63,8 +63,9 @@ def test_repair_gradient_matches_oracle_adjoint_and_finite_differences(model):
         fd = (o.repair_objective(x0, v + eps * d, ctr, grad=False)
               - o.repair_objective(x0, v - eps * d, ctr, grad=False)) / (2 * eps)
         assert float(np.sum(g * d)) == pytest.approx(fd, rel=2e-3)
-    print(f"[repair {model}] J {J:.6g} (oracle {J_ref:.6g}); grad max rel err per channel "
-          f"{(np.abs(g - g_ref).max(axis=0) / scale).tolist()}")
+    err = np.abs(g - g_ref).max(axis=0)
+    rel = [f"{e / s:.2e}" if s > 0 else f"{e:.1e} abs (gradient identically 0)" for e, s in zip(err, scale)]
+    print(f"[repair {model}] J {J:.6g} (oracle {J_ref:.6g}); grad max rel err per channel {rel}")
 
 
 def test_repair_iterations_match_oracle_projected_gradient():
