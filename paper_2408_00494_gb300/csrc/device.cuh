@@ -236,6 +236,17 @@ __device__ __forceinline__ float track_curvature(const DevParams& P, const float
     return fmaf(f, k1 - k0, k0);
 }
 
+// The same lookup from a table of (kappa_i, kappa_{i+1} - kappa_i) pairs (one 8-byte load; the
+// difference is the same FP32 subtraction, so the result is bit-identical).
+__device__ __forceinline__ float track_curvature(const DevParams& P, const float2* __restrict__ kap, float s)
+{
+    const float x = s * P.track_scale;
+    const float fl = floorf(x);
+    const float f = x - fl;
+    const float2 k = kap[((int)fl) & P.n_track_mask];
+    return fmaf(f, k.y, k.x);
+}
+
 // The heading's sine and cosine carried across the substeps of one step: seeded from the series at
 // the step's first substep, then rotated by each substep's increment d = h e_psi' (|d| << 1:
 // sin d and cos d from three-term series, errors below |d|^7/7! and |d|^6/6!).
@@ -249,8 +260,10 @@ __device__ __forceinline__ void rotate_heading(float d, float& sp, float& cp)
     sp = s;
 }
 
-// One explicit-Euler substep; (sp, cp) = (sin e_psi, cos e_psi) on entry and on exit.
-__device__ __forceinline__ void bicycle_substep(const DevParams& P, const float* __restrict__ kap, float s0,
+// One explicit-Euler substep; (sp, cp) = (sin e_psi, cos e_psi) on entry and on exit. Tab: the
+// curvature table's element (float, or float2 pairs of value and difference).
+template <typename Tab>
+__device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
                                                 const Control& u, float (&x)[6], float& sp, float& cp)
 {
     const float vx = x[0], vy = x[1], r = x[2], ep = x[3], ey = x[4];
@@ -291,7 +304,8 @@ __device__ __forceinline__ float tyre_ratio(const DevParams& P, float sl)
     return sl > 1e-6f ? __fdividef(__sinf(P.tC * atanf(P.tB * sl)), sl) : P.CB;
 }
 
-__device__ __forceinline__ void wheels_substep(const DevParams& P, const float* __restrict__ kap, float s0,
+template <typename Tab>
+__device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
                                                const Control& u, float (&x)[8], float& sp, float& cp)
 {
     const float vx = x[0], vy = x[1], r = x[2], wf = x[3], wr = x[4], ep = x[5], ey = x[6];

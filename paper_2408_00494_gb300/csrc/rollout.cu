@@ -313,13 +313,17 @@ __global__ void __launch_bounds__(roll_max_threads<MODEL, P>()) rollout_kernel(c
     const int ntab = dp.n_track_mask + 1;
     const int TN = 2 * dp.T;
     const int wpb = blockDim.x / kWarp;
-    float* kap_s = smem;
-    float* v_s = smem + ((ntab + 1 + 3) & ~3);
+    // curvature table as (kappa_i, kappa_{i+1} - kappa_i) pairs: one 8-byte load per lookup
+    float2* kap_s = reinterpret_cast<float2*>(smem);
+    float* v_s = smem + ((2 * ntab + 3) & ~3);
     float* u_s = v_s + TN;
     float* red = u_s + (size_t)wpb * dp.spw * TN;  // tail scratch: max(TN, threads) floats
 
     if constexpr (MODEL != 1) {
-        for (int i = threadIdx.x; i <= ntab; i += blockDim.x) kap_s[i] = dp.kappa[i];
+        for (int i = threadIdx.x; i < ntab; i += blockDim.x) {
+            const float k0 = dp.kappa[i];
+            kap_s[i] = make_float2(k0, dp.kappa[i + 1] - k0);
+        }
     }
     for (int i = threadIdx.x; i < TN; i += blockDim.x) v_s[i] = io.v[i];
     __syncthreads();
@@ -351,7 +355,7 @@ size_t rollout_smem_bytes(const DevParams& dp, int wpb)
 {
     const int ntab = dp.n_track_mask + 1;
     const size_t TN = 2 * (size_t)dp.T;
-    const size_t floats = (size_t)((ntab + 1 + 3) & ~3) + TN + (size_t)wpb * dp.spw * TN
+    const size_t floats = (size_t)((2 * ntab + 3) & ~3) + TN + (size_t)wpb * dp.spw * TN
                         + std::max(TN, (size_t)wpb * kWarp);
     return floats * sizeof(float);
 }

@@ -241,8 +241,8 @@ __host__ __device__ constexpr int roll_max_threads()
 // full-belief variant: every mean and the whole covariance each step, which the general constraint
 // set (cs->n > 0, Eq. "DCBFchoice") and the literal reading of Algorithm 2 (dp.resample: particles
 // re-drawn from N(mean, cov) before the next step) need; cs is read only by it.
-template <int MODEL, int P, bool COMP, bool FULL = false>
-__device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO& io, const float* __restrict__ kap_s,
+template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float>
+__device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO& io, const Tab* __restrict__ kap_s,
                                                const float* __restrict__ v_s, float* __restrict__ my_u, int group,
                                                uint32_t ctr, const ConSet* cs = nullptr)
 {
