@@ -385,7 +385,9 @@ static cudaError_t launch_model(const DevParams& dp, const RollIO& io, const Tai
 }
 
 // Block shape: one block per SM with w warps, w chosen to minimise the makespan of an issue-bound
-// kernel, ceil(groups / (SMs w)) rounds of w warps each, among the w that fit on an SM.
+// kernel, ceil(groups / (SMs w)) rounds of max(w, kSatWarps) warp-times each, among the w that fit
+// on an SM (fewer than kSatWarps warps leave issue slots idle on latency).
+constexpr int kSatWarps = 16;
 template <int MODEL, int P, bool COMP, bool FULL>
 static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
 {
@@ -416,8 +418,10 @@ static cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, w * kWarp, rollout_smem_bytes(dp, w));
         if (e != cudaSuccess) return e;
         if (nb < 1) continue;
+        // an SM issues at full rate once about kSatWarps warps hide each other's latency: a round
+        // of w warps costs max(w, kSatWarps)
         const long slots = (long)sms * w;
-        const long cost = ((groups + slots - 1) / slots) * w;
+        const long cost = ((groups + slots - 1) / slots) * std::max(w, kSatWarps);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
             best_w = w;
