@@ -309,7 +309,7 @@ def run_closed_loop(bssmppi, p, dev, stream, steps: int, seed: int = 1):
 
 
 def run_km_sweep(bssmppi, dev, stream, Ks, Ms, runs, T=20, noise_scale=4.0, v_goal=10.0, w_T=2.0,
-                 collide_at=1.8, seed0=100):
+                 collide_at=1.8, seed0=100, q_ey=(0.1,)):
     """Monte-Carlo laps over a grid of sample counts K and particle counts M (Sec. "Simulation
     Results": crash and collision rates versus the number of control sequences and of uncertainty
     trajectories). Each run starts from a seeded state near the centre line at a random lap position,
@@ -320,56 +320,57 @@ def run_km_sweep(bssmppi, dev, stream, Ks, Ms, runs, T=20, noise_scale=4.0, v_go
     import torch
 
     out = []
-    for K in Ks:
-        for M in Ms:
-            crashes = collisions = 0
-            dcbf_ok = dcbf_n = 0
-            step_s, laps_s = [], []
-            for r in range(runs):
-                p = workload.racing_problem(K, M, T, track_seed=1, noise_scale=noise_scale, lam=1.0,
-                                            seed=seed0 + r, w_T=w_T,
-                                            x_goal=(v_goal, 0.0, 0.0, 0.0, 0.0, 0.0))
-                rng = np.random.default_rng(seed0 + r)
-                x0 = np.array([v_goal * rng.uniform(0.9, 1.0), 0.0, 0.0, rng.normal(0.0, 0.02),
-                               rng.uniform(-0.5, 0.5), rng.uniform(0.0, p.track_len)], np.float32)
-                steps = int(1.25 * p.track_len / (v_goal * p.dt)) + 1
-                std = np.sqrt(np.diag(np.asarray(p.Sigma_w)))
-                W = torch.as_tensor((rng.standard_normal((steps, 6)) * std).astype(np.float32), device=dev)
-                traj = torch.empty(steps + 1, 6, device=dev)
-                traj[0] = torch.as_tensor(x0, device=dev)
-                u0 = torch.zeros(1, 2, device=dev)
-                ctl = bssmppi.Controller(p, stream=stream)
-                try:
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    for k in range(steps):
-                        bssmppi.solve(ctl.h, traj[k], None, None, u0[0])
-                        bssmppi.model_step(ctl.h, traj[k:k + 1], u0, traj[k + 1:k + 2], W[k:k + 1])
-                        bssmppi.shift(ctl.h, None, 1)
-                    torch.cuda.synchronize()
-                    step_s.append((time.perf_counter() - t0) / steps)
-                finally:
-                    ctl.close()
-                x = traj.double().cpu().numpy()
-                ey, ds = x[:, 4], x[:, 5] - x[0, 5]
-                lap = np.nonzero(ds >= p.track_len)[0]
-                end = int(lap[0]) if lap.size else steps
-                out_of = np.nonzero(~(np.abs(ey[: end + 1]) <= w_T))[0]  # NaN counts as a crash
-                if out_of.size:
-                    crashes += 1
-                    end = int(out_of[0])
-                else:
-                    laps_s.append(end * p.dt)
-                near = np.abs(ey[: end + 1]) > collide_at
-                collisions += int(near[0]) + int(np.count_nonzero(near[1:] & ~near[:-1]))
-                h = w_T * w_T - ey[: end + 1] ** 2
-                dcbf_ok += int(np.count_nonzero(h[1:] >= (1.0 - p.gamma) * h[:-1]))
-                dcbf_n += max(end, 0)
-            out.append({"K": K, "M": M, "runs": runs, "crash_rate": crashes / runs,
-                        "collision_rate": collisions / runs,
-                        "dcbf_condition_satisfied": dcbf_ok / max(dcbf_n, 1),
-                        "mean_lap_time_s": float(np.mean(laps_s)) if laps_s else None,
-                        "ms_per_closed_loop_step": 1e3 * float(np.mean(step_s))})
+    cells = [(q, K, M) for q in q_ey for K in Ks for M in Ms]
+    for qe, K, M in cells:
+        crashes = collisions = 0
+        dcbf_ok = dcbf_n = 0
+        step_s, laps_s = [], []
+        for r in range(runs):
+            p = workload.racing_problem(K, M, T, track_seed=1, noise_scale=noise_scale, lam=1.0,
+                                        seed=seed0 + r, w_T=w_T,
+                                        x_goal=(v_goal, 0.0, 0.0, 0.0, 0.0, 0.0),
+                                        Q=(1.0, 0.0, 0.0, 1.0, qe, 0.0), Qf=(1.0, 0.0, 0.0, 1.0, qe, 0.0))
+            rng = np.random.default_rng(seed0 + r)
+            x0 = np.array([v_goal * rng.uniform(0.9, 1.0), 0.0, 0.0, rng.normal(0.0, 0.02),
+                           rng.uniform(-0.5, 0.5), rng.uniform(0.0, p.track_len)], np.float32)
+            steps = int(1.25 * p.track_len / (v_goal * p.dt)) + 1
+            std = np.sqrt(np.diag(np.asarray(p.Sigma_w)))
+            W = torch.as_tensor((rng.standard_normal((steps, 6)) * std).astype(np.float32), device=dev)
+            traj = torch.empty(steps + 1, 6, device=dev)
+            traj[0] = torch.as_tensor(x0, device=dev)
+            u0 = torch.zeros(1, 2, device=dev)
+            ctl = bssmppi.Controller(p, stream=stream)
+            try:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for k in range(steps):
+                    bssmppi.solve(ctl.h, traj[k], None, None, u0[0])
+                    bssmppi.model_step(ctl.h, traj[k:k + 1], u0, traj[k + 1:k + 2], W[k:k + 1])
+                    bssmppi.shift(ctl.h, None, 1)
+                torch.cuda.synchronize()
+                step_s.append((time.perf_counter() - t0) / steps)
+            finally:
+                ctl.close()
+            x = traj.double().cpu().numpy()
+            ey, ds = x[:, 4], x[:, 5] - x[0, 5]
+            lap = np.nonzero(ds >= p.track_len)[0]
+            end = int(lap[0]) if lap.size else steps
+            out_of = np.nonzero(~(np.abs(ey[: end + 1]) <= w_T))[0]  # NaN counts as a crash
+            if out_of.size:
+                crashes += 1
+                end = int(out_of[0])
+            else:
+                laps_s.append(end * p.dt)
+            near = np.abs(ey[: end + 1]) > collide_at
+            collisions += int(near[0]) + int(np.count_nonzero(near[1:] & ~near[:-1]))
+            h = w_T * w_T - ey[: end + 1] ** 2
+            dcbf_ok += int(np.count_nonzero(h[1:] >= (1.0 - p.gamma) * h[:-1]))
+            dcbf_n += max(end, 0)
+        out.append({"q_ey": qe, "K": K, "M": M, "runs": runs, "crash_rate": crashes / runs,
+                    "collision_rate": collisions / runs,
+                    "dcbf_condition_satisfied": dcbf_ok / max(dcbf_n, 1),
+                    "mean_lap_time_s": float(np.mean(laps_s)) if laps_s else None,
+                    "ms_per_closed_loop_step": 1e3 * float(np.mean(step_s))})
     return {"T": T, "noise_scale": noise_scale, "v_goal": v_goal, "w_T": w_T, "collide_at": collide_at,
             "track": "seeded Fourier-perturbed circle (track seed 1), one lap per run", "grid": out}
 
@@ -541,7 +542,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and args.km_sweep:
         ks, ms = (tuple(int(v) for v in part.split(",")) for part in args.km_sweep.split(";"))
         line["km_sweep"] = run_km_sweep(bssmppi, dev, stream, ks, ms, args.km_runs, T=args.km_T,
-                                        noise_scale=args.km_noise, v_goal=args.km_speed, w_T=args.km_wT)
+                                        noise_scale=args.km_noise, v_goal=args.km_speed, w_T=args.km_wT,
+                                        q_ey=tuple(float(q) for q in args.km_qey.split(",")))
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(p, args.cpu_budget)
     return line
@@ -568,6 +570,7 @@ def main():
     ap.add_argument("--km-noise", type=float, default=4.0)
     ap.add_argument("--km-speed", type=float, default=10.0)
     ap.add_argument("--km-wT", type=float, default=2.0)
+    ap.add_argument("--km-qey", default="0.1", help="lateral-deviation cost weights q_ey to sweep (comma list)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
