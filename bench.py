@@ -186,12 +186,12 @@ def run_reference(args):
 SERVE_BATCH_WORK = 40_000_000  # particle-steps per batch: about 2 ms of GPU time
 
 
-def _serve_stream(bssmppi, n_ctrl, rate_hz, duration_s, seed, batched, probs_params):
+def _serve_stream(bssmppi, n_ctrl, rate_hz, duration_s, seed, batched, probs_params, batch_work=SERVE_BATCH_WORK):
     """Replay a Poisson arrival stream against a server; returns latency/throughput statistics."""
     reqs = workload.serving_requests(n_ctrl=n_ctrl, rate_hz=rate_hz, duration_s=duration_s, seed=seed)
     if batched:
         s = bssmppi.server_create(n_ctrl, max_batch=512, T_max=60, slots=2, use_graphs=True,
-                                  hbm_budget_bytes=2 << 30, max_batch_work=SERVE_BATCH_WORK)
+                                  hbm_budget_bytes=2 << 30, max_batch_work=int(batch_work))
     else:
         s = bssmppi.server_create(n_ctrl, max_batch=1, T_max=60, slots=1, use_graphs=False,
                                   hbm_budget_bytes=2 << 30)
@@ -240,15 +240,16 @@ def run_serving(args):
         params.append(bssmppi.make_params(p))
     out = {"controllers": n_ctrl, "rate_hz_per_controller": 20.0, "duration_s": args.serve_seconds,
            "policy": "latest state wins: a newer request of a controller replaces its pending one"}
-    out["batch_work_limit_particle_steps"] = SERVE_BATCH_WORK
-    out["batched"] = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, True, params)
+    bw = args.serve_batch_work
+    out["batch_work_limit_particle_steps"] = bw
+    out["batched"] = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, True, params, bw)
     out["plain"] = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, False, params)
     # rate sweep of both paths on the same arrival streams: the highest sustained solves/s at which
     # the K=4096, M=64, T=40 class keeps its p99 latency under 10 ms
     for name, batched in (("batched", True), ("plain", False)):
         sweep, best = [], None
         for rate in (0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0):
-            r = _serve_stream(bssmppi, n_ctrl, rate, max(1.0, args.serve_seconds), 5, batched, params)
+            r = _serve_stream(bssmppi, n_ctrl, rate, max(1.0, args.serve_seconds), 5, batched, params, bw)
             p99 = r["class_4096_64_40_latency_ms_p99"]
             sweep.append({"rate_hz_per_controller": rate, "offered_req_per_s": r["offered_req_per_s"],
                           "solves_per_s": r["solves_per_s"], "latency_ms_p99": r["latency_ms_p99"],
@@ -562,6 +563,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--closed-loop-steps", type=int, default=1000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-batch-work", type=float, default=SERVE_BATCH_WORK,
+                    help="particle-steps admitted per serving batch (bounds a batch's duration)")
     ap.add_argument("--repair-iters", type=int, default=5)
     ap.add_argument("--repair-step", type=float, default=2e-6)
     ap.add_argument("--km-sweep", default="", help="closed-loop lap study over 'K1,K2,...;M1,M2,...' (off by default)")
