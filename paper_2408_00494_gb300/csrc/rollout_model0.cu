@@ -1,0 +1,22 @@
+// Rollout kernel instantiations for the 6-state bicycle (model 0).
+#include "rollout_kernel.cuh"
+
+namespace bss {
+
+template <>
+cudaError_t prepare_model<0>(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L)
+{
+    if (full) return plan_model<0, true, true>(dp, P, L);
+    return comp ? plan_model<0, true, false>(dp, P, L) : plan_model<0, false, false>(dp, P, L);
+}
+
+template <>
+cudaError_t launch_model_variant<0>(const DevParams& dp, const RollIO& io, const TailIO& tail, const ConSet& cs, int P,
+                                     bool comp, bool full, const RollLaunch& L, cudaStream_t st)
+{
+    if (full) return launch_model<0, true, true>(dp, io, tail, cs, P, L, st);
+    return comp ? launch_model<0, true, false>(dp, io, tail, cs, P, L, st)
+                : launch_model<0, false, false>(dp, io, tail, cs, P, L, st);
+}
+
+}  // namespace bss
