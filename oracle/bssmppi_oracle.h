@@ -98,7 +98,9 @@ void orc_shift(int T, double* v);
 /* Shield repair objective J_r(v) = sum_{t=1..T} C_safe,t of the M-particle rollout of the
  * nominal sequence v (no control noise, disturbance draws of sample 0) and its gradient dJ/dv
  * by a reverse sweep (adjoint). grad [T*2] and args_out [T+1] (the hinge arguments
- * -h_t + (1 - gamma) h_{t-1}, entry 0 unused) may be NULL. Returns J. */
+ * -h_t + (1 - gamma) h_{t-1}, entry 0 unused) may be NULL. Returns J.
+ * Parity unpinned with respect to the paper: the paper leaves the repair step undefined, so this
+ * objective is a reading of it; the gradient is pinned by central finite differences of J_r. */
 double orc_repair_objective(const orc_problem* p, const double* x0, const double* v,
                             uint32_t solve_ctr, double* grad, double* args_out);
 
