@@ -3,8 +3,8 @@
 
 A step is one pass of the whole path on the racing workload K=4096 control samples, M=64
 particles, T=40 steps (6-state dynamic bicycle, 5 Euler substeps): control noise, clamp,
-disturbance draws, particle rollout, per-step belief moments, barrier and cost, then weights and
-update in the same kernel's tail (one launch), then the warm-start shift. Inputs are resident on the device;
+disturbance draws, particle rollout, per-step belief moments, barrier and cost, then weights,
+update and the warm-start shift in the same kernel's tail (one launch per step). Inputs are resident on the device;
 the L2 cache is flushed (a 256 MiB write) before every timed step, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
@@ -284,9 +284,8 @@ def run_closed_loop(bssmppi, p, dev, stream, steps: int, seed: int = 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(steps):  # only library calls inside the loop
-            bssmppi.solve(ctl.h, traj[k], None, None, u0[0])
+            bssmppi.solve_shift(ctl.h, traj[k], None, u0[0], 1)
             bssmppi.model_step(ctl.h, traj[k:k + 1], u0, traj[k + 1:k + 2], W[k:k + 1])
-            bssmppi.shift(ctl.h, None, 1)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         roll_ms, _ = bssmppi.timing_read(ctl.h, min(steps, 4096))
@@ -345,9 +344,8 @@ def run_km_sweep(bssmppi, dev, stream, Ks, Ms, runs, T=20, noise_scale=4.0, v_go
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 for k in range(steps):
-                    bssmppi.solve(ctl.h, traj[k], None, None, u0[0])
+                    bssmppi.solve_shift(ctl.h, traj[k], None, u0[0], 1)
                     bssmppi.model_step(ctl.h, traj[k:k + 1], u0, traj[k + 1:k + 2], W[k:k + 1])
-                    bssmppi.shift(ctl.h, None, 1)
                 torch.cuda.synchronize()
                 step_s.append((time.perf_counter() - t0) / steps)
             finally:
@@ -406,8 +404,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
 
     def step():
-        bssmppi.solve(h, x0)       # resident nominal in, v+ resident out
-        bssmppi.shift(h, None, 1)  # warm start for the next solve
+        bssmppi.solve_shift(h, x0, None, None, 1)  # solve + warm-start shift of the resident nominal, one launch
 
     for _ in range(args.warmup):
         step()
@@ -458,8 +455,7 @@ def run_ours(args, rank, world, local_rank):
             flush.fill_(float(i))
             if i >= args.warmup:
                 ev[i - args.warmup][0].record(stream)
-            bssmppi.solve(cv.h, xv)
-            bssmppi.shift(cv.h, None, 1)
+            bssmppi.solve_shift(cv.h, xv, None, None, 1)
             if i >= args.warmup:
                 ev[i - args.warmup][1].record(stream)
         torch.cuda.synchronize()
@@ -519,16 +515,16 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": whole_job_throughput(units, mean_e2e_ms, world), "unit": "particle-steps/s",
                 "h2d_bytes_per_step": 4 * (8 + 2 * p.T), "d2h_bytes_per_step": 4 * (2 * p.T + 2),
                 "copies_per_step": "one H2D (x0 padded to 8 floats | v) and one D2H (v+ | u0)"},
-        "gpu_launches": 2 * args.steps,  # per step: the solve kernel and the shift kernel
+        "gpu_launches": args.steps,  # per step: one kernel (solve, update and shift fused)
         "resample_variant": {"ms_per_step": rs_ms, "particle_steps_per_s": units / (rs_ms * 1e-3),
                              "note": "Algorithm 2 read literally: full moments, Cholesky and re-draw of "
-                                     "every particle before each step; solve + shift, same L2 flush"},
+                                     "every particle before each step; solve + shift in one launch, same L2 flush"},
         "wheels8_variant": {"ms_per_step": w8_ms, "particle_steps_per_s": units / (w8_ms * 1e-3),
                             "note": "8-state single-track model with wheel speeds and friction-ellipse "
-                                    "combined slip, n_sub = 10, AutoRally scale; solve + shift"},
+                                    "combined slip, n_sub = 10, AutoRally scale; solve + shift in one launch"},
         "constraint_set_variant": {"ms_per_step": con_ms, "particle_steps_per_s": units / (con_ms * 1e-3),
                                    "note": "general set h = min_q h_q: two track-edge half-spaces and a disk "
-                                           "obstacle on (s, e_y), full covariance every step; solve + shift"},
+                                           "obstacle on (s, e_y), full covariance every step; solve + shift in one launch"},
         "shield_repair": {"iters": args.repair_iters, "step": args.repair_step, "ms_per_step": rep_ms,
                           "repair_ms": rep_ms - mean_ms, "solves_per_s": 1e3 / rep_ms,
                           "particle_steps_per_s": units / (rep_ms * 1e-3),

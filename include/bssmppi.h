@@ -176,6 +176,15 @@ int bssmppi_create(const bssmppi_params* params, void* cuda_stream, bssmppi_t* o
 int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* d_v, float* d_u0);
 
 /*
+ * A solve on the resident nominal followed, in the same launch, by the warm-start shift of
+ * bssmppi_shift: the resident nominal ends as v+ shifted left by n steps with its last element
+ * repeated (v[t] <- v+[min(t + n, T - 1)]), and d_u0 (device, 2, or NULL for the handle's) receives
+ * v+_0 from before the shift. Equivalent to bssmppi_solve(h, d_x0, d_Sigma0, NULL, d_u0) followed by
+ * bssmppi_shift(h, NULL, n), in one launch instead of two. 0 <= n <= T. Asynchronous.
+ */
+int bssmppi_solve_shift(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* d_u0, int32_t n);
+
+/*
  * The same solve with host buffers: stages h_x0, h_v (NULL = resident) and h_Sigma0 (if non-NULL)
  * in the handle's pinned buffer and copies them to the device in one transfer, solves, reads v+ and
  * the first control back in one transfer into h_v and h_u0 (each if non-NULL), and waits for the

@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         "bssmppi_solve_host": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "bssmppi_shift": (ctypes.c_int, [vp, vp, i32]),
         "bssmppi_set_constraints": (ctypes.c_int, [vp, vp, i32]),
+        "bssmppi_solve_shift": (ctypes.c_int, [vp, vp, vp, vp, i32]),
         "bssmppi_set_sample_range": (ctypes.c_int, [vp, i32, i32]),
         "bssmppi_solve_partial": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "bssmppi_merge_partials": (ctypes.c_int, [vp, vp, i32, vp, vp]),
@@ -226,6 +227,11 @@ def create(params: Params, stream=None):
 
 def solve(h, x0, Sigma0=None, v=None, u0=None):
     _check(load().bssmppi_solve(h, _ptr(x0), _ptr(Sigma0), _ptr(v), _ptr(u0)), h)
+
+
+def solve_shift(h, x0, Sigma0=None, u0=None, n: int = 1):
+    """Solve on the resident nominal and shift it by n steps, in one launch (u0 = v+_0)."""
+    _check(load().bssmppi_solve_shift(h, _ptr(x0), _ptr(Sigma0), _ptr(u0), int(n)), h)
 
 
 def solve_host(h, x0, Sigma0=None, v=None, u0=None):

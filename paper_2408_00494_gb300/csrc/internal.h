@@ -32,6 +32,7 @@ struct TailIO {
     float* v_out;           // T*2: v+ (the resident nominal, read by every block first)
     float* part_out;        // nullptr: apply the update; else write the merged log-sum-exp partial
                             // (3 + 2T floats: beta, eta, sum omega^2, N) there and leave v, u0, w, diag
+    int shift_n;            // > 0: write v+ shifted left by shift_n steps (last repeated) to v_out
 };
 size_t rollout_smem_bytes(const DevParams& dp, int wpb);
 // full: the full-belief kernel variant (re-sampled particles and/or a general constraint set).

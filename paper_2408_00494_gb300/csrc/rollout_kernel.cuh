@@ -110,8 +110,15 @@ __device__ __noinline__ void tail_merge(const int G, const float* part, const in
             continue;
         }
         const float vn = v_s[i] + N / eta;
-        tail.v_out[i] = vn;
         if (tail.u0 != nullptr && i < 2) tail.u0[i] = vn;
+        if (tail.shift_n == 0) {
+            tail.v_out[i] = vn;
+        } else {  // the warm-start shift in the same launch: v[t] <- v+[min(t + n, T - 1)]
+            const int t = i >> 1, c = i & 1, n = tail.shift_n;
+            if (t >= n) tail.v_out[2 * (t - n) + c] = vn;
+            if (t == T - 1)
+                for (int tt = max(T - n, 0); tt < T; ++tt) tail.v_out[2 * tt + c] = vn;
+        }
     }
     if (tail.part_out != nullptr) {
         if (tid == 0) {

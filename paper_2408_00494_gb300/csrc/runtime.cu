@@ -370,12 +370,12 @@ namespace {
 
 // One solve launch: the rollout reads the nominal from v_in; the tail writes v+ to the resident
 // nominal and the first control to u0.
-int launch_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, const float* v_in, float* u0)
+int launch_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, const float* v_in, float* u0, int shift_n = 0)
 {
     cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 2 * h->ev_count : nullptr;
     if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], h->stream));
     // One launch: rollout, costs, and (in its tail) weights, update, u0, diagnostics, counter.
-    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, u0, h->d_diag, h->d_ctr, h->d_v, nullptr};
+    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, u0, h->d_diag, h->d_ctr, h->d_v, nullptr, shift_n};
     BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, v_in, h->d_ctr,
                                     h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, h->stream));
     if (ev) {
@@ -397,6 +397,14 @@ int bssmppi_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* 
     if (rc != BSSMPPI_OK) return rc;
     if (d_v) BSS_CUDA(h, cudaMemcpyAsync(d_v, h->d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
     return BSSMPPI_OK;
+}
+
+int bssmppi_solve_shift(bssmppi_t h, const float* d_x0, const float* d_Sigma0, float* d_u0, int32_t n)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
+    if (!d_x0) return fail(h, BSSMPPI_EINVAL, "x0 is NULL");
+    if (n < 0 || n > h->prm.T) return fail(h, BSSMPPI_EINVAL, "shift n must be in [0, T]");
+    return launch_solve(h, d_x0, d_Sigma0, h->d_v, d_u0 ? d_u0 : h->d_u0, n);
 }
 
 int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, float* h_v, float* h_u0)

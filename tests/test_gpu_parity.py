@@ -309,3 +309,28 @@ def test_full_size_config1_sampled_parity():
     assert abs(g["w"].sum() - 1.0) < 1e-5 and g["w"].min() >= 0.0
     lo, hi = np.asarray(p.u_min), np.asarray(p.u_max)
     assert np.all(u_gpu >= lo - 1e-6) and np.all(u_gpu <= hi + 1e-6)
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 20])
+def test_solve_shift_equals_solve_then_shift(n):
+    """The fused call leaves the resident nominal and u0 exactly as a solve followed by a shift."""
+    p = workload.config0()
+    x0, v = workload.random_state(p, 17), workload.random_nominal(p, 17)
+    out = []
+    for fused in (False, True):
+        c = bssmppi.Controller(p)
+        try:
+            bssmppi.set_counter(c.h, 4)
+            bssmppi.set_nominal(c.h, _dev(v))
+            u0 = torch.zeros(2, device="cuda")
+            xt = _dev(x0)
+            if fused:
+                bssmppi.solve_shift(c.h, xt, None, u0, n)
+            else:
+                bssmppi.solve(c.h, xt, None, None, u0)
+                bssmppi.shift(c.h, None, n)
+            out.append((c.buffer(bssmppi.BUF_V).cpu().numpy(), u0.cpu().numpy(), bssmppi.get_counter(c.h)))
+        finally:
+            c.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] == 5
