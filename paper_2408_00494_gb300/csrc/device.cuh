@@ -297,11 +297,14 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* _
 // g = sin(C atan(B s)) on the combined slip s = sqrt(kappa^2 + alpha^2), split along the slip
 // direction and scaled by the friction ellipse's axes: F_x = mu_x F_z g kappa / s,
 // F_y = mu F_z g alpha / s. Rear-wheel drive torque tau_max * throttle; static axle loads.
-__device__ __forceinline__ float tyre_ratio(const DevParams& P, float sl)
+__device__ __forceinline__ float tyre_ratio(const DevParams& P, float sl2)
 {
-    // g(s) / s, which tends to C B at zero slip; |C atan(B s)| < C pi / 2 < pi keeps the hardware
-    // sine inside its accurate range
-    return sl > 1e-6f ? __fdividef(__sinf(P.tC * atanf(P.tB * sl)), sl) : P.CB;
+    // g(s) / s for the squared combined slip sl2 = s^2, which tends to C B at zero slip. One
+    // reciprocal square root gives both s = sl2 / sqrt(sl2) and 1 / s. |C atan(B s)| < C pi / 2 < pi
+    // keeps the hardware sine inside its accurate range.
+    if (!(sl2 > 1e-12f)) return P.CB;
+    const float rs = rsqrtf(sl2);
+    return __sinf(P.tC * atanf(P.tB * (sl2 * rs))) * rs;
 }
 
 template <typename Tab>
@@ -316,8 +319,8 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __
     const float vwf = fmaf(vx, u.cos_steer, yf * u.sin_steer);
     const float kf = __fdividef(fmaf(P.Rw, wf, -vwf), fmaxf(fabsf(vwf), P.slip_floor));
     const float kr = __fdividef(fmaf(P.Rw, wr, -vx), fmaxf(fabsf(vx), P.slip_floor));
-    const float gf = tyre_ratio(P, sqrtf(fmaf(kf, kf, alpha_f * alpha_f)));
-    const float gr = tyre_ratio(P, sqrtf(fmaf(kr, kr, alpha_r * alpha_r)));
+    const float gf = tyre_ratio(P, fmaf(kf, kf, alpha_f * alpha_f));
+    const float gr = tyre_ratio(P, fmaf(kr, kr, alpha_r * alpha_r));
     const float Fxf = P.Dxf * gf * kf, Fyf = P.Df * gf * alpha_f;
     const float Fxr = P.Dxr * gr * kr, Fyr = P.Dr * gr * alpha_r;
     const float FXf = fmaf(Fxf, u.cos_steer, -Fyf * u.sin_steer);
