@@ -96,13 +96,16 @@ __device__ __forceinline__ uint4 draw_words(const DevParams& P, uint32_t step, u
 // Box-Muller from two 32-bit words: u1 in (0, 1], u2 in [0, 1) from their top 24 bits (exact in
 // FP32), z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2). The angle is taken centred,
 // theta = 2 pi (u2 - 1/2) in [-pi, pi) (u2 - 1/2 is exact), where the hardware sine and cosine are
-// accurate to 2^-21.4 absolute; (cos, sin)(2 pi u2) = -(cos, sin)(theta).
+// accurate to 2^-21.4 absolute; (cos, sin)(2 pi u2) = -(cos, sin)(theta). The radius is taken as
+// t rsqrt(t), t = -2 ln u1, within a few ulp of the square root (t = 0 at u1 = 1 gives 0); the
+// smallest positive t is about 2^-23, far from the subnormal range.
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 {
     const float two_m24 = 5.9604644775390625e-08f;
     const float u1 = (float)((a >> 8) + 1u) * two_m24;
     const float theta = 6.28318530717958647692f * ((float)(b >> 8) * two_m24 - 0.5f);
-    const float rad = sqrtf(-2.0f * logf(u1));
+    const float t = -2.0f * logf(u1);
+    const float rad = t > 0.0f ? t * rsqrtf(t) : 0.0f;
     float sn, cs;
     __sincosf(theta, &sn, &cs);
     return make_float2(-rad * cs, -rad * sn);
@@ -141,9 +144,10 @@ __device__ __forceinline__ void draw_disturbance(const DevParams& P, uint32_t st
         const uint32_t q = upper ? particle - (uint32_t)P.dist_half : particle;
         const uint4 wa = draw_words(P, step, upper ? 1u : 0u, q, sample, kStreamDisturbance, ctr);
         const uint4 wb = draw_words(P, step, upper ? 2u : 1u, q, sample, kStreamDisturbance, ctr);
-        const float2 g0 = upper ? box_muller(wa.z, wa.w) : box_muller(wa.x, wa.y);
-        const float2 g1 = upper ? box_muller(wb.x, wb.y) : box_muller(wa.z, wa.w);
-        const float2 g2 = upper ? box_muller(wb.z, wb.w) : box_muller(wb.x, wb.y);
+        // Select the words, then transform: one Box-Muller per pair whichever half the particle is in.
+        const float2 g0 = box_muller(upper ? wa.z : wa.x, upper ? wa.w : wa.y);
+        const float2 g1 = box_muller(upper ? wb.x : wa.z, upper ? wb.y : wa.w);
+        const float2 g2 = box_muller(upper ? wb.z : wb.x, upper ? wb.w : wb.y);
         z[0] = g0.x; z[1] = g0.y; z[2] = g1.x; z[3] = g1.y; z[4] = g2.x; z[5] = g2.y;
     } else {
         draw_normals<NX>(P, step, particle, sample, kStreamDisturbance, ctr, z);
