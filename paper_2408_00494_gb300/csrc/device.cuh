@@ -16,6 +16,21 @@ __host__ __device__ constexpr int model_s_index(int model) { return model == 0 ?
 
 // Everything a solve's kernels need, derived on the host at create time and passed by value
 // (kernel parameter space), so several controllers can run concurrently without global state.
+// Constant operands of the bicycle substep: the model's h, -h, l_f, -l_r, B, -B, C, h D_r / m,
+// -h l_r D_r / I_z, then fixed numbers: 1, -1 and the heading-rotation series' 1/24, -1/2, 1/120,
+// -1/6.
+enum : int {
+    kFoldH, kFoldNH, kFoldLf, kFoldNLr, kFoldTB, kFoldNTB, kFoldTC, kFoldHa3, kFoldHb2,
+    kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldN
+};
+
+// The fixed numbers among them (i >= kFoldOne).
+__host__ __device__ constexpr float fold_fixed(int i)
+{
+    return i == kFoldOne ? 1.0f : i == kFoldM1 ? -1.0f : i == kFoldC24 ? 4.1666667e-2f : i == kFoldMHalf ? -0.5f
+         : i == kFoldC120 ? 8.3333333e-3f : i == kFoldM6 ? -1.6666667e-1f : 0.0f;
+}
+
 struct DevParams {
     int K, M, T, n_sub, nx;
     int seg;          // lanes per control sample (power of two <= 32)
@@ -42,6 +57,11 @@ struct DevParams {
     float Dxf, Dxr, Rw, inv_Iw, tau_max, slip_floor, CB;
     float track_scale;               // n_track / track_len
     float Mf, invM, invM1;           // M, 1/M, 1/(M-1)
+    float hDf_m, hlfDf_Iz;           // h D_f / m and h l_f D_f / I_z (per-step force factors)
+    // Constant operands of the bicycle substep (kFold* indices), alone and as (v, v) pairs for the
+    // packed two-particle form.
+    float fold[kFoldN];
+    float2 fold2[kFoldN];
     const float* kappa;              // device curvature table, n_track + 1 entries (last = first)
 };
 
@@ -264,35 +284,100 @@ __device__ __forceinline__ void rotate_heading(float d, float& sp, float& cp)
     sp = s;
 }
 
-// One explicit-Euler substep; (sp, cp) = (sin e_psi, cos e_psi) on entry and on exit. Tab: the
-// curvature table's element (float, or float2 pairs of value and difference).
-template <typename Tab>
-__device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
-                                                const Control& u, float (&x)[6], float& sp, float& cp)
+// One explicit-Euler substep of one particle (V = float) or of two particles side by side (V =
+// float2, with the packed FP32 instructions of the sm_100 family: fma / mul / add on .f32x2 register
+// pairs, round-to-nearest in each half, so one issued instruction does the operation for both).
+// Every rounding is explicit (fmaf, __fmul_rn, __fadd_rn are never contracted), so each half of a
+// packed pair is bit-identical to the one-particle substep on the same particle. The
+// transcendentals, quotients and the curvature lookup are taken per particle. (sp, cp) =
+// (sin e_psi, cos e_psi) on entry and on exit. Tab: the curvature table's element (float, or float2
+// pairs of value and difference). The force constants are folded into per-step factors
+// (SubstepCtl): v_x' = v_x + h a - h D_f sin(delta)/m g_f + h v_y r, and so on.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <typename F> __device__ __forceinline__ float each(float a, F f) { return f(a); }
+template <typename F> __device__ __forceinline__ float2 each(float2 a, F f) { return make_float2(f(a.x), f(a.y)); }
+template <typename F> __device__ __forceinline__ float each(float a, float b, F f) { return f(a, b); }
+template <typename F> __device__ __forceinline__ float2 each(float2 a, float2 b, F f)
 {
-    const float vx = x[0], vy = x[1], r = x[2], ep = x[3], ey = x[4];
+    return make_float2(f(a.x, b.x), f(a.y, b.y));
+}
+template <typename V> __device__ __forceinline__ V splat(float a);
+template <> __device__ __forceinline__ float splat<float>(float a) { return a; }
+template <> __device__ __forceinline__ float2 splat<float2>(float a) { return make_float2(a, a); }
+template <typename V> __device__ __forceinline__ V fold(const DevParams& P, int i);
+template <> __device__ __forceinline__ float fold<float>(const DevParams& P, int i)
+{
+    return i >= kFoldOne ? fold_fixed(i) : P.fold[i];  // fixed numbers as immediate operands
+}
+template <> __device__ __forceinline__ float2 fold<float2>(const DevParams& P, int i) { return P.fold2[i]; }
+
+// Per-step factors (the control is the same for every particle of a sample): steer, h a,
+// -h D_f sin(delta) / m, h D_f cos(delta) / m, h l_f D_f cos(delta) / I_z.
+template <typename V>
+struct SubstepCtl {
+    V steer, hacc, ha1, ha2, hb1;
+};
+
+template <typename V>
+__device__ __forceinline__ SubstepCtl<V> substep_ctl(const DevParams& P, const Control& u)
+{
+    SubstepCtl<V> c;
+    c.steer = splat<V>(u.steer);
+    c.hacc = splat<V>(__fmul_rn(P.fold[kFoldH], u.accel));
+    c.ha1 = splat<V>(__fmul_rn(-P.hDf_m, u.sin_steer));
+    c.ha2 = splat<V>(__fmul_rn(P.hDf_m, u.cos_steer));
+    c.hb1 = splat<V>(__fmul_rn(P.hlfDf_Iz, u.cos_steer));
+    return c;
+}
+
+template <typename V>
+__device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp, V& cp)
+{
+    const V d2 = vmul(d, d);
+    const V cd = vfma(d2, vfma(d2, fold<V>(P, kFoldC24), fold<V>(P, kFoldMHalf)), fold<V>(P, kFoldOne));
+    const V sd = vfma(vmul(d, d2), vfma(d2, fold<V>(P, kFoldC120), fold<V>(P, kFoldM6)), d);
+    const V s = vfma(sp, cd, vmul(cp, sd));
+    cp = vfma(cp, cd, vmul(vmul(sp, sd), fold<V>(P, kFoldM1)));
+    sp = s;
+}
+
+template <typename V, typename Tab>
+__device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
+                                                const SubstepCtl<V>& u, V (&X)[6], V& sp, V& cp)
+{
+    const V vx = X[0], vy = X[1], r = X[2];
     // v_x >= vx_floor >= 1 and 1 - kappa e_y is near 1, so the fast (2-ulp) quotients are safe.
-    const float inv_vx = __fdividef(1.0f, fmaxf(vx, P.vx_floor));
-    const float alpha_f = u.steer - atanf((vy + P.lf * r) * inv_vx);
-    const float alpha_r = -atanf((vy - P.lr * r) * inv_vx);
+    const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
+    const V tf = vmul(vfma(fold<V>(P, kFoldLf), r, vy), ivx);    // (v_y + l_f r) / v_x
+    const V tr = vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx);   // (v_y - l_r r) / v_x
+    const auto at = [](float a) { return atanf(a); };
+    const V af = vfma(each(tf, at), fold<V>(P, kFoldM1), u.steer);    // alpha_f
+    const V bf = vmul(fold<V>(P, kFoldTB), af);                        // B alpha_f
+    const V br = vmul(fold<V>(P, kFoldNTB), each(tr, at));             // B alpha_r
     // |C atan(B alpha)| < C pi / 2 < pi: inside the range where the hardware sine's absolute error
     // is at most 2^-21.4 of the unit amplitude (a relative force error of a few FP32 ulps).
-    const float Ff = P.Df * __sinf(P.tC * atanf(P.tB * alpha_f));
-    const float Fr = P.Dr * __sinf(P.tC * atanf(P.tB * alpha_r));
-    const float kap_s = track_curvature(P, kap, s0 + x[5]);
-    const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
-    const float dvx = u.accel - Ff * u.sin_steer * P.inv_m + vy * r;
-    const float dvy = (Ff * u.cos_steer + Fr) * P.inv_m - vx * r;
-    const float dr = (P.lf * Ff * u.cos_steer - P.lr * Fr) * P.inv_Iz;
-    const float dep = r - kap_s * sdot;
-    const float dey = vx * sp + vy * cp;
-    x[0] = fmaf(P.h, dvx, vx);
-    x[1] = fmaf(P.h, dvy, vy);
-    x[2] = fmaf(P.h, dr, r);
-    x[3] = fmaf(P.h, dep, ep);
-    x[4] = fmaf(P.h, dey, ey);
-    x[5] = fmaf(P.h, sdot, x[5]);
-    rotate_heading(P.h * dep, sp, cp);
+    const auto sn = [](float a) { return __sinf(a); };
+    const V gf = each(vmul(fold<V>(P, kFoldTC), each(bf, at)), sn);   // F_f / D_f
+    const V gr = each(vmul(fold<V>(P, kFoldTC), each(br, at)), sn);   // F_r / D_r
+    const V nk = each(X[5], [&](float a) { return -track_curvature(P, kap, s0 + a); });  // -kappa(s)
+    const V num = vfma(vx, cp, vmul(vmul(vy, sp), fold<V>(P, kFoldM1)));                // v_x cos - v_y sin
+    const V den = vfma(nk, X[4], fold<V>(P, kFoldOne));                                 // 1 - kappa e_y
+    const V sdot = each(num, den, [](float a, float b) { return __fdividef(a, b); });
+    const V dep = vfma(nk, sdot, r);
+    const V dey = vfma(vx, sp, vmul(vy, cp));
+    const V h = fold<V>(P, kFoldH);
+    X[0] = vfma(gf, u.ha1, vfma(vmul(vy, r), h, vadd(vx, u.hacc)));
+    X[1] = vfma(gf, u.ha2, vfma(gr, fold<V>(P, kFoldHa3), vfma(vmul(vx, r), fold<V>(P, kFoldNH), vy)));
+    X[2] = vfma(gf, u.hb1, vfma(gr, fold<V>(P, kFoldHb2), r));
+    X[3] = vfma(h, dep, X[3]);
+    X[4] = vfma(h, dey, X[4]);
+    X[5] = vfma(h, sdot, X[5]);
+    rotate_heading_v(P, vmul(h, dep), sp, cp);
 }
 
 // Single-track model with wheel speeds and combined slip, x = [v_x, v_y, r, omega_F, omega_R, e_psi,
@@ -472,7 +557,8 @@ __device__ __forceinline__ void model_step(const DevParams& P, const float* __re
     if constexpr (MODEL == 0) {
         float sp, cp;
         sincos_series(x[3], &sp, &cp);
-        for (int j = 0; j < P.n_sub; ++j) bicycle_substep(P, kap, s0, u, x, sp, cp);
+        const SubstepCtl<float> c = substep_ctl<float>(P, u);
+        for (int j = 0; j < P.n_sub; ++j) bicycle_substep(P, kap, s0, c, x, sp, cp);
     } else if constexpr (MODEL == 2) {
         float sp, cp;
         sincos_series(x[5], &sp, &cp);

@@ -269,6 +269,14 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.n_track_mask = ntab - 1;
     d.track_scale = track ? (float)((double)ntab / p->track_len) : 0.0f;
     d.Mf = (float)p->M; d.invM = 1.0f / (float)p->M; d.invM1 = 1.0f / (float)(p->M - 1);
+    d.hDf_m = (float)((double)d.h * d.Df * d.inv_m);
+    d.hlfDf_Iz = (float)((double)d.h * d.lf * d.Df * d.inv_Iz);
+    d.fold[kFoldH] = d.h; d.fold[kFoldNH] = -d.h; d.fold[kFoldLf] = d.lf; d.fold[kFoldNLr] = -d.lr;
+    d.fold[kFoldTB] = d.tB; d.fold[kFoldNTB] = -d.tB; d.fold[kFoldTC] = d.tC;
+    d.fold[kFoldHa3] = (float)((double)d.h * d.Dr * d.inv_m);
+    d.fold[kFoldHb2] = (float)(-(double)d.h * d.lr * d.Dr * d.inv_Iz);
+    for (int i = kFoldOne; i < kFoldN; ++i) d.fold[i] = fold_fixed(i);
+    for (int i = 0; i < kFoldN; ++i) d.fold2[i] = make_float2(d.fold[i], d.fold[i]);
     return BSSMPPI_OK;
 }
 

@@ -4,7 +4,7 @@ A request's result is a deterministic function of its controller's state (nomina
 state estimate and its (K, M, T): alone or in a mix of other controllers' requests, with or without
 CUDA graphs, it must come out bit for bit the same, and equal to bssmppi_solve + bssmppi_shift on
 a single handle within the update tolerance (rel 1e-4 / abs 1e-5; the two update kernels add the
-weighted perturbations in different orders).
+weighted perturbations in different orders), with the same minimum trajectory cost bit for bit.
 """
 import time
 
@@ -53,7 +53,7 @@ def _x0(i):
 
 def _run(s, requests, ctr0=5):
     """requests: list of (ctrl, K, M, T). Resets the controllers, submits all, drains, returns
-    {ctrl: (u0, v_after, counter_after)}."""
+    {ctrl: (u0, v_after, counter_after, beta)}."""
     for c, *_ in requests:
         bssmppi.server_set_state(s, c, _v0(c), ctr0)
     for j, (c, K, M, T) in enumerate(requests):
@@ -64,7 +64,7 @@ def _run(s, requests, ctr0=5):
     for c, *_ in requests:
         assert res[c].status == 0
         v, ctr = bssmppi.server_get_state(s, c, T_MAX)
-        out[c] = (np.array(res[c].u0), v, ctr)
+        out[c] = (np.array(res[c].u0), v, ctr, res[c].beta)
     return out
 
 
@@ -108,8 +108,13 @@ def test_server_matches_single_solve(K, M, T):
     bssmppi.shift(c.h, v, 1)
     torch.cuda.synchronize()
     ctr = bssmppi.get_counter(c.h)
+    S = c.buffer(bssmppi.BUF_S).cpu().numpy()
     c.close()
     ref_u0, ref_v = u0.cpu().numpy(), v.cpu().numpy()
+    # The rollouts are the same arithmetic: the server steps bicycle particles one at a time, the
+    # solve two at a time in packed FP32 pairs, and each half of a pair rounds as the single
+    # particle does. So the minimum trajectory cost agrees bit for bit.
+    assert np.float32(got[3]) == S.min()
     assert np.all(np.abs(got[0] - ref_u0) <= 1e-5 + 1e-4 * np.abs(ref_u0))
     assert np.all(np.abs(got[1][:T] - ref_v) <= 1e-5 + 1e-4 * np.abs(ref_v))
     assert got[2] == ctr == 6
