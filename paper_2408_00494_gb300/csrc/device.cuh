@@ -19,8 +19,11 @@ __host__ __device__ constexpr int model_s_index(int model) { return model == 0 ?
 // Constant operands of the bicycle substep: the model's h, -h, l_f, -l_r, B, -B, C, h D_r / m,
 // -h l_r D_r / I_z, then fixed numbers: 1, -1 and the heading-rotation series' 1/24, -1/2, 1/120,
 // -1/6.
+// The wheel-speed model adds R_w, h mu_x F_zf (h D_xf), h D_f, 1/m, h D_xr / m, -h D_r / m, l_f / I_z,
+// h l_r D_r / I_z, -R_w / I_w and -h R_w D_xr / I_w (kFoldW*).
 enum : int {
     kFoldH, kFoldNH, kFoldLf, kFoldNLr, kFoldTB, kFoldNTB, kFoldTC, kFoldHa3, kFoldHb2,
+    kFoldWRw, kFoldWhDxf, kFoldWhDf, kFoldWInvM, kFoldWk3, kFoldWk6, kFoldWLfIz, kFoldWk9, kFoldWk10, kFoldWk11,
     kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldN
 };
 
@@ -271,19 +274,6 @@ __device__ __forceinline__ float track_curvature(const DevParams& P, const float
     return fmaf(f, k.y, k.x);
 }
 
-// The heading's sine and cosine carried across the substeps of one step: seeded from the series at
-// the step's first substep, then rotated by each substep's increment d = h e_psi' (|d| << 1:
-// sin d and cos d from three-term series, errors below |d|^7/7! and |d|^6/6!).
-__device__ __forceinline__ void rotate_heading(float d, float& sp, float& cp)
-{
-    const float d2 = d * d;
-    const float cd = fmaf(d2, fmaf(d2, 4.1666667e-2f, -0.5f), 1.0f);                       // 1 - d^2/2 + d^4/24
-    const float sd = fmaf(d * d2, fmaf(d2, 8.3333333e-3f, -1.6666667e-1f), d);           // d - d^3/6 + d^5/120
-    const float s = fmaf(sp, cd, cp * sd);
-    cp = fmaf(cp, cd, -sp * sd);
-    sp = s;
-}
-
 // One explicit-Euler substep of one particle (V = float) or of two particles side by side (V =
 // float2, with the packed FP32 instructions of the sm_100 family: fma / mul / add on .f32x2 register
 // pairs, round-to-nearest in each half, so one issued instruction does the operation for both).
@@ -335,6 +325,9 @@ __device__ __forceinline__ SubstepCtl<V> substep_ctl(const DevParams& P, const C
     return c;
 }
 
+// The heading's sine and cosine carried across the substeps of one step: seeded from the series at
+// the step's first substep, then rotated by each substep's increment d = h e_psi' (|d| << 1:
+// sin d and cos d from three-term series, errors below |d|^7/7! and |d|^6/6!).
 template <typename V>
 __device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp, V& cp)
 {
@@ -386,60 +379,93 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* _
 // g = sin(C atan(B s)) on the combined slip s = sqrt(kappa^2 + alpha^2), split along the slip
 // direction and scaled by the friction ellipse's axes: F_x = mu_x F_z g kappa / s,
 // F_y = mu F_z g alpha / s. Rear-wheel drive torque tau_max * throttle; static axle loads.
-__device__ __forceinline__ float tyre_ratio(const DevParams& P, float sl2)
+// g(s) / s for the squared combined slip sl2 = s^2, which tends to C B at zero slip. One reciprocal
+// square root gives both s = sl2 / sqrt(sl2) and 1 / s. |C atan(B s)| < C pi / 2 < pi keeps the
+// hardware sine inside its accurate range. (At sl2 = 0 the reciprocal square root is infinite and
+// the product not a number: the select returns C B there.)
+template <typename V>
+__device__ __forceinline__ V tyre_ratio(const DevParams& P, V sl2)
 {
-    // g(s) / s for the squared combined slip sl2 = s^2, which tends to C B at zero slip. One
-    // reciprocal square root gives both s = sl2 / sqrt(sl2) and 1 / s. |C atan(B s)| < C pi / 2 < pi
-    // keeps the hardware sine inside its accurate range.
-    if (!(sl2 > 1e-12f)) return P.CB;
-    const float rs = rsqrtf(sl2);
-    return __sinf(P.tC * atanf(P.tB * (sl2 * rs))) * rs;
+    const V rs = each(sl2, [](float a) { return rsqrtf(a); });
+    const V b = vmul(fold<V>(P, kFoldTB), vmul(sl2, rs));
+    const V c = vmul(fold<V>(P, kFoldTC), each(b, [](float a) { return atanf(a); }));
+    const V g = vmul(each(c, [](float a) { return __sinf(a); }), rs);
+    return each(sl2, g, [&](float q, float gq) { return q > 1e-12f ? gq : P.CB; });
 }
 
-template <typename Tab>
-__device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
-                                               const Control& u, float (&x)[8], float& sp, float& cp)
+// Per-step factors of the wheel-speed substep: steer, cos delta, sin delta, -sin delta and
+// h tau_max a / I_w.
+template <typename V>
+struct WheelsCtl {
+    V steer, cs, sn, nsn, hwa;
+};
+
+template <typename V>
+__device__ __forceinline__ WheelsCtl<V> wheels_ctl(const DevParams& P, const Control& u)
 {
-    const float vx = x[0], vy = x[1], r = x[2], wf = x[3], wr = x[4], ep = x[5], ey = x[6];
-    const float inv_vx = __fdividef(1.0f, fmaxf(vx, P.vx_floor));
-    const float yf = vy + P.lf * r;
-    const float alpha_f = u.steer - atanf(yf * inv_vx);
-    const float alpha_r = -atanf((vy - P.lr * r) * inv_vx);
-    const float vwf = fmaf(vx, u.cos_steer, yf * u.sin_steer);
-    const float kf = __fdividef(fmaf(P.Rw, wf, -vwf), fmaxf(fabsf(vwf), P.slip_floor));
-    const float kr = __fdividef(fmaf(P.Rw, wr, -vx), fmaxf(fabsf(vx), P.slip_floor));
-    const float gf = tyre_ratio(P, fmaf(kf, kf, alpha_f * alpha_f));
-    const float gr = tyre_ratio(P, fmaf(kr, kr, alpha_r * alpha_r));
-    const float Fxf = P.Dxf * gf * kf, Fyf = P.Df * gf * alpha_f;
-    const float Fxr = P.Dxr * gr * kr, Fyr = P.Dr * gr * alpha_r;
-    const float FXf = fmaf(Fxf, u.cos_steer, -Fyf * u.sin_steer);
-    const float FYf = fmaf(Fxf, u.sin_steer, Fyf * u.cos_steer);
-    const float kap_s = track_curvature(P, kap, s0 + x[7]);
-    const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
-    const float dvx = fmaf(FXf + Fxr, P.inv_m, vy * r);
-    const float dvy = fmaf(FYf + Fyr, P.inv_m, -vx * r);
-    const float dr = (P.lf * FYf - P.lr * Fyr) * P.inv_Iz;
-    const float dwf = -P.Rw * Fxf * P.inv_Iw;
-    const float dwr = fmaf(P.tau_max, u.accel, -P.Rw * Fxr) * P.inv_Iw;
-    const float dep = r - kap_s * sdot;
-    const float dey = vx * sp + vy * cp;
-    x[0] = fmaf(P.h, dvx, vx);
-    x[1] = fmaf(P.h, dvy, vy);
-    x[2] = fmaf(P.h, dr, r);
-    x[3] = fmaf(P.h, dwf, wf);
-    x[4] = fmaf(P.h, dwr, wr);
-    x[5] = fmaf(P.h, dep, ep);
-    x[6] = fmaf(P.h, dey, ey);
-    x[7] = fmaf(P.h, sdot, x[7]);
-    rotate_heading(P.h * dep, sp, cp);
+    WheelsCtl<V> c;
+    c.steer = splat<V>(u.steer);
+    c.cs = splat<V>(u.cos_steer);
+    c.sn = splat<V>(u.sin_steer);
+    c.nsn = splat<V>(-u.sin_steer);
+    c.hwa = splat<V>(__fmul_rn(__fmul_rn(P.h, P.tau_max), __fmul_rn(u.accel, P.inv_Iw)));
+    return c;
+}
+
+// One explicit-Euler substep of the wheel-speed model for one particle (V = float) or two side by
+// side (V = float2), as the bicycle substep: explicit roundings, per-particle transcendentals and
+// quotients, packed multiply-adds. With A = g_f kappa_f, B = g_f alpha_f, C = g_r kappa_r,
+// D = -g_r alpha_r and the front forces' h-scaled rotation into the body frame
+// F_X = h (F_xf cos - F_yf sin), F_Y = h (F_xf sin + F_yf cos):
+//   v_x' = v_x + F_X / m + (h D_xr / m) C + h v_y r,    v_y' = v_y + F_Y / m - (h D_r / m) D - h v_x r,
+//   r' = r + (l_f / I_z) F_Y + (h l_r D_r / I_z) D,      w_F' = w_F - (R_w / I_w) h D_xf A,
+//   w_R' = w_R + h tau_max a / I_w - (h R_w D_xr / I_w) C.
+template <typename V, typename Tab>
+__device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
+                                               const WheelsCtl<V>& u, V (&X)[8], V& sp, V& cp)
+{
+    const V vx = X[0], vy = X[1], r = X[2], wf = X[3], wr = X[4];
+    const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
+    const auto at = [](float a) { return atanf(a); };
+    const V yf = vfma(fold<V>(P, kFoldLf), r, vy);                                         // v_y + l_f r
+    const V af = vfma(each(vmul(yf, ivx), at), fold<V>(P, kFoldM1), u.steer);               // alpha_f
+    const V nar = each(vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx), at);                  // -alpha_r
+    const V vwf = vfma(vx, u.cs, vmul(yf, u.sn));                                          // front wheel's speed
+    const auto slip = [&](float num, float vw) { return __fdividef(num, fmaxf(fabsf(vw), P.slip_floor)); };
+    const V kf = each(vfma(fold<V>(P, kFoldWRw), wf, vmul(vwf, fold<V>(P, kFoldM1))), vwf, slip);
+    const V kr = each(vfma(fold<V>(P, kFoldWRw), wr, vmul(vx, fold<V>(P, kFoldM1))), vx, slip);
+    const V gf = tyre_ratio(P, vfma(kf, kf, vmul(af, af)));
+    const V gr = tyre_ratio(P, vfma(kr, kr, vmul(nar, nar)));
+    const V G1 = vmul(vmul(gf, kf), fold<V>(P, kFoldWhDxf));                               // h F_xf
+    const V G2 = vmul(vmul(gf, af), fold<V>(P, kFoldWhDf));                                // h F_yf
+    const V C = vmul(gr, kr), D = vmul(gr, nar);
+    const V FX = vfma(G2, u.nsn, vmul(G1, u.cs));
+    const V FY = vfma(G1, u.sn, vmul(G2, u.cs));
+    const V nk = each(X[7], [&](float a) { return -track_curvature(P, kap, s0 + a); });     // -kappa(s)
+    const V num = vfma(vx, cp, vmul(vmul(vy, sp), fold<V>(P, kFoldM1)));
+    const V den = vfma(nk, X[6], fold<V>(P, kFoldOne));
+    const V sdot = each(num, den, [](float a, float b) { return __fdividef(a, b); });
+    const V dep = vfma(nk, sdot, r);
+    const V dey = vfma(vx, sp, vmul(vy, cp));
+    const V h = fold<V>(P, kFoldH);
+    X[0] = vfma(FX, fold<V>(P, kFoldWInvM), vfma(C, fold<V>(P, kFoldWk3), vfma(vmul(vy, r), h, vx)));
+    X[1] = vfma(FY, fold<V>(P, kFoldWInvM), vfma(D, fold<V>(P, kFoldWk6), vfma(vmul(vx, r), fold<V>(P, kFoldNH), vy)));
+    X[2] = vfma(FY, fold<V>(P, kFoldWLfIz), vfma(D, fold<V>(P, kFoldWk9), r));
+    X[3] = vfma(G1, fold<V>(P, kFoldWk10), wf);
+    X[4] = vfma(C, fold<V>(P, kFoldWk11), vadd(wr, u.hwa));
+    X[5] = vfma(h, dep, X[5]);
+    X[6] = vfma(h, dey, X[6]);
+    X[7] = vfma(h, sdot, X[7]);
+    rotate_heading_v(P, vmul(h, dep), sp, cp);
 }
 
 // Tape of one bicycle substep: the transcendental results its adjoint needs
 // {F_yf, dF_yf/dalpha_f, dF_yr/dalpha_r, sin e_psi, cos e_psi, kappa(s), dkappa/ds}.
 constexpr int kTapeFloats = 7;
 
-// The same substep as bicycle_substep, also writing its tape (the repair's forward pass records it
-// so that the reverse sweep needs no transcendental functions).
+// The bicycle model's substep for one particle, with the forces written out unfolded, also writing
+// its tape (the repair's forward pass records it so that the reverse sweep needs no transcendental
+// functions). Its roundings differ from bicycle_substep's folded form by a few FP32 ulps.
 __device__ __forceinline__ void bicycle_substep_taped(const DevParams& P, const float* __restrict__ kap, float s0,
                                                       const Control& u, float (&x)[6], float (&tp)[kTapeFloats])
 {
@@ -562,7 +588,8 @@ __device__ __forceinline__ void model_step(const DevParams& P, const float* __re
     } else if constexpr (MODEL == 2) {
         float sp, cp;
         sincos_series(x[5], &sp, &cp);
-        for (int j = 0; j < P.n_sub; ++j) wheels_substep(P, kap, s0, u, x, sp, cp);
+        const WheelsCtl<float> c = wheels_ctl<float>(P, u);
+        for (int j = 0; j < P.n_sub; ++j) wheels_substep(P, kap, s0, c, x, sp, cp);
     } else {
         double_integrator_step(P, u, x);
     }

@@ -242,9 +242,9 @@ __host__ __device__ constexpr int roll_max_threads()
 // the segment's clamped control sequence u (T x 2) until the warp's next group. FULL selects the
 // full-belief variant: every mean and the whole covariance each step, which the general constraint
 // set (cs->n > 0, Eq. "DCBFchoice") and the literal reading of Algorithm 2 (dp.resample: particles
-// re-drawn from N(mean, cov) before the next step) need; cs is read only by it. PACK: bicycle
-// particles are stepped two at a time with packed FP32 instructions, bit-identical to stepping
-// them one at a time. Their constant operands come from the kernel's parameter space; a caller
+// re-drawn from N(mean, cov) before the next step) need; cs is read only by it. PACK: bicycle and
+// wheel-speed particles are stepped two at a time with packed FP32 instructions, bit-identical to
+// stepping them one at a time. Their constant operands come from the kernel's parameter space; a caller
 // whose parameters sit in shared memory turns it off, since there the packed operands would take
 // registers of their own.
 template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float, bool PACK = true>
@@ -368,35 +368,42 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         c.steer = u0;
         c.accel = u1;
         if constexpr (MODEL != 1) sincosf(u0, &c.sin_steer, &c.cos_steer);
-        if constexpr (MODEL == 0) {
+        if constexpr (MODEL != 1) {
             // the heading's sine and cosine: series at the step's start, rotated through the
             // substeps. With PACK, particles 2q and 2q + 1 of the lane share packed FP32 registers.
+            constexpr int HI = MODEL == 0 ? 3 : 5;
             constexpr bool PAIRS = PACK && P % 2 == 0;
             using V = typename std::conditional<PAIRS, float2, float>::type;
             constexpr int NV = PAIRS ? P / 2 : P;
-            const SubstepCtl<V> sc = substep_ctl<V>(dp, c);
-            V X[NV][6], hs[NV], hc[NV];
+            using Ctl = typename std::conditional<MODEL == 0, SubstepCtl<V>, WheelsCtl<V>>::type;
+            Ctl sc;
+            if constexpr (MODEL == 0) sc = substep_ctl<V>(dp, c);
+            else sc = wheels_ctl<V>(dp, c);
+            V X[NV][NX], hs[NV], hc[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
                 if constexpr (PAIRS) {
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) X[q][i] = make_float2(x[2 * q][i], x[2 * q + 1][i]);
-                    sincos_series(x[2 * q][3], &hs[q].x, &hc[q].x);
-                    sincos_series(x[2 * q + 1][3], &hs[q].y, &hc[q].y);
+                    for (int i = 0; i < NX; ++i) X[q][i] = make_float2(x[2 * q][i], x[2 * q + 1][i]);
+                    sincos_series(x[2 * q][HI], &hs[q].x, &hc[q].x);
+                    sincos_series(x[2 * q + 1][HI], &hs[q].y, &hc[q].y);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) X[q][i] = x[q][i];
-                    sincos_series(x[q][3], &hs[q], &hc[q]);
+                    for (int i = 0; i < NX; ++i) X[q][i] = x[q][i];
+                    sincos_series(x[q][HI], &hs[q], &hc[q]);
                 }
             }
             for (int j = 0; j < dp.n_sub; ++j) {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) bicycle_substep(dp, kap_s, s0, sc, X[q], hs[q], hc[q]);
+                for (int q = 0; q < NV; ++q) {
+                    if constexpr (MODEL == 0) bicycle_substep(dp, kap_s, s0, sc, X[q], hs[q], hc[q]);
+                    else wheels_substep(dp, kap_s, s0, sc, X[q], hs[q], hc[q]);
+                }
             }
 #pragma unroll
             for (int q = 0; q < NV; ++q)
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
+                for (int i = 0; i < NX; ++i) {
                     if constexpr (PAIRS) {
                         x[2 * q][i] = X[q][i].x;
                         x[2 * q + 1][i] = X[q][i].y;
@@ -404,16 +411,6 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
                         x[q][i] = X[q][i];
                     }
                 }
-        } else if constexpr (MODEL != 1) {
-            // the heading's sine and cosine: series at the step's start, rotated through the substeps
-            constexpr int HI = MODEL == 0 ? 3 : 5;
-            float hs[P], hc[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) sincos_series(x[p][HI], &hs[p], &hc[p]);
-            for (int j = 0; j < dp.n_sub; ++j) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) wheels_substep(dp, kap_s, s0, c, x[p], hs[p], hc[p]);
-            }
         } else {
 #pragma unroll
             for (int p = 0; p < P; ++p) double_integrator_step(dp, c, x[p]);

@@ -275,6 +275,19 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.fold[kFoldTB] = d.tB; d.fold[kFoldNTB] = -d.tB; d.fold[kFoldTC] = d.tC;
     d.fold[kFoldHa3] = (float)((double)d.h * d.Dr * d.inv_m);
     d.fold[kFoldHb2] = (float)(-(double)d.h * d.lr * d.Dr * d.inv_Iz);
+    if (p->model == BSSMPPI_MODEL_WHEELS8) {
+        const double h = d.h;
+        d.fold[kFoldWRw] = d.Rw;
+        d.fold[kFoldWhDxf] = (float)(h * d.Dxf);
+        d.fold[kFoldWhDf] = (float)(h * d.Df);
+        d.fold[kFoldWInvM] = d.inv_m;
+        d.fold[kFoldWk3] = (float)(h * d.Dxr / p->mass);
+        d.fold[kFoldWk6] = (float)(-h * d.Dr / p->mass);
+        d.fold[kFoldWLfIz] = (float)((double)p->lf / p->Iz);
+        d.fold[kFoldWk9] = (float)(h * p->lr * d.Dr / p->Iz);
+        d.fold[kFoldWk10] = (float)(-(double)p->wheel_radius / p->wheel_inertia);
+        d.fold[kFoldWk11] = (float)(-h * p->wheel_radius * d.Dxr / p->wheel_inertia);
+    }
     for (int i = kFoldOne; i < kFoldN; ++i) d.fold[i] = fold_fixed(i);
     for (int i = 0; i < kFoldN; ++i) d.fold2[i] = make_float2(d.fold[i], d.fold[i]);
     return BSSMPPI_OK;
