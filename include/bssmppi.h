@@ -39,7 +39,7 @@ extern "C" {
 
 #define BSSMPPI_ABI_VERSION 2u
 #define BSSMPPI_NU 2          /* controls: [steer delta (rad), acceleration (m/s^2)] */
-#define BSSMPPI_NX_MAX 6
+#define BSSMPPI_NX_MAX 8          /* states: 6 (bicycle), 4 (double integrator), 8 (wheel speeds) */
 #define BSSMPPI_K_MAX (1 << 20)
 #define BSSMPPI_M_MAX 256
 #define BSSMPPI_T_MAX 256

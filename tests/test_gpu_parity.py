@@ -198,6 +198,38 @@ def test_solve_extreme_shapes(model, K, M, T):
     check_solve(p, workload.random_state(p, K), workload.random_nominal(p, K), ctr=K)
 
 
+def test_maximum_sample_count_sampled_parity():
+    """K = BSSMPPI_K_MAX = 2^20 samples (65,536 groups of 16 two-particle samples per warp, through
+    the persistent grid and its 152-block tail): sampled perturbations and costs against the oracle,
+    the weights and update against the oracle's from the GPU's own costs."""
+    p = workload.config0()
+    p.K, p.M, p.T = 1 << 20, 2, 3
+    x0, v = workload.random_state(p, 9), workload.random_nominal(p, 9)
+    g = gpu_solve(p, x0, v, ctr=1, record=False)
+    o = oracle.Oracle(p)
+    for k in (0, 1, 15, 16, 777777, p.K - 1):
+        r = o.solve(x0, v, 1, k_range=(k, k + 1))
+        assert_close(g["eps"][k], r["eps"][k], 0.0, 1e-6, f"eps[{k}]")
+        if r["margin"][k] > 1e-3:
+            assert abs(g["S"][k] - r["S"][k]) <= 1e-4 * max(1.0, abs(r["S"][k])), k
+    u_gpu = v.astype(np.float64)[None] + g["eps"]
+    w_iso, vp_iso, _ = oracle.optimal_control(g["S"], u_gpu, float(np.float32(p.lam)))
+    assert_close(g["w"], w_iso, 1e-5, 1e-7, "weights")
+    assert_close(g["v_plus"], vp_iso, 1e-4, 1e-5, "v+")
+    assert g["counter"] == 2
+
+
+@pytest.mark.parametrize("n_track,M,T", [(2, 16, 20), (16384, 256, 32)])
+def test_curvature_table_sizes(n_track, M, T):
+    """The smallest curvature table (two entries) and the largest (BSSMPPI_NTRACK_MAX = 2^14
+    entries: 128 KiB of (value, difference) pairs staged in shared memory beside the largest particle
+    count's buffers)."""
+    p = workload.config0()
+    p.M, p.T = M, T
+    p.kappa, p.track_len = workload.make_track(7, n_s=n_track)
+    check_solve(p, workload.random_state(p, 3), workload.random_nominal(p, 3), ctr=2)
+
+
 def test_solve_ragged_K_and_long_horizon():
     p = workload.config1()
     p.K, p.M, p.T = 1001, 64, 40
