@@ -407,6 +407,13 @@ int bssmppi_philox4x32_10(const uint32_t* d_ctr, uint64_t seed, uint32_t* d_out,
  */
 int bssmppi_box_muller(const uint32_t* d_words, float* d_z, int64_t n, void* cuda_stream);
 
+/*
+ * The slip-angle arctangent as the bicycle substep evaluates it: d_y[i] = atan(d_t[i])
+ * for n values; device arrays. For |t| <= 1/2 an odd polynomial of degree 11 (within one FP32 ulp), beyond
+ * it the library's atanf. Exported so that its error can be checked against an exact reference.
+ */
+int bssmppi_slip_atan(const float* d_t, float* d_y, int64_t n, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -130,6 +130,7 @@ def load(build_if_missing: bool = True):
         "bssmppi_model_step": (ctypes.c_int, [vp, vp, vp, vp, vp, i64]),
         "bssmppi_philox4x32_10": (ctypes.c_int, [vp, u64, vp, i64, vp]),
         "bssmppi_box_muller": (ctypes.c_int, [vp, vp, i64, vp]),
+        "bssmppi_slip_atan": (ctypes.c_int, [vp, vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -405,6 +406,11 @@ def philox4x32_10(ctr, seed: int, out, stream=None):
 
 def box_muller(words, z, stream=None):
     _check(load().bssmppi_box_muller(_ptr(words), _ptr(z), words.numel() // 2, _stream_handle(stream)))
+
+
+def slip_atan(t, y, stream=None):
+    """y = atan(t) as the substeps take the slip angles (float32 device tensors of equal size)."""
+    _check(load().bssmppi_slip_atan(_ptr(t), _ptr(y), t.numel(), _stream_handle(stream)))
 
 
 class Controller:

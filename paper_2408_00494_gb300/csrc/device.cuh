@@ -306,6 +306,27 @@ template <> __device__ __forceinline__ float fold<float>(const DevParams& P, int
 }
 template <> __device__ __forceinline__ float2 fold<float2>(const DevParams& P, int i) { return P.fold2[i]; }
 
+// atan t for the bicycle's slip angles, whose arguments (v_y + l_f r) / v_x and (v_y - l_r r) / v_x
+// stay small while the tyres grip. For |t| <= 1/2, atan t = t + t z p(z) with z = t^2 and p of degree 4, its
+// coefficients fitted for the least maximum relative error on [0, 1/2] by Lawson's iteratively
+// reweighted least squares (fit_slip_atan.py beside this package): 5.3e-9 in exact arithmetic,
+// 0.72 FP32 ulp by Horner's rule with fused multiply-adds. Beyond, the library's atanf. The choice
+// is made per particle, so a result does not depend on which particles share a warp. (The
+// wheel-speed model keeps atanf for its slip angles: there the branch measured slower.)
+__device__ __forceinline__ float slip_atan(float t)
+{
+    if (fabsf(t) <= 0.5f) {
+        const float z = __fmul_rn(t, t);
+        float p = -5.1325989538e-2f;
+        p = fmaf(p, z, 1.0160016107e-1f);
+        p = fmaf(p, z, -1.4175010834e-1f);
+        p = fmaf(p, z, 1.9994226694e-1f);
+        p = fmaf(p, z, -3.3333234306e-1f);
+        return fmaf(__fmul_rn(t, z), p, t);
+    }
+    return atanf(t);
+}
+
 // Per-step factors (the control is the same for every particle of a sample): steer, h a,
 // -h D_f sin(delta) / m, h D_f cos(delta) / m, h l_f D_f cos(delta) / I_z.
 template <typename V>
@@ -349,9 +370,10 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* _
     const V tf = vmul(vfma(fold<V>(P, kFoldLf), r, vy), ivx);    // (v_y + l_f r) / v_x
     const V tr = vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx);   // (v_y - l_r r) / v_x
     const auto at = [](float a) { return atanf(a); };
-    const V af = vfma(each(tf, at), fold<V>(P, kFoldM1), u.steer);    // alpha_f
+    const auto slip = [](float a) { return slip_atan(a); };
+    const V af = vfma(each(tf, slip), fold<V>(P, kFoldM1), u.steer);  // alpha_f
     const V bf = vmul(fold<V>(P, kFoldTB), af);                        // B alpha_f
-    const V br = vmul(fold<V>(P, kFoldNTB), each(tr, at));             // B alpha_r
+    const V br = vmul(fold<V>(P, kFoldNTB), each(tr, slip));           // B alpha_r
     // |C atan(B alpha)| < C pi / 2 < pi: inside the range where the hardware sine's absolute error
     // is at most 2^-21.4 of the unit amplitude (a relative force error of a few FP32 ulps).
     const auto sn = [](float a) { return __sinf(a); };
@@ -426,10 +448,10 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __
 {
     const V vx = X[0], vy = X[1], r = X[2], wf = X[3], wr = X[4];
     const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
-    const auto at = [](float a) { return atanf(a); };
     const V yf = vfma(fold<V>(P, kFoldLf), r, vy);                                         // v_y + l_f r
-    const V af = vfma(each(vmul(yf, ivx), at), fold<V>(P, kFoldM1), u.steer);               // alpha_f
-    const V nar = each(vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx), at);                  // -alpha_r
+    const auto sa = [](float a) { return atanf(a); };
+    const V af = vfma(each(vmul(yf, ivx), sa), fold<V>(P, kFoldM1), u.steer);               // alpha_f
+    const V nar = each(vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx), sa);                  // -alpha_r
     const V vwf = vfma(vx, u.cs, vmul(yf, u.sn));                                          // front wheel's speed
     const auto slip = [&](float num, float vw) { return __fdividef(num, fmaxf(fabsf(vw), P.slip_floor)); };
     const V kf = each(vfma(fold<V>(P, kFoldWRw), wf, vmul(vwf, fold<V>(P, kFoldM1))), vwf, slip);

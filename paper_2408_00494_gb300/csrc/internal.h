@@ -48,6 +48,7 @@ cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* 
                               cudaStream_t st);
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st);
 cudaError_t box_muller_launch(const uint32_t* words, float* z, int64_t n, cudaStream_t st);
+cudaError_t slip_atan_launch(const float* t, float* y, int64_t n, cudaStream_t st);
 
 // Weights + update: the number of blocks for K samples, and the launch.
 int update_blocks(int K);

@@ -123,6 +123,12 @@ __global__ void box_muller_kernel(const uint2* __restrict__ words, float2* __res
     if (i < n) z[i] = box_muller(words[i].x, words[i].y);
 }
 
+__global__ void slip_atan_kernel(const float* __restrict__ t, float* __restrict__ y, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = slip_atan(t[i]);
+}
+
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
@@ -139,6 +145,14 @@ cudaError_t box_muller_launch(const uint32_t* words, float* z, int64_t n, cudaSt
     const int threads = 256;
     box_muller_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
         reinterpret_cast<const uint2*>(words), reinterpret_cast<float2*>(z), n);
+    return cudaGetLastError();
+}
+
+cudaError_t slip_atan_launch(const float* t, float* y, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    slip_atan_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(t, y, n);
     return cudaGetLastError();
 }
 

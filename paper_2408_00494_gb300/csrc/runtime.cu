@@ -705,4 +705,11 @@ int bssmppi_box_muller(const uint32_t* d_words, float* d_z, int64_t n, void* cud
     return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(nullptr, e, "box_muller");
 }
 
+int bssmppi_slip_atan(const float* d_t, float* d_y, int64_t n, void* cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!d_t || !d_y))) return fail(nullptr, BSSMPPI_EINVAL, "bad arrays");
+    cudaError_t e = bss::slip_atan_launch(d_t, d_y, n, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(nullptr, e, "slip_atan");
+}
+
 }  // extern "C"

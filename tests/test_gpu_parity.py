@@ -137,6 +137,29 @@ def test_box_muller_matches_oracle():
     assert zg[0, 0] == 0.0 and zg[0, 1] == 0.0
 
 
+def test_slip_angle_arctangent_within_an_ulp():
+    """The substeps' slip-angle arctangent against atan in FP64: within one FP32 ulp on the
+    polynomial's range |t| <= 1/2 (the fit gives 0.72), within the library atanf's documented 2 ulp
+    beyond it, exact at 0 and odd."""
+    pos = np.linspace(0.0, 0.5, 1 << 19, dtype=np.float32)
+    inner = np.concatenate([pos, -pos])
+    edge = np.nextafter(np.float32(0.5), np.float32([0.0, 1.0])).astype(np.float32)
+    outer = np.concatenate([np.geomspace(0.5, 1e6, 1 << 16), -np.geomspace(0.5, 1e6, 1 << 16)]).astype(np.float32)
+    t = np.concatenate([inner, edge, -edge, outer, np.float32([0.0, 1e-30, -1e-30])])
+    y = torch.zeros(t.size, device="cuda")
+    bssmppi.slip_atan(_dev(t), y)
+    y = y.cpu().numpy()
+    ref = np.arctan(t.astype(np.float64))
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    err = np.abs(y - ref) / ulp
+    small = np.abs(t) <= 0.5
+    assert err[small].max() <= 1.0, err[small].max()
+    assert err[~small].max() <= 2.0, err[~small].max()
+    assert y[t == 0].max() == 0.0
+    n = pos.size
+    assert np.array_equal(y[:n], -y[n:2 * n])
+
+
 @pytest.mark.parametrize("model", ["bicycle", "double_integrator"])
 def test_model_step_matches_oracle(model):
     if model == "bicycle":
