@@ -7,13 +7,15 @@
 // (common random numbers), so J_r is a deterministic, piecewise-smooth function of v.
 //
 // One block, one thread per particle (M <= 256). Forward: propagate, store every particle's state
-// at every Euler substep in scratch (L2-resident), merge count/mean/M2 of e_y across the block
-// (Chan's pairwise update), and form h_t, the hinge arguments and J. Reverse: for t = T..1 add
-// dJ/dh_t through the mean and the unbiased standard deviation to each particle's e_y cotangent,
-// then pull the cotangent back through the n_sub substeps from their stored states (the next
-// state is loaded while the current adjoint runs) and sum dJ/du_{t-1} over the particles. The
-// kernel is latency-bound (a serial chain per particle); storing the substates removes the
-// forward recomputation from the reverse chain. `iters` projected gradient steps
+// at every Euler substep in scratch (L2-resident); then, in parallel over the steps, merge
+// count/mean/M2 of e_y across the particles (Chan's pairwise update) and form h_t, the hinge
+// arguments and J. Reverse: for t = T..1 add dJ/dh_t through the mean and the unbiased standard
+// deviation to each particle's e_y cotangent, then pull the cotangent back through the n_sub
+// substeps from their stored states (the next state is loaded while the current adjoint runs) and
+// sum dJ/du_{t-1} over the warp's particles; the sum over warps follows the sweep. Neither pass
+// has a barrier inside its loop over the steps, so each warp runs its particles' chains at its own
+// pace. The kernel is latency-bound (a serial chain per particle); storing the substates removes
+// the forward recomputation from the reverse chain. `iters` projected gradient steps
 // v <- clamp(v - step dJ/dv) run inside one launch.
 #include "device.cuh"
 #include "internal.h"
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
     float* sig_s = mean_s + (T + 1);             // T+1
     float* arg_s = sig_s + (T + 1);              // T+2 (arg_s[T+1] < 0: no successor)
     float* gv_s = arg_s + (T + 2);               // 2T
-    float* red = gv_s + 2 * T;                   // 2 buffers x 8 warps x 3
+    float* part_s = gv_s + 2 * T;                // 2T x 8: per-warp sums of dJ/du
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int n = tid;
@@ -130,7 +132,16 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
 #pragma unroll
                 for (int i = 0; i < NX; ++i) *Xat(t + 1, i) = x[i];
             }
-            float cnt = valid ? 1.0f : 0.0f, mu = valid ? x[EY] : 0.0f, m2 = 0.0f;
+        }
+        __syncthreads();  // every particle's states are in X
+        // The moments of e_y at every step, in parallel over the steps (the dynamics do not read
+        // them, so no particle waits for another during the rollout): warp w takes t = 1 + w,
+        // 1 + w + nw, ...; each lane merges particles lane, lane + 32, ... one by one, then Chan's
+        // pairwise merge across the lanes.
+        for (int t = 1 + wid; t <= T; t += nw) {
+            const float* ey = io.X + (((size_t)t * nsub) * R + EY) * M;
+            float cnt = 0.0f, mu = 0.0f, m2 = 0.0f;
+            for (int q = lane; q < M; q += 32) chan_merge(cnt, mu, m2, 1.0f, ey[q], 0.0f);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const float nb = __shfl_xor_sync(0xffffffffu, cnt, off);
@@ -138,18 +149,9 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
                 const float m2b = __shfl_xor_sync(0xffffffffu, m2, off);
                 chan_merge(cnt, mu, m2, nb, mb, m2b);
             }
-            float* rb = red + (t & 1) * 24;
             if (lane == 0) {
-                rb[3 * wid] = cnt;
-                rb[3 * wid + 1] = mu;
-                rb[3 * wid + 2] = m2;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                float n0 = rb[0], m0 = rb[1], q0 = rb[2];
-                for (int w = 1; w < nw; ++w) chan_merge(n0, m0, q0, rb[3 * w], rb[3 * w + 1], rb[3 * w + 2]);
-                mean_s[t + 1] = m0;
-                sig_s[t + 1] = sqrtf(fmaxf(q0 * dp.invM1, 0.0f));
+                mean_s[t] = mu;
+                sig_s[t] = sqrtf(fmaxf(m2 * dp.invM1, 0.0f));
             }
         }
         __syncthreads();
@@ -175,39 +177,22 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
         float g[NX];
 #pragma unroll
         for (int i = 0; i < NX; ++i) g[i] = 0.0f;
-        for (int t = T; t >= 1; --t) {
+        // dJ/dh_t into the e_y cotangent (through the mean and the unbiased standard deviation);
+        // ey_t is this particle's e_y at step t.
+        auto inject = [&](int t, float ey_t) {
             const float gh = (arg_s[t] > 0.0f ? -dp.Csafe : 0.0f) + (arg_s[t + 1] > 0.0f ? dp.Csafe * dp.one_m_gamma : 0.0f);
             if (valid && gh != 0.0f) {
                 const float mt = mean_s[t], st = sig_s[t];
                 float term = -2.0f * mt * dp.invM;
                 if (st > 0.0f) {
                     const float dh_dsig = -2.0f * dp.nu * (dp.wT - dp.nu * st);
-                    term += dh_dsig * (*Xat(t, EY) - mt) * dp.invM1 / st;
+                    term += dh_dsig * (ey_t - mt) * dp.invM1 / st;
                 }
                 g[EY] += gh * term;
             }
-            Control c;
-            c.steer = v_s[2 * (t - 1)];
-            c.accel = v_s[2 * (t - 1) + 1];
-            float gs = 0.0f, ga = 0.0f;
-            if constexpr (MODEL == 0) {
-                sincosf(c.steer, &c.sin_steer, &c.cos_steer);
-                // The forward pass stored each substep's state and tape; the next record is loaded
-                // while the current substep's adjoint runs, so the loads stay off the chain.
-                float cur[R], nxt[R];
-#pragma unroll
-                for (int i = 0; i < R; ++i) cur[i] = valid ? *Xs(t - 1, nsub - 1, i) : (i < 6 ? x0[i] : 0.0f);
-                for (int j = nsub - 1; j >= 0; --j) {
-#pragma unroll
-                    for (int i = 0; i < R; ++i) nxt[i] = (valid && j > 0) ? *Xs(t - 1, j - 1, i) : cur[i];
-                    bicycle_substep_vjp_taped(dp, c, *reinterpret_cast<const float(*)[6]>(cur),
-                                              *reinterpret_cast<const float(*)[kTapeFloats]>(cur + 6), g, gs, ga);
-#pragma unroll
-                    for (int i = 0; i < R; ++i) cur[i] = nxt[i];
-                }
-            } else {
-                double_integrator_step_vjp(dp, g, gs, ga);
-            }
+        };
+        // the warp's sum of dJ/du_t; the sum over warps waits until the sweep is done (no barrier per step)
+        auto store_du = [&](int t, float gs, float ga) {
             if (!valid) {
                 gs = 0.0f;
                 ga = 0.0f;
@@ -217,21 +202,70 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
                 gs += __shfl_xor_sync(0xffffffffu, gs, off);
                 ga += __shfl_xor_sync(0xffffffffu, ga, off);
             }
-            float* rb = red + 48 + (t & 1) * 16;
             if (lane == 0) {
-                rb[2 * wid] = gs;
-                rb[2 * wid + 1] = ga;
+                part_s[(2 * t) * 8 + wid] = gs;
+                part_s[(2 * t + 1) * 8 + wid] = ga;
             }
-            __syncthreads();
-            if (tid == 0) {
-                float a0 = 0.0f, a1 = 0.0f;
-                for (int w = 0; w < nw; ++w) {
-                    a0 += rb[2 * w];
-                    a1 += rb[2 * w + 1];
+        };
+        if constexpr (MODEL == 0) {
+            // One pass over the S = T n_sub substep records from the last to the first (record
+            // s = t n_sub + j: the state entering substep j of step t and that substep's tape).
+            // Records s - 1, s - 2 and s - 3 are in flight while substep s's adjoint runs, across
+            // the step boundaries too, so the L2 latency stays off the chain.
+            const int S = T * nsub;
+            auto load = [&](float (&r)[R], int sr) {
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    r[i] = (valid && sr >= 0) ? io.X[((size_t)sr * R + i) * M + n] : (i < 6 ? x0[i] : 0.0f);
+            };
+            float r0[R], r1[R], r2[R], r3[R];
+            load(r0, S - 1);
+            load(r1, S - 2);
+            load(r2, S - 3);
+            float ey_next = valid ? *Xat(T, EY) : 0.0f;  // e_y at the end of the step being entered
+            int t = T - 1, j = nsub - 1;
+            Control c;
+            float gs = 0.0f, ga = 0.0f;
+            for (int sr = S - 1; sr >= 0; --sr) {
+                load(r3, sr - 3);
+                if (j == nsub - 1) {  // entering step t from its end
+                    inject(t + 1, ey_next);
+                    c.steer = v_s[2 * t];
+                    c.accel = v_s[2 * t + 1];
+                    sincosf(c.steer, &c.sin_steer, &c.cos_steer);
+                    gs = 0.0f;
+                    ga = 0.0f;
                 }
-                gv_s[2 * (t - 1)] = a0;
-                gv_s[2 * (t - 1) + 1] = a1;
+                bicycle_substep_vjp_taped(dp, c, *reinterpret_cast<const float(*)[6]>(r0),
+                                          *reinterpret_cast<const float(*)[kTapeFloats]>(r0 + 6), g, gs, ga);
+                if (j == 0) {  // left step t at its start
+                    ey_next = r0[EY];
+                    store_du(t, gs, ga);
+                    --t;
+                    j = nsub - 1;
+                } else {
+                    --j;
+                }
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    r0[i] = r1[i];
+                    r1[i] = r2[i];
+                    r2[i] = r3[i];
+                }
             }
+        } else {
+            for (int t = T; t >= 1; --t) {
+                inject(t, valid ? *Xat(t, EY) : 0.0f);
+                float gs = 0.0f, ga = 0.0f;
+                double_integrator_step_vjp(dp, g, gs, ga);
+                store_du(t - 1, gs, ga);
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < 2 * T; i += blockDim.x) {
+            float a = 0.0f;
+            for (int w = 0; w < nw; ++w) a += part_s[i * 8 + w];
+            gv_s[i] = a;
         }
         __syncthreads();
         if (last) {
@@ -260,7 +294,7 @@ size_t repair_scratch_floats(const DevParams& dp)
 static size_t repair_smem_bytes(const DevParams& dp)
 {
     const int ntab = dp.n_track_mask + 1;
-    const size_t floats = (size_t)((ntab + 1 + 3) & ~3) + 2 * dp.T + 2 * (dp.T + 1) + (dp.T + 2) + 2 * dp.T + 48 + 32;
+    const size_t floats = (size_t)((ntab + 1 + 3) & ~3) + 2 * dp.T + 2 * (dp.T + 1) + (dp.T + 2) + 2 * dp.T + 16 * dp.T;
     return floats * sizeof(float);
 }
 
