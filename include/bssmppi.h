@@ -188,7 +188,10 @@ int bssmppi_solve_shift(bssmppi_t h, const float* d_x0, const float* d_Sigma0, f
  * The same solve with host buffers: stages h_x0, h_v (NULL = resident) and h_Sigma0 (if non-NULL)
  * in the handle's pinned buffer and copies them to the device in one transfer, solves, reads v+ and
  * the first control back in one transfer into h_v and h_u0 (each if non-NULL), and waits for the
- * stream. Synchronous; the host pointers may be pageable.
+ * stream. Synchronous; the host pointers may be pageable. The two copies and the kernel are
+ * captured once per combination of the optional buffers as a CUDA graph and replayed (rebuilt
+ * after bssmppi_set_constraints or bssmppi_set_sample_range); while timing events are requested
+ * (bssmppi_timing) they are issued one by one instead.
  */
 int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, float* h_v, float* h_u0);
 

@@ -156,7 +156,7 @@ def _hptr(a):
         return None
     if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
         raise ValueError("expected a contiguous float32 numpy array")
-    return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(a.__array_interface__["data"][0])
 
 
 def _check(rc, h=None):

@@ -36,6 +36,11 @@ struct bssmppi_ctx {
     float* d_repair_X = nullptr;  // stored particle states of the repair rollout
     float* d_repair_J = nullptr;  // objective of the last repair_grad call
     float* h_stage = nullptr;   // pinned host staging: x0 (8) | v (2T) | Sigma0 (64) || v+ (2T) | u0 (2)
+    // The host-buffer solve as CUDA graphs (H2D copy, solve kernel, D2H copy), one per combination
+    // of the optional buffers, captured on first use on a private stream and replayed on `stream`.
+    // Dropped whenever the kernel's by-value parameters change (sample range, constraint set).
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t host_graph[8] = {};
     // timing ring: 2 events per recorded solve
     cudaEvent_t* ev = nullptr;
     int ev_cap = 0, ev_count = 0;
@@ -177,6 +182,13 @@ void release(bssmppi_ctx* h)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_stage) cudaFreeHost(h->h_stage);
+    for (cudaGraphExec_t& g : h->host_graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
     for (int i = 0; i < 2 * h->ev_cap; ++i) cudaEventDestroy(h->ev[i]);
     delete[] h->ev;
     h->ev = nullptr;
@@ -391,19 +403,58 @@ namespace {
 
 // One solve launch: the rollout reads the nominal from v_in; the tail writes v+ to the resident
 // nominal and the first control to u0.
-int launch_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, const float* v_in, float* u0, int shift_n = 0)
+int launch_solve(bssmppi_t h, const float* d_x0, const float* d_Sigma0, const float* v_in, float* u0, int shift_n = 0,
+                 cudaStream_t st = nullptr, bool timed = true)
 {
-    cudaEvent_t* ev = (h->ev_count < h->ev_cap) ? h->ev + 2 * h->ev_count : nullptr;
-    if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], h->stream));
+    if (!st) st = h->stream;
+    cudaEvent_t* ev = (timed && h->ev_count < h->ev_cap) ? h->ev + 2 * h->ev_count : nullptr;
+    if (ev) BSS_CUDA(h, cudaEventRecord(ev[0], st));
     // One launch: rollout, costs, and (in its tail) weights, update, u0, diagnostics, counter.
     bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, u0, h->d_diag, h->d_ctr, h->d_v, nullptr, shift_n};
     BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, v_in, h->d_ctr,
-                                    h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, h->stream));
+                                    h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, st));
     if (ev) {
-        BSS_CUDA(h, cudaEventRecord(ev[1], h->stream));
+        BSS_CUDA(h, cudaEventRecord(ev[1], st));
         ++h->ev_count;
     }
     return BSSMPPI_OK;
+}
+
+void drop_host_graphs(bssmppi_t h)
+{
+    for (cudaGraphExec_t& g : h->host_graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Records the host-buffer solve's three operations (H2D of n_in staged floats, the solve, D2H of
+// v+ | u0 when `out`) on the private capture stream and instantiates them as one graph.
+int capture_host_graph(bssmppi_t h, size_t n_in, bool with_v, bool with_S0, bool out, cudaGraphExec_t* ex)
+{
+    if (!h->cap_stream) BSS_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream;
+    const int T = h->prm.T;
+    float* sout = h->h_stage + 8 + 2 * T + 64;
+    BSS_CUDA(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemcpyAsync(h->d_in, h->h_stage, sizeof(float) * n_in, cudaMemcpyHostToDevice, cs);
+    int rc = BSSMPPI_OK;
+    if (e == cudaSuccess)
+        rc = launch_solve(h, h->d_x0, with_S0 ? h->d_Sigma0 : nullptr, with_v ? h->d_in + 8 : h->d_v, h->d_u0, 0, cs,
+                          false);
+    if (e == cudaSuccess && rc == BSSMPPI_OK && out)
+        e = cudaMemcpyAsync(sout, h->d_v, sizeof(float) * (2 * T + 2), cudaMemcpyDeviceToHost, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(cs, &g);  // always ends the capture
+    if (rc != BSSMPPI_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e == cudaSuccess) e = e_end;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(h, e, "host-buffer solve graph");
 }
 
 }  // namespace
@@ -442,11 +493,21 @@ int bssmppi_solve_host(bssmppi_t h, const float* h_x0, const float* h_Sigma0, fl
     if (h_v) std::memcpy(sv, h_v, sizeof(float) * 2 * T);
     if (h_Sigma0) std::memcpy(sS0, h_Sigma0, sizeof(float) * nx * nx);
     const size_t n_in = h_Sigma0 ? (size_t)(8 + 2 * T + nx * nx) : (h_v ? (size_t)(8 + 2 * T) : (size_t)nx);
-    BSS_CUDA(h, cudaMemcpyAsync(h->d_in, sx0, sizeof(float) * n_in, cudaMemcpyHostToDevice, h->stream));
-    const int rc = launch_solve(h, h->d_x0, h_Sigma0 ? h->d_Sigma0 : nullptr, h_v ? h->d_in + 8 : h->d_v, h->d_u0);
-    if (rc != BSSMPPI_OK) return rc;
-    if (h_v || h_u0)
-        BSS_CUDA(h, cudaMemcpyAsync(sout, h->d_v, sizeof(float) * (2 * T + 2), cudaMemcpyDeviceToHost, h->stream));
+    const bool out = h_v || h_u0;
+    if (h->ev_count < h->ev_cap) {  // timing events requested: plain launches, so each solve records its own
+        BSS_CUDA(h, cudaMemcpyAsync(h->d_in, sx0, sizeof(float) * n_in, cudaMemcpyHostToDevice, h->stream));
+        const int rc = launch_solve(h, h->d_x0, h_Sigma0 ? h->d_Sigma0 : nullptr, h_v ? h->d_in + 8 : h->d_v, h->d_u0);
+        if (rc != BSSMPPI_OK) return rc;
+        if (out)
+            BSS_CUDA(h, cudaMemcpyAsync(sout, h->d_v, sizeof(float) * (2 * T + 2), cudaMemcpyDeviceToHost, h->stream));
+    } else {  // one graph launch: the copies and the kernel run back to back without host round trips
+        cudaGraphExec_t& ex = h->host_graph[(h_v ? 1 : 0) | (h_Sigma0 ? 2 : 0) | (out ? 4 : 0)];
+        if (!ex) {
+            const int rc = capture_host_graph(h, n_in, h_v != nullptr, h_Sigma0 != nullptr, out, &ex);
+            if (rc != BSSMPPI_OK) return rc;
+        }
+        BSS_CUDA(h, cudaGraphLaunch(ex, h->stream));
+    }
     BSS_CUDA(h, cudaStreamSynchronize(h->stream));
     if (h_v) std::memcpy(h_v, sout, sizeof(float) * 2 * T);
     if (h_u0) std::memcpy(h_u0, sout + 2 * T, sizeof(float) * 2);
@@ -461,6 +522,7 @@ int bssmppi_set_sample_range(bssmppi_t h, int32_t k_begin, int32_t K_total)
     BSS_CUDA(h, cudaStreamSynchronize(h->stream));  // solves in flight keep the old range
     h->dp.k_off = k_begin;
     h->dp.K_norm = K_total;
+    drop_host_graphs(h);
     return BSSMPPI_OK;
 }
 
@@ -538,6 +600,7 @@ int bssmppi_set_constraints(bssmppi_t h, const bssmppi_constraint* cons, int32_t
     BSS_CUDA(h, bss::rollout_prepare(h->dp, h->P, h->prm.compensated != 0, full, L));
     h->roll = L;
     h->cons = cs;
+    drop_host_graphs(h);
     return BSSMPPI_OK;
 }
 

@@ -345,6 +345,40 @@ def test_solve_host_matches_device_path(case):
     assert np.array_equal(u0.astype(np.float64), g["u0"])
 
 
+def test_host_solve_graph_follows_the_handle_state():
+    """The host-buffer solve replays a captured graph (H2D, solve kernel, D2H). Replays must read the
+    current solve counter and nominal, a new constraint set must replace the graph (the kernel takes
+    the set by value), and with timing events on the plain path must run: each result equals the
+    device-buffer solve of the same state bit for bit."""
+    p = workload.config0()
+    x0, v = workload.random_state(p, 21), workload.random_nominal(p, 21)
+    cons = (workload.halfspace((0, 0, 0, 0, 1, 0), p.w_T, p.delta),
+            workload.disk(5, 4, (float(x0[5]) + 5.0, 0.2), 0.8, 0.05))
+    c = bssmppi.Controller(p)
+    try:
+        bssmppi.set_counter(c.h, 7)
+        got = []
+        for step in range(4):
+            if step == 2:
+                bssmppi.set_constraints(c.h, cons)
+            if step == 3:
+                bssmppi.timing(c.h, 2)
+            vh, u0 = v.copy(), np.zeros(2, np.float32)
+            bssmppi.solve_host(c.h, x0.astype(np.float32), None, vh, u0)
+            got.append((vh.astype(np.float64), u0.astype(np.float64)))
+        roll_ms, _ = bssmppi.timing_read(c.h, 2)
+        assert len(roll_ms) == 1 and roll_ms[0] > 0.0
+    finally:
+        c.close()
+    for step, (vh, u0) in enumerate(got):
+        q = workload.config0()
+        if step >= 2:
+            q.constraints = cons
+        g = gpu_solve(q, x0, v, ctr=7 + step, record=False)
+        assert np.array_equal(vh, g["v_plus"]), step
+        assert np.array_equal(u0, g["u0"]), step
+
+
 def test_full_size_config1_sampled_parity():
     """The benchmark's workload and launch configuration (K=4096, M=64, T=40, moments not kept):
     sampled costs and perturbations against the oracle sample by sample, the update against the
