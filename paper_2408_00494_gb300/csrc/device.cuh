@@ -274,15 +274,10 @@ __device__ __forceinline__ float track_curvature(const DevParams& P, const float
     return fmaf(f, k.y, k.x);
 }
 
-// One explicit-Euler substep of one particle (V = float) or of two particles side by side (V =
-// float2, with the packed FP32 instructions of the sm_100 family: fma / mul / add on .f32x2 register
-// pairs, round-to-nearest in each half, so one issued instruction does the operation for both).
-// Every rounding is explicit (fmaf, __fmul_rn, __fadd_rn are never contracted), so each half of a
-// packed pair is bit-identical to the one-particle substep on the same particle. The
-// transcendentals, quotients and the curvature lookup are taken per particle. (sp, cp) =
-// (sin e_psi, cos e_psi) on entry and on exit. Tab: the curvature table's element (float, or float2
-// pairs of value and difference). The force constants are folded into per-step factors
-// (SubstepCtl): v_x' = v_x + h a - h D_f sin(delta)/m g_f + h v_y r, and so on.
+// Arithmetic on one particle's value (float) or two particles' values side by side (float2, the
+// packed FP32 instructions of the sm_100 family: fma / mul / add on .f32x2 register pairs, rounded
+// to nearest in each half). Every rounding is explicit (fmaf, __fmul_rn and __fadd_rn are never
+// contracted), so each half of a packed result equals the one-particle result bit for bit.
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
@@ -360,6 +355,12 @@ __device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp,
     sp = s;
 }
 
+// One explicit-Euler substep of one particle (V = float) or of two particles side by side
+// (V = float2: one issued instruction does each multiply-add for both). The transcendentals,
+// quotients and the curvature lookup are taken per particle. (sp, cp) = (sin e_psi, cos e_psi) on
+// entry and on exit. Tab: the curvature table's element (float, or float2 pairs of value and
+// difference). The force constants are folded into per-step factors (SubstepCtl):
+// v_x' = v_x + h a - h D_f sin(delta)/m g_f + h v_y r, and so on.
 template <typename V, typename Tab>
 __device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
                                                 const SubstepCtl<V>& u, V (&X)[6], V& sp, V& cp)
