@@ -16,14 +16,15 @@ __host__ __device__ constexpr int model_s_index(int model) { return model == 0 ?
 
 // Everything a solve's kernels need, derived on the host at create time and passed by value
 // (kernel parameter space), so several controllers can run concurrently without global state.
-// Constant operands of the bicycle substep: the model's h, -h, l_f, -l_r, B, -B, C, h D_r / m,
-// -h l_r D_r / I_z, then fixed numbers: 1, -1 and the heading-rotation series' 1/24, -1/2, 1/120,
+// Constant operands of the bicycle substep: the model's h, -h, l_f, -l_r, B, -B, C, -D_r / m,
+// -l_r D_r / I_z, then fixed numbers: 1, -1 and the heading-rotation series' 1/24, -1/2, 1/120,
 // -1/6.
-// The wheel-speed model adds R_w, h mu_x F_zf (h D_xf), h D_f, 1/m, h D_xr / m, -h D_r / m, l_f / I_z,
-// h l_r D_r / I_z, -R_w / I_w and -h R_w D_xr / I_w (kFoldW*).
+// The wheel-speed model adds R_w, D_xf = mu_x F_zf, D_f, 1/m, -1/m, D_xr / m, D_r / m, l_f / I_z,
+// l_r D_r / I_z, -h R_w / I_w and -R_w D_xr / I_w (kFoldW*).
 enum : int {
-    kFoldH, kFoldNH, kFoldLf, kFoldNLr, kFoldTB, kFoldNTB, kFoldTC, kFoldHa3, kFoldHb2,
-    kFoldWRw, kFoldWhDxf, kFoldWhDf, kFoldWInvM, kFoldWk3, kFoldWk6, kFoldWLfIz, kFoldWk9, kFoldWk10, kFoldWk11,
+    kFoldH, kFoldNH, kFoldLf, kFoldNLr, kFoldTB, kFoldNTB, kFoldTC, kFoldNDrM, kFoldNLrDrIz,
+    kFoldWRw, kFoldWDxf, kFoldWDf, kFoldWInvM, kFoldWNInvM, kFoldWDxrM, kFoldWDrM, kFoldWLfIz, kFoldWLrDrIz,
+    kFoldWNhRwIw, kFoldWNRwDxrIw,
     kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldN
 };
 
@@ -60,7 +61,7 @@ struct DevParams {
     float Dxf, Dxr, Rw, inv_Iw, tau_max, slip_floor, CB;
     float track_scale;               // n_track / track_len
     float Mf, invM, invM1;           // M, 1/M, 1/(M-1)
-    float hDf_m, hlfDf_Iz;           // h D_f / m and h l_f D_f / I_z (per-step force factors)
+    float Df_m, lfDf_Iz;             // D_f / m and l_f D_f / I_z (per-step force factors)
     // Constant operands of the bicycle substep (kFold* indices), alone and as (v, v) pairs for the
     // packed two-particle form.
     float fold[kFoldN];
@@ -322,11 +323,11 @@ __device__ __forceinline__ float slip_atan(float t)
     return atanf(t);
 }
 
-// Per-step factors (the control is the same for every particle of a sample): steer, h a,
-// -h D_f sin(delta) / m, h D_f cos(delta) / m, h l_f D_f cos(delta) / I_z.
+// Per-step factors (the control is the same for every particle of a sample): steer, a,
+// -D_f sin(delta) / m, -D_f cos(delta) / m, l_f D_f cos(delta) / I_z.
 template <typename V>
 struct SubstepCtl {
-    V steer, hacc, ha1, ha2, hb1;
+    V steer, acc, a1, na2, b1;
 };
 
 template <typename V>
@@ -334,10 +335,10 @@ __device__ __forceinline__ SubstepCtl<V> substep_ctl(const DevParams& P, const C
 {
     SubstepCtl<V> c;
     c.steer = splat<V>(u.steer);
-    c.hacc = splat<V>(__fmul_rn(P.fold[kFoldH], u.accel));
-    c.ha1 = splat<V>(__fmul_rn(-P.hDf_m, u.sin_steer));
-    c.ha2 = splat<V>(__fmul_rn(P.hDf_m, u.cos_steer));
-    c.hb1 = splat<V>(__fmul_rn(P.hlfDf_Iz, u.cos_steer));
+    c.acc = splat<V>(u.accel);
+    c.a1 = splat<V>(__fmul_rn(-P.Df_m, u.sin_steer));
+    c.na2 = splat<V>(__fmul_rn(-P.Df_m, u.cos_steer));
+    c.b1 = splat<V>(__fmul_rn(P.lfDf_Iz, u.cos_steer));
     return c;
 }
 
@@ -359,8 +360,10 @@ __device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp,
 // (V = float2: one issued instruction does each multiply-add for both). The transcendentals,
 // quotients and the curvature lookup are taken per particle. (sp, cp) = (sin e_psi, cos e_psi) on
 // entry and on exit. Tab: the curvature table's element (float, or float2 pairs of value and
-// difference). The force constants are folded into per-step factors (SubstepCtl):
-// v_x' = v_x + h a - h D_f sin(delta)/m g_f + h v_y r, and so on.
+// difference). The force constants are folded into per-step factors (SubstepCtl), and each state's
+// derivative is summed at its own (small) magnitude before one fused multiply-add adds h times it
+// to the state: v_x' = v_x + h (a - D_f sin(delta)/m g_f + v_y r), and so on, with g_f, g_r the
+// tyre curves' values sin(C atan(B alpha)).
 template <typename V, typename Tab>
 __device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
                                                 const SubstepCtl<V>& u, V (&X)[6], V& sp, V& cp)
@@ -387,9 +390,12 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* _
     const V dep = vfma(nk, sdot, r);
     const V dey = vfma(vx, sp, vmul(vy, cp));
     const V h = fold<V>(P, kFoldH);
-    X[0] = vfma(gf, u.ha1, vfma(vmul(vy, r), h, vadd(vx, u.hacc)));
-    X[1] = vfma(gf, u.ha2, vfma(gr, fold<V>(P, kFoldHa3), vfma(vmul(vx, r), fold<V>(P, kFoldNH), vy)));
-    X[2] = vfma(gf, u.hb1, vfma(gr, fold<V>(P, kFoldHb2), r));
+    const V dvx = vfma(gf, u.a1, vfma(vy, r, u.acc));                                            // a - F_f sin / m + v_y r
+    const V ndvy = vfma(vx, r, vfma(gf, u.na2, vmul(gr, fold<V>(P, kFoldNDrM))));             // -v_y' (exact sign flip)
+    const V dr = vfma(gf, u.b1, vmul(gr, fold<V>(P, kFoldNLrDrIz)));                           // (l_f F_f cos - l_r F_r) / I_z
+    X[0] = vfma(h, dvx, vx);
+    X[1] = vfma(fold<V>(P, kFoldNH), ndvy, vy);
+    X[2] = vfma(h, dr, r);
     X[3] = vfma(h, dep, X[3]);
     X[4] = vfma(h, dey, X[4]);
     X[5] = vfma(h, sdot, X[5]);
@@ -417,10 +423,10 @@ __device__ __forceinline__ V tyre_ratio(const DevParams& P, V sl2)
 }
 
 // Per-step factors of the wheel-speed substep: steer, cos delta, sin delta, -sin delta and
-// h tau_max a / I_w.
+// tau_max a / I_w.
 template <typename V>
 struct WheelsCtl {
-    V steer, cs, sn, nsn, hwa;
+    V steer, cs, sn, nsn, taw;
 };
 
 template <typename V>
@@ -431,18 +437,18 @@ __device__ __forceinline__ WheelsCtl<V> wheels_ctl(const DevParams& P, const Con
     c.cs = splat<V>(u.cos_steer);
     c.sn = splat<V>(u.sin_steer);
     c.nsn = splat<V>(-u.sin_steer);
-    c.hwa = splat<V>(__fmul_rn(__fmul_rn(P.h, P.tau_max), __fmul_rn(u.accel, P.inv_Iw)));
+    c.taw = splat<V>(__fmul_rn(P.tau_max, __fmul_rn(u.accel, P.inv_Iw)));
     return c;
 }
 
 // One explicit-Euler substep of the wheel-speed model for one particle (V = float) or two side by
 // side (V = float2), as the bicycle substep: explicit roundings, per-particle transcendentals and
-// quotients, packed multiply-adds. With A = g_f kappa_f, B = g_f alpha_f, C = g_r kappa_r,
-// D = -g_r alpha_r and the front forces' h-scaled rotation into the body frame
-// F_X = h (F_xf cos - F_yf sin), F_Y = h (F_xf sin + F_yf cos):
-//   v_x' = v_x + F_X / m + (h D_xr / m) C + h v_y r,    v_y' = v_y + F_Y / m - (h D_r / m) D - h v_x r,
-//   r' = r + (l_f / I_z) F_Y + (h l_r D_r / I_z) D,      w_F' = w_F - (R_w / I_w) h D_xf A,
-//   w_R' = w_R + h tau_max a / I_w - (h R_w D_xr / I_w) C.
+// quotients, packed multiply-adds, each derivative summed before h times it is added to the state.
+// With F_xf = D_xf g_f kappa_f, F_yf = D_f g_f alpha_f, C = g_r kappa_r, D = -g_r alpha_r and the
+// front forces rotated into the body frame, F_X = F_xf cos - F_yf sin, F_Y = F_xf sin + F_yf cos:
+//   v_x' = v_x + h (F_X / m + (D_xr / m) C + v_y r),   v_y' = v_y + h (F_Y / m - (D_r / m) D - v_x r),
+//   r' = r + h ((l_f / I_z) F_Y + (l_r D_r / I_z) D),   w_F' = w_F - (h R_w / I_w) F_xf,
+//   w_R' = w_R + h (tau_max a / I_w - (R_w D_xr / I_w) C).
 template <typename V, typename Tab>
 __device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
                                                const WheelsCtl<V>& u, V (&X)[8], V& sp, V& cp)
@@ -459,8 +465,8 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __
     const V kr = each(vfma(fold<V>(P, kFoldWRw), wr, vmul(vx, fold<V>(P, kFoldM1))), vx, slip);
     const V gf = tyre_ratio(P, vfma(kf, kf, vmul(af, af)));
     const V gr = tyre_ratio(P, vfma(kr, kr, vmul(nar, nar)));
-    const V G1 = vmul(vmul(gf, kf), fold<V>(P, kFoldWhDxf));                               // h F_xf
-    const V G2 = vmul(vmul(gf, af), fold<V>(P, kFoldWhDf));                                // h F_yf
+    const V G1 = vmul(vmul(gf, kf), fold<V>(P, kFoldWDxf));                                // F_xf
+    const V G2 = vmul(vmul(gf, af), fold<V>(P, kFoldWDf));                                 // F_yf
     const V C = vmul(gr, kr), D = vmul(gr, nar);
     const V FX = vfma(G2, u.nsn, vmul(G1, u.cs));
     const V FY = vfma(G1, u.sn, vmul(G2, u.cs));
@@ -471,11 +477,15 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __
     const V dep = vfma(nk, sdot, r);
     const V dey = vfma(vx, sp, vmul(vy, cp));
     const V h = fold<V>(P, kFoldH);
-    X[0] = vfma(FX, fold<V>(P, kFoldWInvM), vfma(C, fold<V>(P, kFoldWk3), vfma(vmul(vy, r), h, vx)));
-    X[1] = vfma(FY, fold<V>(P, kFoldWInvM), vfma(D, fold<V>(P, kFoldWk6), vfma(vmul(vx, r), fold<V>(P, kFoldNH), vy)));
-    X[2] = vfma(FY, fold<V>(P, kFoldWLfIz), vfma(D, fold<V>(P, kFoldWk9), r));
-    X[3] = vfma(G1, fold<V>(P, kFoldWk10), wf);
-    X[4] = vfma(C, fold<V>(P, kFoldWk11), vadd(wr, u.hwa));
+    const V dvx = vfma(FX, fold<V>(P, kFoldWInvM), vfma(C, fold<V>(P, kFoldWDxrM), vmul(vy, r)));
+    const V ndvy = vfma(vx, r, vfma(FY, fold<V>(P, kFoldWNInvM), vmul(D, fold<V>(P, kFoldWDrM))));  // -v_y'
+    const V dr = vfma(FY, fold<V>(P, kFoldWLfIz), vmul(D, fold<V>(P, kFoldWLrDrIz)));
+    const V dwr = vfma(C, fold<V>(P, kFoldWNRwDxrIw), u.taw);
+    X[0] = vfma(h, dvx, vx);
+    X[1] = vfma(fold<V>(P, kFoldNH), ndvy, vy);
+    X[2] = vfma(h, dr, r);
+    X[3] = vfma(G1, fold<V>(P, kFoldWNhRwIw), wf);
+    X[4] = vfma(h, dwr, wr);
     X[5] = vfma(h, dep, X[5]);
     X[6] = vfma(h, dey, X[6]);
     X[7] = vfma(h, sdot, X[7]);

@@ -281,24 +281,24 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.n_track_mask = ntab - 1;
     d.track_scale = track ? (float)((double)ntab / p->track_len) : 0.0f;
     d.Mf = (float)p->M; d.invM = 1.0f / (float)p->M; d.invM1 = 1.0f / (float)(p->M - 1);
-    d.hDf_m = (float)((double)d.h * d.Df * d.inv_m);
-    d.hlfDf_Iz = (float)((double)d.h * d.lf * d.Df * d.inv_Iz);
+    d.Df_m = (float)((double)d.Df / p->mass);
+    d.lfDf_Iz = (float)((double)p->lf * d.Df / p->Iz);
     d.fold[kFoldH] = d.h; d.fold[kFoldNH] = -d.h; d.fold[kFoldLf] = d.lf; d.fold[kFoldNLr] = -d.lr;
     d.fold[kFoldTB] = d.tB; d.fold[kFoldNTB] = -d.tB; d.fold[kFoldTC] = d.tC;
-    d.fold[kFoldHa3] = (float)((double)d.h * d.Dr * d.inv_m);
-    d.fold[kFoldHb2] = (float)(-(double)d.h * d.lr * d.Dr * d.inv_Iz);
+    d.fold[kFoldNDrM] = (float)(-(double)d.Dr / p->mass);
+    d.fold[kFoldNLrDrIz] = (float)(-(double)p->lr * d.Dr / p->Iz);
     if (p->model == BSSMPPI_MODEL_WHEELS8) {
-        const double h = d.h;
         d.fold[kFoldWRw] = d.Rw;
-        d.fold[kFoldWhDxf] = (float)(h * d.Dxf);
-        d.fold[kFoldWhDf] = (float)(h * d.Df);
+        d.fold[kFoldWDxf] = d.Dxf;
+        d.fold[kFoldWDf] = d.Df;
         d.fold[kFoldWInvM] = d.inv_m;
-        d.fold[kFoldWk3] = (float)(h * d.Dxr / p->mass);
-        d.fold[kFoldWk6] = (float)(-h * d.Dr / p->mass);
+        d.fold[kFoldWNInvM] = -d.inv_m;
+        d.fold[kFoldWDxrM] = (float)((double)d.Dxr / p->mass);
+        d.fold[kFoldWDrM] = (float)((double)d.Dr / p->mass);
         d.fold[kFoldWLfIz] = (float)((double)p->lf / p->Iz);
-        d.fold[kFoldWk9] = (float)(h * p->lr * d.Dr / p->Iz);
-        d.fold[kFoldWk10] = (float)(-(double)p->wheel_radius / p->wheel_inertia);
-        d.fold[kFoldWk11] = (float)(-h * p->wheel_radius * d.Dxr / p->wheel_inertia);
+        d.fold[kFoldWLrDrIz] = (float)((double)p->lr * d.Dr / p->Iz);
+        d.fold[kFoldWNhRwIw] = (float)(-(double)d.h * p->wheel_radius / p->wheel_inertia);
+        d.fold[kFoldWNRwDxrIw] = (float)(-(double)p->wheel_radius * d.Dxr / p->wheel_inertia);
     }
     for (int i = kFoldOne; i < kFoldN; ++i) d.fold[i] = fold_fixed(i);
     for (int i = 0; i < kFoldN; ++i) d.fold2[i] = make_float2(d.fold[i], d.fold[i]);
