@@ -43,7 +43,7 @@ size_t rollout_smem_bytes(const DevParams& dp, int wpb)
 {
     const int ntab = dp.n_track_mask + 1;
     const size_t TN = 2 * (size_t)dp.T;
-    const size_t floats = (size_t)((2 * ntab + 3) & ~3) + TN + (size_t)wpb * dp.spw * TN
+    const size_t floats = (size_t)((2 * ntab + 3) & ~3) + TN + (size_t)wpb * dp.spw * 2 * TN
                         + std::max(TN, (size_t)wpb * kWarp);
     return floats * sizeof(float);
 }

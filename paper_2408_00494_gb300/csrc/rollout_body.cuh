@@ -246,8 +246,10 @@ __host__ __device__ constexpr int roll_max_threads()
 // wheel-speed particles are stepped two at a time with packed FP32 instructions, bit-identical to
 // stepping them one at a time. Their constant operands come from the kernel's parameter space; a caller
 // whose parameters sit in shared memory turns it off, since there the packed operands would take
-// registers of their own.
-template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float, bool PACK = true>
+// registers of their own. UTRIG: my_u holds (u_0, u_1, sin u_0, cos u_0) per step (T x 4), so the
+// steering angle's sine and cosine are taken once per step by the lanes that draw the controls
+// instead of by every lane in every step; otherwise T x 2.
+template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float, bool PACK = true, bool UTRIG = false>
 __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO& io, const Tab* __restrict__ kap_s,
                                                const float* __restrict__ v_s, float* __restrict__ my_u, int group,
                                                uint32_t ctr, const ConSet* cs = nullptr)
@@ -266,6 +268,8 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
 
     // (a1, a2) control noise eps ~ N(0, Sigma_eps) and clamped samples u = clamp(v + eps); the
     // lanes of the segment split the horizon. eps_eff = u - v feeds the update.
+    constexpr bool TRIG = UTRIG && MODEL != 1;
+    constexpr int UPS = UTRIG ? 4 : 2;  // floats of my_u per step
     for (int t = ls; t < dp.T; t += seg) {
         const uint4 w = draw_words(dp, (uint32_t)t, 0u, 0u, kg, kStreamControl, ctr);
         const float2 z = box_muller(w.x, w.y);
@@ -274,8 +278,9 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         const float v0 = v_s[2 * t], v1 = v_s[2 * t + 1];
         const float u0 = fminf(fmaxf(v0 + e0, dp.umin0), dp.umax0);
         const float u1 = fminf(fmaxf(v1 + e1, dp.umin1), dp.umax1);
-        my_u[2 * t] = u0;
-        my_u[2 * t + 1] = u1;
+        my_u[UPS * t] = u0;
+        my_u[UPS * t + 1] = u1;
+        if constexpr (TRIG) sincosf(u0, &my_u[UPS * t + 2], &my_u[UPS * t + 3]);
         if (active) reinterpret_cast<float2*>(io.eps)[(size_t)k * dp.T + t] = make_float2(u0 - v0, u1 - v1);
     }
     __syncwarp();
@@ -349,7 +354,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
     float S_naive = 0.0f;
     for (int t = 0; t < dp.T; ++t) {
         // (a7) S += q(x_bar_t) + ctrl_w v_t^T Sigma_eps^-1 u_t + C_safe(z_t)
-        const float u0 = my_u[2 * t], u1 = my_u[2 * t + 1];
+        const float u0 = my_u[UPS * t], u1 = my_u[UPS * t + 1];
         const float v0 = v_s[2 * t], v1 = v_s[2 * t + 1];
         const float ctrl = dp.ctrl_w * (v0 * fmaf(dp.Si00, u0, dp.Si01 * u1) + v1 * fmaf(dp.Si10, u0, dp.Si11 * u1));
         const float csafe = dp.Csafe * fmaxf(fmaf(dp.one_m_gamma, h_prev, -h_cur), 0.0f);
@@ -367,7 +372,12 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         Control c;
         c.steer = u0;
         c.accel = u1;
-        if constexpr (MODEL != 1) sincosf(u0, &c.sin_steer, &c.cos_steer);
+        if constexpr (TRIG) {
+            c.sin_steer = my_u[UPS * t + 2];
+            c.cos_steer = my_u[UPS * t + 3];
+        } else if constexpr (MODEL != 1) {
+            sincosf(u0, &c.sin_steer, &c.cos_steer);
+        }
         if constexpr (MODEL != 1) {
             // the heading's sine and cosine: series at the step's start, rotated through the
             // substeps. With PACK, particles 2q and 2q + 1 of the lane share packed FP32 registers.

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(roll_max_threads<MODEL, P>()) rollout_kernel(c
     float2* kap_s = reinterpret_cast<float2*>(smem);
     float* v_s = smem + ((2 * ntab + 3) & ~3);
     float* u_s = v_s + TN;
-    float* red = u_s + (size_t)wpb * dp.spw * TN;  // tail scratch: max(TN, threads) floats
+    float* red = u_s + (size_t)wpb * dp.spw * 2 * TN;  // tail scratch: max(TN, threads) floats
 
     if constexpr (MODEL != 1) {
         for (int i = threadIdx.x; i < ntab; i += blockDim.x) {
@@ -308,10 +308,10 @@ __global__ void __launch_bounds__(roll_max_threads<MODEL, P>()) rollout_kernel(c
     const uint32_t ctr = *io.ctr;
     const int warp = threadIdx.x / kWarp;
     const int lane = threadIdx.x & (kWarp - 1);
-    float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * TN;
+    float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * 2 * TN;  // T x (u_0, u_1, sin u_0, cos u_0)
     const int n_groups = (dp.K + dp.spw - 1) / dp.spw;
     for (int group = blockIdx.x * wpb + warp; group < n_groups; group += gridDim.x * wpb)
-        rollout_group<MODEL, P, COMP, FULL>(dp, io, kap_s, v_s, my_u, group, ctr, &cs);
+        rollout_group<MODEL, P, COMP, FULL, float2, true, true>(dp, io, kap_s, v_s, my_u, group, ctr, &cs);
     __syncthreads();
 
     float* part = tail.part + (size_t)blockIdx.x * (3 + TN);
