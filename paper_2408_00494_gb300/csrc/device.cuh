@@ -276,15 +276,13 @@ __device__ __forceinline__ float track_curvature(const DevParams& P, const float
 }
 
 // Arithmetic on one particle's value (float) or two particles' values side by side (float2, the
-// packed FP32 instructions of the sm_100 family: fma / mul / add on .f32x2 register pairs, rounded
-// to nearest in each half). Every rounding is explicit (fmaf, __fmul_rn and __fadd_rn are never
-// contracted), so each half of a packed result equals the one-particle result bit for bit.
+// packed FP32 instructions of the sm_100 family: fma / mul on .f32x2 register pairs, rounded to
+// nearest in each half). Every rounding is explicit (fmaf and __fmul_rn are never contracted), so
+// each half of a packed result equals the one-particle result bit for bit.
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 template <typename F> __device__ __forceinline__ float each(float a, F f) { return f(a); }
 template <typename F> __device__ __forceinline__ float2 each(float2 a, F f) { return make_float2(f(a.x), f(a.y)); }
 template <typename F> __device__ __forceinline__ float each(float a, float b, F f) { return f(a, b); }
