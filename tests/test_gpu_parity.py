@@ -170,8 +170,10 @@ def test_model_step_matches_oracle(model):
     o = oracle.Oracle(p)
     n = 4096
     xs = np.stack([workload.random_state(p, i) for i in range(n)])
-    if model == "bicycle":  # heading errors on both sides of the series/library switch at pi/4
+    if model == "bicycle":  # heading errors on both sides of the series' range |e_psi| <= pi/4, and
+        # several turns away (the fallback's reduction by multiples of 2 pi)
         xs[n // 2:, 3] = np.linspace(-1.5, 1.5, n - n // 2, dtype=np.float32)
+        xs[n // 4: n // 2, 3] = np.linspace(-40.0, 40.0, n // 4, dtype=np.float32)
     us = np.stack([workload.random_nominal(p, i)[0] for i in range(n)]) * 3.0
     us = np.clip(us, p.u_min, p.u_max).astype(np.float32)
     out = torch.zeros((n, p.nx), device="cuda")
