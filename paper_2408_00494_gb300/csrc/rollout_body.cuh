@@ -31,8 +31,9 @@ struct RollIO {
 
 // Moments of the M particles of one sample. x[p] is particle ls + seg p (valid iff < M).
 // mean[i] = particle mean, var[i] = unbiased variance 1/(M-1) sum (x - mean)^2 (Algorithm 2);
-// var is produced for EY only unless all_var. Means outside dp.mean_mask (states no cost term
-// weights) are not merged across lanes and are left lane-local.
+// var is produced for EY only unless all_var. With equal counts on every lane and no recording,
+// all means are merged; otherwise means outside dp.mean_mask (states no cost term weights) are not
+// merged across lanes and are left lane-local.
 template <int NX, int EY, int P, bool COMP>
 __device__ __forceinline__ void belief_moments(const DevParams& dp, const float (&x)[P][NX], int ls, int seg,
                                                bool all_var, float (&mean)[NX], float (&var)[NX])
@@ -66,7 +67,37 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
         }
         // Chan et al. pairwise merge across the segment; the formulas are symmetric in the two
         // partners, so both ends of every exchange compute bit-identical results.
-        if (dp.uniform) {
+        if (dp.uniform && !all_var) {
+            // Equal counts on every lane: merging two halves of n each gives mean = (mean_a +
+            // mean_b) / 2 and M2 = M2_a + M2_b + (mean_b - mean_a)^2 n / 2. The lanes carry the sums
+            // 2^r mean after r merges instead (scaling by a power of two is exact, so every rounding
+            // is the same), which saves a multiply per value and round; all means are merged,
+            // two states per packed add, and M2 for e_y only.
+            float sm[NX];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) sm[i] = mean[i];
+            float m2e = m2[EY], scale = 1.0f;
+            for (int off = seg >> 1; off > 0; off >>= 1) {
+                float sb[NX];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) sb[i] = __shfl_xor_sync(0xffffffffu, sm[i], off);
+                const float d = (sb[EY] - sm[EY]) * scale;
+                const float m2b = __shfl_xor_sync(0xffffffffu, m2e, off);
+                m2e = fmaf(d * d, 0.5f * cnt, m2e + m2b);
+#pragma unroll
+                for (int i = 0; i + 1 < NX; i += 2) {
+                    const float2 a = __fadd2_rn(make_float2(sm[i], sm[i + 1]), make_float2(sb[i], sb[i + 1]));
+                    sm[i] = a.x;
+                    sm[i + 1] = a.y;
+                }
+                if constexpr (NX % 2 == 1) sm[NX - 1] = __fadd_rn(sm[NX - 1], sb[NX - 1]);
+                scale *= 0.5f;
+                cnt *= 2.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < NX; ++i) mean[i] = sm[i] * scale;
+            m2[EY] = m2e;
+        } else if (dp.uniform) {
             for (int off = seg >> 1; off > 0; off >>= 1) {
                 const float half_n = 0.5f * cnt;
 #pragma unroll
