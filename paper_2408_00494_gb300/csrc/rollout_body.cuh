@@ -165,6 +165,25 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
     }
 }
 
+// xor-butterfly sum of N values across the segment, two values per packed add (each half rounds as
+// the scalar add would, so the sums are those of the one-value butterfly).
+template <int N>
+__device__ __forceinline__ void butterfly_sum(float (&v)[N], int seg)
+{
+    for (int off = seg >> 1; off > 0; off >>= 1) {
+        float w[N];
+#pragma unroll
+        for (int e = 0; e < N; ++e) w[e] = __shfl_xor_sync(0xffffffffu, v[e], off);
+#pragma unroll
+        for (int e = 0; e + 1 < N; e += 2) {
+            const float2 a = __fadd2_rn(make_float2(v[e], v[e + 1]), make_float2(w[e], w[e + 1]));
+            v[e] = a.x;
+            v[e + 1] = a.y;
+        }
+        if constexpr (N % 2 == 1) v[N - 1] = __fadd_rn(v[N - 1], w[N - 1]);
+    }
+}
+
 // Full belief of one sample for the re-sampling reading of Algorithm 2: every mean and the unbiased
 // covariance (packed lower triangle by rows), in two passes over the segment: the sums give the
 // means, then the centred products are summed. xor-butterfly sums are symmetric in the two partners,
@@ -180,10 +199,7 @@ __device__ __forceinline__ void belief_moments_full(const DevParams& dp, const f
 #pragma unroll
         for (int p = 0; p < P; ++p) s[i] += (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
     }
-    for (int off = seg >> 1; off > 0; off >>= 1) {
-#pragma unroll
-        for (int i = 0; i < NX; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
-    }
+    butterfly_sum<NX>(s, seg);
 #pragma unroll
     for (int i = 0; i < NX; ++i) mean[i] = s[i] * dp.invM;
 #pragma unroll
@@ -199,10 +215,7 @@ __device__ __forceinline__ void belief_moments_full(const DevParams& dp, const f
             C[i * (i + 1) / 2 + j] = c;
         }
     }
-    for (int off = seg >> 1; off > 0; off >>= 1) {
-#pragma unroll
-        for (int e = 0; e < NX * (NX + 1) / 2; ++e) C[e] += __shfl_xor_sync(0xffffffffu, C[e], off);
-    }
+    butterfly_sum<NX * (NX + 1) / 2>(C, seg);
 #pragma unroll
     for (int e = 0; e < NX * (NX + 1) / 2; ++e) C[e] *= dp.invM1;
 }
