@@ -39,6 +39,9 @@ cudaError_t merge_partials_launch(const DevParams& dp, int G, const float* parts
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of the rollout kernel at wpb warps per block: the curvature table as
+// (value, difference) pairs, the nominal (2T), each segment's controls with the steering angle's
+// sine and cosine (4T per segment) and the tail's scratch.
 size_t rollout_smem_bytes(const DevParams& dp, int wpb)
 {
     const int ntab = dp.n_track_mask + 1;
