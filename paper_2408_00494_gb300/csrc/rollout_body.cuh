@@ -284,10 +284,10 @@ __host__ __device__ constexpr int roll_max_threads()
 // One sample group (the spw samples of one warp): control sequence, rollout, moments, cost.
 // Returns the cost S of the lane's own sample (identical on every lane of its segment); my_u keeps
 // the segment's clamped control sequence u (T x 2, or T x 4 with UTRIG) until the warp's next group.
-// FULL selects the
-// full-belief variant: every mean and the whole covariance each step, which the general constraint
-// set (cs->n > 0, Eq. "DCBFchoice") and the literal reading of Algorithm 2 (dp.resample: particles
-// re-drawn from N(mean, cov) before the next step) need; cs is read only by it. PACK: bicycle and
+// FULL selects the full-belief variant: every mean and the whole covariance each step, which the
+// general constraint set (cs->n > 0, Eq. "DCBFchoice") and the literal reading of Algorithm 2
+// (dp.resample: particles re-drawn from N(mean, cov) before the next step) need; cs is read only by
+// it. PACK: bicycle and
 // wheel-speed particles are stepped two at a time with packed FP32 instructions, bit-identical to
 // stepping them one at a time. Their constant operands come from the kernel's parameter space; a caller
 // whose parameters sit in shared memory turns it off, since there the packed operands would take
