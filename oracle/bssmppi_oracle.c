@@ -165,7 +165,7 @@ static void bicycle_rhs_vjp(const orc_problem* p, const double* x, const double*
     double Dfz = p->mu * m * p->g * lr / (lf + lr);
     double Drz = p->mu * m * p->g * lf / (lf + lr);
     double tf = atan(B * alpha_f), tr = atan(B * alpha_r);
-    double Fyf = Dfz * sin(C * tf), Fyr = Drz * sin(C * tr);
+    double Fyf = Dfz * sin(C * tf);  /* the rear force enters the adjoint only through dFr */
     double dFf = Dfz * cos(C * tf) * C * B / (1.0 + B * alpha_f * B * alpha_f);
     double dFr = Drz * cos(C * tr) * C * B / (1.0 + B * alpha_r * B * alpha_r);
     double kap = orc_track_kappa(p, s), dkap = track_dkappa_ds(p, s);

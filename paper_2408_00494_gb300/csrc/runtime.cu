@@ -532,7 +532,7 @@ int bssmppi_solve_partial(bssmppi_t h, const float* d_x0, const float* d_Sigma0,
     if (!d_x0 || !d_partial) return fail(h, BSSMPPI_EINVAL, "x0 and partial must be non-NULL");
     const size_t vbytes = sizeof(float) * 2 * h->prm.T;
     if (d_v) BSS_CUDA(h, cudaMemcpyAsync(h->d_v, d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));
-    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, nullptr, nullptr, h->d_ctr, h->d_v, d_partial};
+    bss::TailIO tail{h->d_tail_part, h->d_ticket, h->d_w, nullptr, nullptr, h->d_ctr, h->d_v, d_partial, 0};
     BSS_CUDA(h, bss::rollout_launch(h->dp, h->P, h->prm.compensated != 0, h->roll, d_x0, d_Sigma0, h->d_v, h->d_ctr,
                                     h->d_S, h->d_eps, h->d_mean, h->d_var, tail, h->cons, h->stream));
     return BSSMPPI_OK;
@@ -543,7 +543,7 @@ int bssmppi_merge_partials(bssmppi_t h, const float* d_partials, int32_t G, floa
     if (!h) return fail(nullptr, BSSMPPI_EINVAL, "handle is NULL");
     if (!d_partials) return fail(h, BSSMPPI_EINVAL, "partials are NULL");
     if (G < 1 || G > bss::kTailMaxBlocks) return fail(h, BSSMPPI_EINVAL, "G must be in [1, 256]");
-    bss::TailIO tail{nullptr, nullptr, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, nullptr, h->d_v, nullptr};
+    bss::TailIO tail{nullptr, nullptr, h->d_w, d_u0 ? d_u0 : h->d_u0, h->d_diag, nullptr, h->d_v, nullptr, 0};
     BSS_CUDA(h, bss::merge_partials_launch(h->dp, G, d_partials, h->prm.compensated != 0, h->d_S, tail, h->stream));
     const size_t vbytes = sizeof(float) * 2 * h->prm.T;
     if (d_v) BSS_CUDA(h, cudaMemcpyAsync(d_v, h->d_v, vbytes, cudaMemcpyDeviceToDevice, h->stream));

@@ -305,7 +305,7 @@ cudaError_t issue_batch(bssmppi_server* s, Slot& sl)
 }
 
 // Fill the slot's descriptors from its admitted requests (sorted by particle class).
-void fill_descriptors(bssmppi_server* s, Slot& sl)
+void fill_descriptors(Slot& sl)
 {
     std::stable_sort(sl.batch.begin(), sl.batch.end(),
                      [](const Pending& a, const Pending& b) { return class_of(a.M) < class_of(b.M); });
@@ -419,7 +419,7 @@ void worker_loop(bssmppi_server* s)
         for (int i = 0; i < s->n_slots && !s->stop.load(); ++i) {
             Slot& sl = s->slots[i];
             if (sl.busy || !form_batch(s, sl)) continue;
-            fill_descriptors(s, sl);
+            fill_descriptors(sl);
             sl.t_launch = now_us(s->t0);
             cudaError_t e = s->cfg.use_graphs ? cudaGraphLaunch(sl.exec, sl.s[0]) : issue_batch(s, sl);
             if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.s[0]);
