@@ -255,6 +255,39 @@ def test_curvature_table_sizes(n_track, M, T):
     check_solve(p, workload.random_state(p, 3), workload.random_nominal(p, 3), ctr=2)
 
 
+@pytest.mark.parametrize("case", ["no_disturbance", "small_lambda", "large_lambda", "gamma_near_0",
+                                  "gamma_near_1", "delta_near_half", "delta_small"])
+def test_solve_degenerate_settings(case):
+    """The method's limiting settings against the oracle: no disturbance (every particle identical,
+    so the belief collapses to a point: zero variance, and the barrier is the deterministic one),
+    lambda -> 0 (the weights pick the best sample) and large (near-uniform weights), gamma at both
+    ends of (0, 1), and chance levels delta near 1/2 (nu -> 0, no back-off) and small (large nu)."""
+    p = workload.config0()
+    if case == "no_disturbance":
+        p.Sigma_w = np.zeros_like(np.asarray(p.Sigma_w))
+    elif case == "small_lambda":
+        p.lam = 1e-3
+    elif case == "large_lambda":
+        p.lam = 1e4
+    elif case == "gamma_near_0":
+        p.gamma = 1e-3
+    elif case == "gamma_near_1":
+        p.gamma = 0.999
+    elif case == "delta_near_half":
+        p.delta = 0.499
+    elif case == "delta_small":
+        p.delta = 1e-4
+    x0, v = workload.random_state(p, 31), workload.random_nominal(p, 31)
+    g, ref = check_solve(p, x0, v, ctr=5)
+    if case == "no_disturbance":
+        assert np.all(g["var"] == 0.0)
+    w = g["w"] / g["w"].sum()
+    if case == "small_lambda":
+        assert w[np.argmin(g["S"])] >= 0.999
+    if case == "large_lambda":
+        assert 1.0 / np.sum(w * w) > 0.5 * p.K  # effective sample size near K
+
+
 def test_solve_ragged_K_and_long_horizon():
     p = workload.config1()
     p.K, p.M, p.T = 1001, 64, 40
