@@ -54,13 +54,23 @@ class OrcOutputs(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (strict IEEE double: no contraction, no fast-math)."""
+    """Compile the oracle with gcc (strict IEEE double: no contraction, no fast-math), with OpenMP
+    for the optional threads over samples when the compiler has it (one thread otherwise)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-               "-o", _LIB_PATH, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+                "-o", _LIB_PATH, _SRC, "-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.run(base, check=True)
     return _LIB_PATH
+
+
+def host_threads() -> int:
+    """Threads the oracle may use on this host: the CPUs this process may run on."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
 
 
 _lib = None
@@ -90,6 +100,10 @@ def lib():
         L.orc_lse_merge.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
         L.orc_solve.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, _dp, ctypes.c_uint32,
                                 ctypes.POINTER(OrcOutputs)]
+        L.orc_rollout_threads.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, _dp, ctypes.c_uint32,
+                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrcOutputs), ctypes.c_int]
+        L.orc_solve_threads.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, _dp, ctypes.c_uint32,
+                                        ctypes.POINTER(OrcOutputs), ctypes.c_int]
         L.orc_repair_objective.restype = ctypes.c_double
         L.orc_repair_objective.argtypes = [ctypes.POINTER(OrcProblem), _dp, _dp, ctypes.c_uint32, _dp, _dp]
         _lib = L
@@ -157,8 +171,9 @@ class Oracle:
         self.p = p
         self.nx = nx
 
-    def solve(self, x0, v, ctr, Sigma0=None, want_cov=False, k_range=None):
-        """Full solve (or rollout of samples k_range=(k0, k1) only). Returns a dict of arrays."""
+    def solve(self, x0, v, ctr, Sigma0=None, want_cov=False, k_range=None, threads=1):
+        """Full solve (or rollout of samples k_range=(k0, k1) only). Returns a dict of arrays.
+        threads > 1 spreads whole samples over OpenMP threads (the same results bit for bit)."""
         K, T, nx = self.prob.K, self.prob.T, self.nx
         x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float32), dtype=np.float64)
         v = np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(T, 2), dtype=np.float64)
@@ -174,11 +189,11 @@ class Oracle:
             r["cov"] = np.zeros((K, T + 1, nx, nx))
         o = OrcOutputs(*[_ptr(r.get(name)) for name, _ in OrcOutputs._fields_])
         if k_range is None:
-            rc = lib().orc_solve(ctypes.byref(self.p), _ptr(x0), _ptr(S0), _ptr(v), ctypes.c_uint32(ctr),
-                                 ctypes.byref(o))
+            rc = lib().orc_solve_threads(ctypes.byref(self.p), _ptr(x0), _ptr(S0), _ptr(v), ctypes.c_uint32(ctr),
+                                         ctypes.byref(o), int(threads))
         else:
-            rc = lib().orc_rollout(ctypes.byref(self.p), _ptr(x0), _ptr(S0), _ptr(v), ctypes.c_uint32(ctr),
-                                   int(k_range[0]), int(k_range[1]), ctypes.byref(o))
+            rc = lib().orc_rollout_threads(ctypes.byref(self.p), _ptr(x0), _ptr(S0), _ptr(v), ctypes.c_uint32(ctr),
+                                           int(k_range[0]), int(k_range[1]), ctypes.byref(o), int(threads))
         if rc != 0:
             raise ValueError("oracle rejected the problem")
         r["eps"] = r["u"] - v[None]
@@ -196,6 +211,8 @@ class Oracle:
 
     def repair_objective(self, x0, v, ctr, grad=True, want_args=False):
         """J_r(v) and (optionally) its gradient dJ/dv [T, 2] and the hinge arguments [T + 1]."""
+        if self.prob.model == 2:
+            raise ValueError("the repair objective has no adjoint for the wheel-speed model")
         T = self.prob.T
         x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float64))
         v = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(T, 2))

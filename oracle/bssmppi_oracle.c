@@ -428,8 +428,8 @@ static double c_safe(const orc_problem* p, double h_now, double h_prev)
 
 static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
-                uint32_t solve_ctr, int k_begin, int k_end, const orc_outputs* out)
+int orc_rollout_threads(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
+                        uint32_t solve_ctr, int k_begin, int k_end, const orc_outputs* out, int n_threads)
 {
     const int nx = orc_nx(p), M = p->M, T = p->T;
     if (M < 2 || T < 1 || k_begin < 0 || k_end > p->K || k_begin > k_end) return -1;
@@ -442,114 +442,127 @@ int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, co
     Sinv[2] = -p->Sigma_eps[2] / det; Sinv[3] = p->Sigma_eps[0] / det;
     const double nu = orc_backoff_gaussian(p->delta);
 
-    double* X = (double*)malloc(sizeof(double) * (size_t)M * nx);      /* particles x^n_k */
-    double* xbar = (double*)malloc(sizeof(double) * (size_t)(T + 1) * nx);
-    double* Sig = (double*)malloc(sizeof(double) * (size_t)(T + 1) * nx * nx);
-    double* hz = (double*)malloc(sizeof(double) * (size_t)(T + 1));
-    double* u = (double*)malloc(sizeof(double) * (size_t)T * 2);
+    /* The samples are independent until the weights (Algorithm 1 rolls each one out on its own),
+     * so with n_threads > 1 (and an OpenMP build) threads take whole samples; every sample's
+     * arithmetic is the same as with one thread. */
+#pragma omp parallel num_threads(n_threads > 1 ? n_threads : 1)
+    {
+        double* X = (double*)malloc(sizeof(double) * (size_t)M * nx);      /* particles x^n_k */
+        double* xbar = (double*)malloc(sizeof(double) * (size_t)(T + 1) * nx);
+        double* Sig = (double*)malloc(sizeof(double) * (size_t)(T + 1) * nx * nx);
+        double* hz = (double*)malloc(sizeof(double) * (size_t)(T + 1));
+        double* u = (double*)malloc(sizeof(double) * (size_t)T * 2);
 
-    for (int m = k_begin; m < k_end; ++m) {
-        /* Algorithm 1: initialise the belief state z_0 = (z_0, z_{-1} = z_0) from the estimate. */
-        memcpy(xbar, x0, sizeof(double) * nx);
-        for (int i = 0; i < nx * nx; ++i) Sig[i] = Sigma0 ? Sigma0[i] : 0.0;
-        uint32_t kk = p->crn_disturbance ? 0u : (uint32_t)m;
-        for (int n = 0; n < M; ++n) {
-            for (int i = 0; i < nx; ++i) X[n * nx + i] = x0[i];
-            if (Sigma0) {
-                double xi[8];
-                draw_normals(p, nx, 0, (uint32_t)n, kk, 3, solve_ctr, xi);
-                for (int i = 0; i < nx; ++i)
-                    for (int j = 0; j <= i; ++j) X[n * nx + i] += L_0[i * nx + j] * xi[j];
-            }
-        }
-        /* Sample the control perturbation sequence eps^m ~ N(0, Sigma_eps). */
-        for (int k = 0; k < T; ++k) {
-            double z[2];
-            draw_normals(p, 2, (uint32_t)k, 0, (uint32_t)m, 0, solve_ctr, z);
-            double e0 = L_eps[0] * z[0];
-            double e1 = L_eps[2] * z[0] + L_eps[3] * z[1];
-            u[2 * k + 0] = clampd(v[2 * k + 0] + e0, p->u_min[0], p->u_max[0]);
-            u[2 * k + 1] = clampd(v[2 * k + 1] + e1, p->u_min[1], p->u_max[1]);
-        }
-        /* Roll out: Algorithm 2 propagates the particles, then the augmented cost accumulates. */
-        hz[0] = p->n_con ? general_h(p, xbar, Sig, nx) : belief_h(p, nu, xbar, Sig, nx);
-        double S = 0.0;
-        for (int k = 0; k < T; ++k) {
-            const double* uk = u + 2 * k;
-            if (p->resample && k > 0) {
-                /* Algorithm 2's sampling of the particles, x^n_k ~ N(xbar_k, Sigma_k), drawn as
-                 * xbar_k + L_k xi^n with L_k the (PSD) Cholesky factor of the Monte-Carlo covariance
-                 * of step k and xi^n from stream 4. At k = 0 the initial particles above are the draw. */
-                double Lk[64];
-                cholesky_psd(nx, Sig + (size_t)k * nx * nx, Lk);
-                const double* mk = xbar + (size_t)k * nx;
-                for (int n = 0; n < M; ++n) {
-                    double xi[8];
-                    draw_normals(p, nx, (uint32_t)k, (uint32_t)n, kk, 4, solve_ctr, xi);
-                    for (int i = 0; i < nx; ++i) {
-                        double x = mk[i];
-                        for (int j = 0; j <= i; ++j) x += Lk[i * nx + j] * xi[j];
-                        X[n * nx + i] = x;
-                    }
-                }
-            }
+#pragma omp for schedule(dynamic, 4)
+        for (int m = k_begin; m < k_end; ++m) {
+            /* Algorithm 1: initialise the belief state z_0 = (z_0, z_{-1} = z_0) from the estimate. */
+            memcpy(xbar, x0, sizeof(double) * nx);
+            for (int i = 0; i < nx * nx; ++i) Sig[i] = Sigma0 ? Sigma0[i] : 0.0;
+            uint32_t kk = p->crn_disturbance ? 0u : (uint32_t)m;
             for (int n = 0; n < M; ++n) {
-                double xn[8], w[8], z[8];
-                orc_model_step(p, X + n * nx, uk, xn);
-                draw_disturbance(p, nx, (uint32_t)k, (uint32_t)n, kk, solve_ctr, z);
-                for (int i = 0; i < nx; ++i) {
-                    w[i] = 0.0;
-                    for (int j = 0; j <= i; ++j) w[i] += L_w[i * nx + j] * z[j];
+                for (int i = 0; i < nx; ++i) X[n * nx + i] = x0[i];
+                if (Sigma0) {
+                    double xi[8];
+                    draw_normals(p, nx, 0, (uint32_t)n, kk, 3, solve_ctr, xi);
+                    for (int i = 0; i < nx; ++i)
+                        for (int j = 0; j <= i; ++j) X[n * nx + i] += L_0[i * nx + j] * xi[j];
                 }
-                for (int i = 0; i < nx; ++i) X[n * nx + i] = xn[i] + w[i];
             }
-            double* mk = xbar + (size_t)(k + 1) * nx;
-            double* Sk = Sig + (size_t)(k + 1) * nx * nx;
-            for (int i = 0; i < nx; ++i) {
-                double s = 0.0;
-                for (int n = 0; n < M; ++n) s += X[n * nx + i];
-                mk[i] = s / M;
+            /* Sample the control perturbation sequence eps^m ~ N(0, Sigma_eps). */
+            for (int k = 0; k < T; ++k) {
+                double z[2];
+                draw_normals(p, 2, (uint32_t)k, 0, (uint32_t)m, 0, solve_ctr, z);
+                double e0 = L_eps[0] * z[0];
+                double e1 = L_eps[2] * z[0] + L_eps[3] * z[1];
+                u[2 * k + 0] = clampd(v[2 * k + 0] + e0, p->u_min[0], p->u_max[0]);
+                u[2 * k + 1] = clampd(v[2 * k + 1] + e1, p->u_min[1], p->u_max[1]);
             }
-            for (int i = 0; i < nx; ++i)
-                for (int j = 0; j < nx; ++j) {
-                    double s = 0.0;
-                    for (int n = 0; n < M; ++n) s += (X[n * nx + i] - mk[i]) * (X[n * nx + j] - mk[j]);
-                    Sk[i * nx + j] = s / (M - 1);
-                }
-            hz[k + 1] = p->n_con ? general_h(p, mk, Sk, nx) : belief_h(p, nu, mk, Sk, nx);
-            /* S += q(xbar_k) + ctrl_w v_k^T Sigma_eps^-1 u_k + C_safe(z_k), with h_{-1} = h_0. */
-            double vSu = v[2 * k] * (Sinv[0] * uk[0] + Sinv[1] * uk[1])
-                       + v[2 * k + 1] * (Sinv[2] * uk[0] + Sinv[3] * uk[1]);
-            double h_prev = (k == 0) ? hz[0] : hz[k - 1];
-            S += state_cost(p, p->Q, xbar + (size_t)k * nx, nx) + p->ctrl_w * vSu + c_safe(p, hz[k], h_prev);
-        }
-        /* Terminal: phi(xbar_T) + C_safe(z_T). */
-        S += state_cost(p, p->Qf, xbar + (size_t)T * nx, nx) + c_safe(p, hz[T], hz[T > 0 ? T - 1 : 0]);
-
-        if (out->S) out->S[m] = S;
-        if (out->u) memcpy(out->u + (size_t)m * T * 2, u, sizeof(double) * T * 2);
-        if (out->mean) memcpy(out->mean + (size_t)m * (T + 1) * nx, xbar, sizeof(double) * (T + 1) * nx);
-        if (out->cov) memcpy(out->cov + (size_t)m * (T + 1) * nx * nx, Sig, sizeof(double) * (T + 1) * nx * nx);
-        if (out->h) memcpy(out->h + (size_t)m * (T + 1), hz, sizeof(double) * (T + 1));
-        if (out->margin) {
-            double mg = INFINITY;
-            for (int k = 0; k <= T; ++k) {
-                if (p->n_con == 0) {
-                    double d = fabs(fabs(xbar[(size_t)k * nx + p->ey_index]) - p->w_T);
-                    if (d < mg) mg = d;
-                } else {
-                    for (int q = 0; q < p->n_con; ++q) {
-                        double eta[8];
-                        double d = fabs(constraint_value(p->con + q, xbar + (size_t)k * nx, nx, eta));
-                        if (d < mg) mg = d;
+            /* Roll out: Algorithm 2 propagates the particles, then the augmented cost accumulates. */
+            hz[0] = p->n_con ? general_h(p, xbar, Sig, nx) : belief_h(p, nu, xbar, Sig, nx);
+            double S = 0.0;
+            for (int k = 0; k < T; ++k) {
+                const double* uk = u + 2 * k;
+                if (p->resample && k > 0) {
+                    /* Algorithm 2's sampling of the particles, x^n_k ~ N(xbar_k, Sigma_k), drawn as
+                     * xbar_k + L_k xi^n with L_k the (PSD) Cholesky factor of the Monte-Carlo covariance
+                     * of step k and xi^n from stream 4. At k = 0 the initial particles above are the draw. */
+                    double Lk[64];
+                    cholesky_psd(nx, Sig + (size_t)k * nx * nx, Lk);
+                    const double* mk = xbar + (size_t)k * nx;
+                    for (int n = 0; n < M; ++n) {
+                        double xi[8];
+                        draw_normals(p, nx, (uint32_t)k, (uint32_t)n, kk, 4, solve_ctr, xi);
+                        for (int i = 0; i < nx; ++i) {
+                            double x = mk[i];
+                            for (int j = 0; j <= i; ++j) x += Lk[i * nx + j] * xi[j];
+                            X[n * nx + i] = x;
+                        }
                     }
                 }
+                for (int n = 0; n < M; ++n) {
+                    double xn[8], w[8], z[8];
+                    orc_model_step(p, X + n * nx, uk, xn);
+                    draw_disturbance(p, nx, (uint32_t)k, (uint32_t)n, kk, solve_ctr, z);
+                    for (int i = 0; i < nx; ++i) {
+                        w[i] = 0.0;
+                        for (int j = 0; j <= i; ++j) w[i] += L_w[i * nx + j] * z[j];
+                    }
+                    for (int i = 0; i < nx; ++i) X[n * nx + i] = xn[i] + w[i];
+                }
+                double* mk = xbar + (size_t)(k + 1) * nx;
+                double* Sk = Sig + (size_t)(k + 1) * nx * nx;
+                for (int i = 0; i < nx; ++i) {
+                    double s = 0.0;
+                    for (int n = 0; n < M; ++n) s += X[n * nx + i];
+                    mk[i] = s / M;
+                }
+                for (int i = 0; i < nx; ++i)
+                    for (int j = 0; j < nx; ++j) {
+                        double s = 0.0;
+                        for (int n = 0; n < M; ++n) s += (X[n * nx + i] - mk[i]) * (X[n * nx + j] - mk[j]);
+                        Sk[i * nx + j] = s / (M - 1);
+                    }
+                hz[k + 1] = p->n_con ? general_h(p, mk, Sk, nx) : belief_h(p, nu, mk, Sk, nx);
+                /* S += q(xbar_k) + ctrl_w v_k^T Sigma_eps^-1 u_k + C_safe(z_k), with h_{-1} = h_0. */
+                double vSu = v[2 * k] * (Sinv[0] * uk[0] + Sinv[1] * uk[1])
+                           + v[2 * k + 1] * (Sinv[2] * uk[0] + Sinv[3] * uk[1]);
+                double h_prev = (k == 0) ? hz[0] : hz[k - 1];
+                S += state_cost(p, p->Q, xbar + (size_t)k * nx, nx) + p->ctrl_w * vSu + c_safe(p, hz[k], h_prev);
             }
-            out->margin[m] = mg;
+            /* Terminal: phi(xbar_T) + C_safe(z_T). */
+            S += state_cost(p, p->Qf, xbar + (size_t)T * nx, nx) + c_safe(p, hz[T], hz[T > 0 ? T - 1 : 0]);
+
+            if (out->S) out->S[m] = S;
+            if (out->u) memcpy(out->u + (size_t)m * T * 2, u, sizeof(double) * T * 2);
+            if (out->mean) memcpy(out->mean + (size_t)m * (T + 1) * nx, xbar, sizeof(double) * (T + 1) * nx);
+            if (out->cov) memcpy(out->cov + (size_t)m * (T + 1) * nx * nx, Sig, sizeof(double) * (T + 1) * nx * nx);
+            if (out->h) memcpy(out->h + (size_t)m * (T + 1), hz, sizeof(double) * (T + 1));
+            if (out->margin) {
+                double mg = INFINITY;
+                for (int k = 0; k <= T; ++k) {
+                    if (p->n_con == 0) {
+                        double d = fabs(fabs(xbar[(size_t)k * nx + p->ey_index]) - p->w_T);
+                        if (d < mg) mg = d;
+                    } else {
+                        for (int q = 0; q < p->n_con; ++q) {
+                            double eta[8];
+                            double d = fabs(constraint_value(p->con + q, xbar + (size_t)k * nx, nx, eta));
+                            if (d < mg) mg = d;
+                        }
+                    }
+                }
+                out->margin[m] = mg;
+            }
         }
+        free(X); free(xbar); free(Sig); free(hz); free(u);
     }
-    free(X); free(xbar); free(Sig); free(hz); free(u);
     return 0;
+}
+
+int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
+                uint32_t solve_ctr, int k_begin, int k_end, const orc_outputs* out)
+{
+    return orc_rollout_threads(p, x0, Sigma0, v, solve_ctr, k_begin, k_end, out, 1);
 }
 
 /* Eq. "Weights" and Eq. "MPPI update law": beta = min S, w = exp(-(S - beta)/lambda),
@@ -618,18 +631,24 @@ void orc_lse_merge(int G, int T, double lambda, int K_total, const double* parts
     if (diag) { diag[0] = beta; diag[1] = eta; diag[2] = eta * eta / q; diag[3] = beta - lambda * log(eta / K_total); }
 }
 
-int orc_solve(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
-              uint32_t solve_ctr, const orc_outputs* out)
+int orc_solve_threads(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
+                      uint32_t solve_ctr, const orc_outputs* out, int n_threads)
 {
     orc_outputs o = *out;
     double* S = o.S ? o.S : (double*)malloc(sizeof(double) * (size_t)p->K);
     double* u = o.u ? o.u : (double*)malloc(sizeof(double) * (size_t)p->K * p->T * 2);
     o.S = S; o.u = u;
-    int rc = orc_rollout(p, x0, Sigma0, v, solve_ctr, 0, p->K, &o);
+    int rc = orc_rollout_threads(p, x0, Sigma0, v, solve_ctr, 0, p->K, &o, n_threads);
     if (rc == 0) orc_optimal_control(p->K, p->T, p->lambda, S, u, o.w, o.v_plus, o.diag);
     if (!out->S) free(S);
     if (!out->u) free(u);
     return rc;
+}
+
+int orc_solve(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
+              uint32_t solve_ctr, const orc_outputs* out)
+{
+    return orc_solve_threads(p, x0, Sigma0, v, solve_ctr, out, 1);
 }
 
 void orc_shift(int T, double* v)
@@ -645,7 +664,9 @@ double orc_repair_objective(const orc_problem* p, const double* x0, const double
                             uint32_t solve_ctr, double* grad, double* args_out)
 {
     const int nx = orc_nx(p), M = p->M, T = p->T, e = p->ey_index;
-    double L_w[36];
+    /* The adjoint covers the bicycle and the double integrator only (model_step_vjp). */
+    if (p->model == 2 || M < 2 || T < 1) return NAN;
+    double L_w[64];
     cholesky_psd(nx, p->Sigma_w, L_w);
     const double nu = orc_backoff_gaussian(p->delta);
     double* X = (double*)malloc(sizeof(double) * (size_t)(T + 1) * M * nx);
@@ -660,7 +681,7 @@ double orc_repair_objective(const orc_problem* p, const double* x0, const double
     hz[0] = (p->w_T) * (p->w_T) - x0[e] * x0[e];
     for (int t = 0; t < T; ++t) {
         for (int n = 0; n < M; ++n) {
-            double xn[6], z[6];
+            double xn[8], z[8];
             const double* xc = X + ((size_t)t * M + n) * nx;
             double* xo = X + ((size_t)(t + 1) * M + n) * nx;
             orc_model_step(p, xc, v + 2 * t, xn);
@@ -708,7 +729,7 @@ double orc_repair_objective(const orc_problem* p, const double* x0, const double
                 }
             }
             for (int n = 0; n < M; ++n) {
-                double gx[6] = {0, 0, 0, 0, 0, 0};
+                double gx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                 model_step_vjp(p, X + ((size_t)(t - 1) * M + n) * nx, v + 2 * (t - 1),
                                G + (size_t)n * nx, gx, grad + 2 * (t - 1));
                 memcpy(G + (size_t)n * nx, gx, sizeof(double) * nx);

@@ -2,7 +2,8 @@
  * FP64 reference oracle for the BSS-MPPI solve (Yin, Tsiotras, Berntorp, "Chance-Constrained
  * Information-Theoretic Stochastic Model Predictive Control with Safety Shielding").
  *
- * TEST INFRASTRUCTURE ONLY. This plain, slow, single-threaded C code exists to check the CUDA
+ * TEST INFRASTRUCTURE ONLY. This plain, slow C code (single-threaded unless a caller asks for
+ * OpenMP threads over the samples) exists to check the CUDA
  * path. Only the test suite, the smoke check and the benchmark's CPU-baseline leg may load it. It
  * shares no code, header, constant or helper with the CUDA library; the two receive the same
  * seeded inputs and nothing else.
@@ -81,6 +82,10 @@ void orc_model_step(const orc_problem* p, const double* x, const double* u, doub
 /* Rollout and cost of samples [k_begin, k_end) (Algorithm 1's inner loop with Algorithm 2). */
 int orc_rollout(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
                 uint32_t solve_ctr, int k_begin, int k_end, const orc_outputs* out);
+/* The same with the samples spread over n_threads OpenMP threads (whole samples per thread, so
+ * every output is the one-thread result bit for bit; one thread when built without OpenMP). */
+int orc_rollout_threads(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
+                        uint32_t solve_ctr, int k_begin, int k_end, const orc_outputs* out, int n_threads);
 /* OptimalControl: weights and v+ = sum w u / sum w from costs S[K] and clamped samples u. */
 void orc_optimal_control(int K, int T, double lambda, const double* S, const double* u,
                          double* w, double* v_plus, double* diag);
@@ -92,15 +97,19 @@ void orc_lse_merge(int G, int T, double lambda, int K_total, const double* parts
 /* Full solve = orc_rollout over all samples + orc_optimal_control. Returns 0 or -1 (bad args). */
 int orc_solve(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
               uint32_t solve_ctr, const orc_outputs* out);
+int orc_solve_threads(const orc_problem* p, const double* x0, const double* Sigma0, const double* v,
+                      uint32_t solve_ctr, const orc_outputs* out, int n_threads);
 /* Warm start with a one-step shift: v[t] <- v[t+1], last element repeated. */
 void orc_shift(int T, double* v);
 
 /* Shield repair objective J_r(v) = sum_{t=1..T} C_safe,t of the M-particle rollout of the
  * nominal sequence v (no control noise, disturbance draws of sample 0) and its gradient dJ/dv
  * by a reverse sweep (adjoint). grad [T*2] and args_out [T+1] (the hinge arguments
- * -h_t + (1 - gamma) h_{t-1}, entry 0 unused) may be NULL. Returns J.
- * Parity unpinned with respect to the paper: the paper leaves the repair step undefined, so this
- * objective is a reading of it; the gradient is pinned by central finite differences of J_r. */
+ * -h_t + (1 - gamma) h_{t-1}, entry 0 unused) may be NULL. Returns J, or NaN for the wheel-speed
+ * model (model 2, which has no adjoint here), M < 2 or T < 1.
+ * The paper leaves the repair step undefined, so this objective is a reading of it. Its value is
+ * pinned to the barrier penalty that orc_rollout's own h gives for the same nominal (no control
+ * noise, common random numbers); its gradient by central finite differences of J_r. */
 double orc_repair_objective(const orc_problem* p, const double* x0, const double* v,
                             uint32_t solve_ctr, double* grad, double* args_out);
 

@@ -5,6 +5,7 @@ moment propagation, a constant-barrier cost), a limit of the update law (lambda 
 an unbiasedness property, the literal brute-force restatement in tests/literal_bssmppi.py, or
 central finite differences.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -233,6 +234,52 @@ def test_repair_adjoint_matches_central_differences(model):
         fd = (o.repair_objective(x0, v + eps * e, 3, grad=False)
               - o.repair_objective(x0, v - eps * e, 3, grad=False)) / (2 * eps)
         assert g[t, j] == pytest.approx(fd, rel=2e-5, abs=1e-6 * abs(J))
+
+
+@pytest.mark.parametrize("model", ["racing", "double_integrator"])
+def test_repair_objective_equals_the_rollouts_barrier_penalty(model):
+    """The value of J_r: the belief-DCBF penalty sum_{t=1..T} C max(-h_t + (1 - gamma) h_{t-1}, 0)
+    (Eq. "cbfpenalty") of the M-particle rollout of the nominal v under sample 0's disturbance
+    draws. The solve's rollout (whose moments, barrier and costs the other tests pin) forms the same
+    barrier values h_t (Eq. "DCBF") when the control noise is zero and every sample shares sample 0's
+    draws, so J_r and its hinge arguments must equal that sum built from the rollout's own h. A 1/M
+    variance, a shifted h_0 or draws taken from another sample in the repair's separate rollout
+    each break it."""
+    p, x0, v = _repair_case(model)
+    o_rep = oracle.Oracle(p)
+    J, args = o_rep.repair_objective(x0, v, ctr=3, grad=False, want_args=True)
+    q = dataclasses.replace(p, K=2, crn_disturbance=1, Sigma_eps=np.zeros((2, 2)))
+    h = oracle.Oracle(q).solve(x0, v, 3, k_range=(1, 2))["h"][1]
+    C, gam = float(np.float32(p.C_safe)), float(np.float32(p.gamma))
+    arg_ref = -h[1:] + (1.0 - gam) * h[:-1]
+    np.testing.assert_allclose(args[1:], arg_ref, rtol=1e-12, atol=1e-12 * np.abs(h).max())
+    J_ref = float(np.sum(C * np.maximum(arg_ref, 0.0)))
+    assert J_ref > 0.0  # the hinge is active in these cases
+    assert J == pytest.approx(J_ref, rel=1e-12)
+
+
+@pytest.mark.parametrize("case", ["racing", "resample", "sigma0"])
+def test_threaded_oracle_equals_one_thread(case):
+    """Samples spread over threads give every output of the one-thread solve bit for bit."""
+    p = workload.config0()
+    p.K, p.T = 67, 8
+    Sig0 = None
+    if case == "resample":
+        p.resample = 1
+    if case == "sigma0":
+        Sig0 = np.eye(6) * 1e-3
+    x0, v = workload.random_state(p, 4), workload.random_nominal(p, 4)
+    o = oracle.Oracle(p)
+    r1 = o.solve(x0, v, 5, Sigma0=Sig0, want_cov=True)
+    r4 = o.solve(x0, v, 5, Sigma0=Sig0, want_cov=True, threads=4)
+    for key in r1:
+        assert np.array_equal(r1[key], r4[key]), key
+
+
+def test_repair_objective_rejects_the_wheel_speed_model():
+    p = workload.wheels_problem(4, 4, 3)
+    with pytest.raises(ValueError):
+        oracle.Oracle(p).repair_objective(workload.racing_x0(p), np.zeros((3, 2)), 0)
 
 
 @pytest.mark.parametrize("cuts", [(), (1,), (37, 38, 100), (5, 17, 64, 65, 90, 120)])
