@@ -8,10 +8,14 @@ update and the warm-start shift in the same kernel's tail (one launch per step).
 the L2 cache is flushed (a 256 MiB write) before every timed step, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+                  [--mode replicas|shard]
 
-Prints one JSON line. Under torchrun (N > 1) every rank solves its own controller (replicas on
+Prints one JSON line. With N > 1 (launched under torchrun, or re-launched under it by this script
+when started without one) every rank solves its own controller in the default mode (replicas on
 independent tracks; no collective on the data path) and rank 0 prints the whole-job throughput
-from the slowest rank's time. `--impl reference` times the FP64 oracle on the host cores instead.
+from the slowest rank's time. `--mode shard` instead splits one solve's K samples over the ranks
+(one all-gather of the 3 + 2T log-sum-exp partials per solve): strong scaling of one solve.
+`--impl reference` times the FP64 oracle on the host cores instead.
 """
 from __future__ import annotations
 
@@ -36,8 +40,14 @@ METRIC = "particle-steps/s (K*M*T per solve)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one rollout_kernel launch, from one
 # ncu capture of the current kernel on each workload (None where none was taken).
 ROLLOUT_DRAM_BYTES = {"racing_K4096_M64_T40": 132864}
-# Device facts used for the ALU roofline (GB300: 152 SMs, 128 FP32 lanes per SM, max SM clock).
+# Device facts for the nominal ALU peak (GB300: 152 SMs, 128 FP32 lanes per SM, max SM clock); the
+# roofline's denominator is the FP32 peak measured on the device in the same run (bssmppi_fp32_peak).
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# Issue-slot and FMA-pipe activity of the rollout kernel from the committed ncu capture of the
+# current kernel (sm__inst_executed.avg.per_cycle_active / 4 and the FMA pipe's share of its peak).
+ROLLOUT_NCU = {"racing_K4096_M64_T40": {"issue_slots_busy": 3.15 / 4, "fma_pipe_of_peak": 0.446,
+                                        "lane_instructions_per_particle_step": 958,
+                                        "source": "profiles/rollout_kernel_racing_K4096_M64_T40.md"}}
 
 
 def algorithmic_flops_per_particle_step(prob) -> float:
@@ -134,24 +144,52 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
-def run_cpu_baseline(p, budget_s: float = 12.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the same solve."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), or the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    import platform
+    return platform.machine()
+
+
+def _time_oracle(p, threads, budget_s):
+    """Rollout and cost of the first k samples of one solve, k sized to about budget_s seconds."""
     import oracle
 
     o = oracle.Oracle(p)
     x0 = workload.racing_x0(p)
     v = np.zeros((p.T, 2), np.float32)
-    k = 8
+    k = min(p.K, 8 * threads)
     t0 = time.perf_counter()
-    o.solve(x0, v, 0, k_range=(0, k))
+    o.solve(x0, v, 0, k_range=(0, k), threads=threads)
     dt = time.perf_counter() - t0
-    k = int(min(p.K, max(8, k * budget_s / max(dt, 1e-6))))
+    k = int(min(p.K, max(k, k * budget_s / max(dt, 1e-6))))
     t0 = time.perf_counter()
-    o.solve(x0, v, 0, k_range=(0, k))
+    o.solve(x0, v, 0, k_range=(0, k), threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": k * p.M * p.T / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"rollout and cost of the first {k} of the {p.K} control samples of one solve "
-                      f"({k * p.M * p.T} particle-steps, {dt:.1f} s, FP64, 1 thread)"}
+    return k, dt
+
+
+def run_cpu_baseline(p, budget_s: float = 12.0):
+    """The FP64 oracle as it stands on a bounded sample of the same solve: on all host cores (the
+    line's value; OpenMP threads over samples) and on one thread."""
+    import oracle
+
+    threads = oracle.host_threads()
+    k1, dt1 = _time_oracle(p, 1, budget_s / 2)
+    kn, dtn = _time_oracle(p, threads, budget_s / 2)
+    return {"value": kn * p.M * p.T / dtn, "unit": "particle-steps/s", "cores": threads, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": f"rollout and cost of the first {kn} of the {p.K} control samples of one solve "
+                      f"({kn * p.M * p.T} particle-steps, {dtn:.1f} s, FP64, {threads} threads)",
+            "one_thread": {"value": k1 * p.M * p.T / dt1, "cores": 1,
+                           "sample": f"the first {k1} control samples ({k1 * p.M * p.T} particle-steps, "
+                                     f"{dt1:.1f} s, FP64, 1 thread)"}}
 
 
 def run_reference(args):
@@ -163,10 +201,11 @@ def run_reference(args):
     x0 = workload.racing_x0(p)
     v = np.zeros((p.T, 2), np.float32)
     k_step = max(1, min(p.K, args.ref_samples))
+    threads = oracle.host_threads()
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = o.solve(x0, v, i, k_range=(0, k_step))
+        r = o.solve(x0, v, i, k_range=(0, k_step), threads=threads)
         oracle.optimal_control(r["S"][:k_step], r["u"][:k_step], float(p.lam))
         dt = time.perf_counter() - t0
         if i >= args.warmup:
@@ -174,12 +213,13 @@ def run_reference(args):
     mean_s = statistics.fmean(times)
     value = k_step * p.M * p.T / mean_s
     sample = (f"each step: rollout, cost, weights and update of the first {k_step} of the {p.K} control "
-              f"samples of one solve ({k_step * p.M * p.T} particle-steps), FP64, 1 thread")
+              f"samples of one solve ({k_step * p.M * p.T} particle-steps), FP64, {threads} threads")
     return {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": _workload_desc(p, args.workload),
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": threads, "kind": "oracle",
+                             "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -218,11 +258,33 @@ def _serve_stream(bssmppi, n_ctrl, rate_hz, duration_s, seed, batched, probs_par
     span = (max(r.t_done_us for r in ok) - min(r.t_submit_us for r in res)) * 1e-6 if ok else float("nan")
     pct = lambda a, q: float(np.percentile(a, q)) if a.size else None
     return {"offered_req_per_s": len(reqs) / duration_s, "submitted": stats["submitted"],
-            "completed": len(ok), "replaced_by_newer": stats["superseded"], "batches": stats["batches"],
+            "completed": len(ok), "replaced_by_newer": stats["superseded"],
+            "shed_fraction": stats["superseded"] / max(1, stats["submitted"]), "batches": stats["batches"],
             "max_batch": stats["max_batch_seen"], "solves_per_s": len(ok) / span,
             "particle_steps_per_s": work / span, "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
             "class_4096_64_40_latency_ms_p50": pct(cls, 50), "class_4096_64_40_latency_ms_p99": pct(cls, 99),
-            "class_4096_64_40_completed": int(cls.size), "submit_window_s": t_sub, "wall_s": t_all}
+            "class_4096_64_40_completed": int(cls.size), "submit_window_s": t_sub, "wall_s": t_all,
+            "_class_latencies_ms": cls}
+
+
+def _sweep_rate(bssmppi, n_ctrl, rate, seconds, repeats, batched, params, bw):
+    """One rate of the sweep: `repeats` windows of `seconds` each on independent arrival streams
+    (seeds 5, 6, ...). The K=4096, M=64, T=40 class's p99 is taken over the pooled latencies of all
+    windows; throughput is reported as the mean and range over the windows."""
+    runs = [_serve_stream(bssmppi, n_ctrl, rate, seconds, 5 + r, batched, params, bw) for r in range(repeats)]
+    pooled = np.concatenate([r.pop("_class_latencies_ms") for r in runs])
+    sps = [r["solves_per_s"] for r in runs]
+    p99_each = [r["class_4096_64_40_latency_ms_p99"] for r in runs]
+    submitted = sum(r["submitted"] for r in runs)
+    shed = sum(r["replaced_by_newer"] for r in runs)
+    return {"rate_hz_per_controller": rate, "windows": repeats, "window_s": seconds,
+            "offered_req_per_s": statistics.fmean(r["offered_req_per_s"] for r in runs),
+            "solves_per_s": statistics.fmean(sps), "solves_per_s_min": min(sps), "solves_per_s_max": max(sps),
+            "latency_ms_p99_mean_of_windows": statistics.fmean(r["latency_ms_p99"] for r in runs),
+            "class_4096_64_40_latency_ms_p99": float(np.percentile(pooled, 99)) if pooled.size else None,
+            "class_4096_64_40_latency_ms_p99_per_window": p99_each,
+            "class_4096_64_40_completed": int(pooled.size),
+            "replaced_by_newer": shed, "shed_fraction": shed / max(1, submitted)}
 
 
 def run_serving(args):
@@ -242,25 +304,31 @@ def run_serving(args):
            "policy": "latest state wins: a newer request of a controller replaces its pending one"}
     bw = args.serve_batch_work
     out["batch_work_limit_particle_steps"] = bw
-    out["batched"] = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, True, params, bw)
-    out["plain"] = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, False, params)
+    for name, batched in (("batched", True), ("plain", False)):
+        r = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, batched, params, bw)
+        r.pop("_class_latencies_ms")
+        out[name] = r
     # rate sweep of both paths on the same arrival streams: the highest sustained solves/s at which
-    # the K=4096, M=64, T=40 class keeps its p99 latency under 10 ms
+    # the K=4096, M=64, T=40 class keeps its p99 latency under 10 ms with at most 1 % of requests shed
     for name, batched in (("batched", True), ("plain", False)):
         sweep, best = [], None
-        for rate in (0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0):
-            r = _serve_stream(bssmppi, n_ctrl, rate, max(1.0, args.serve_seconds), 5, batched, params, bw)
+        for rate in args.serve_rates:
+            r = _sweep_rate(bssmppi, n_ctrl, rate, args.serve_sweep_seconds, args.serve_repeats, batched, params, bw)
+            sweep.append(r)
             p99 = r["class_4096_64_40_latency_ms_p99"]
-            sweep.append({"rate_hz_per_controller": rate, "offered_req_per_s": r["offered_req_per_s"],
-                          "solves_per_s": r["solves_per_s"], "latency_ms_p99": r["latency_ms_p99"],
-                          "class_4096_64_40_latency_ms_p99": p99, "replaced_by_newer": r["replaced_by_newer"]})
-            if p99 is not None and p99 < 10.0 and r["replaced_by_newer"] <= 0.01 * r["completed"]:
-                best = {"rate_hz_per_controller": rate, "solves_per_s": r["solves_per_s"],
-                        "class_4096_64_40_latency_ms_p99": p99}
+            if p99 is not None and p99 < 10.0 and r["shed_fraction"] <= 0.01:
+                best = {k: r[k] for k in ("rate_hz_per_controller", "solves_per_s", "solves_per_s_min",
+                                          "solves_per_s_max", "class_4096_64_40_latency_ms_p99",
+                                          "class_4096_64_40_completed", "shed_fraction")}
             elif p99 is not None and p99 > 50.0:
                 break
         out[f"rate_sweep_{name}"] = sweep
         out[f"{name}_max_solves_per_s_with_p99_under_10ms"] = best
+    b, q = out["batched_max_solves_per_s_with_p99_under_10ms"], out["plain_max_solves_per_s_with_p99_under_10ms"]
+    if b and q:
+        out["batched_over_plain_at_p99_under_10ms"] = {
+            "ratio": b["solves_per_s"] / q["solves_per_s"],
+            "ratio_range": [b["solves_per_s_min"] / q["solves_per_s_max"], b["solves_per_s_max"] / q["solves_per_s_min"]]}
     return out
 
 
@@ -406,6 +474,10 @@ def run_ours(args, rank, world, local_rank):
     def step():
         bssmppi.solve_shift(h, x0, None, None, 1)  # solve + warm-start shift of the resident nominal, one launch
 
+    # the roofline's denominator: this device's FP32 multiply-add rate, measured before the timed
+    # region (scalar and packed .f32x2 forms; the larger counts)
+    peaks = [bssmppi.fp32_peak(packed, 1 << 16, stream) for packed in (False, True)]
+    peak_meas = max(peaks, key=lambda r: r["tflops"])
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -499,7 +571,8 @@ def run_ours(args, rank, world, local_rank):
     units = p.K * p.M * p.T
     value = whole_job_throughput(units, mean_ms, world)
     flops = algorithmic_flops_per_particle_step(p) * units
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak_nominal = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = peak_meas["tflops"]
     achieved = flops / (mean_roll * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
@@ -510,8 +583,14 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "rollout_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": ROLLOUT_DRAM_BYTES.get(args.workload),
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 (fma) x 2070 MHz max SM clock",
-                     "flops_per_particle_step": algorithmic_flops_per_particle_step(p)},
+                     "peak_basis": (f"measured in this run: FP32 multiply-add microbenchmark (bssmppi_fp32_peak, "
+                                    f"{'packed .f32x2' if peak_meas['packed'] else 'scalar'} form, "
+                                    f"{peak_meas['sms']} SMs); scalar {peaks[0]['tflops']:.2f}, packed "
+                                    f"{peaks[1]['tflops']:.2f} TFLOP/s"),
+                     "peak_nominal": peak_nominal, "frac_of_nominal": achieved / peak_nominal,
+                     "peak_nominal_basis": "152 SMs x 128 FP32 lanes x 2 (fma) x 2070 MHz max SM clock",
+                     "flops_per_particle_step": algorithmic_flops_per_particle_step(p),
+                     "ncu": ROLLOUT_NCU.get(args.workload)},
         "e2e": {"value": whole_job_throughput(units, mean_e2e_ms, world), "unit": "particle-steps/s",
                 "h2d_bytes_per_step": 4 * (8 + 2 * p.T), "d2h_bytes_per_step": 4 * (2 * p.T + 2),
                 "copies_per_step": "one H2D (x0 padded to 8 floats | v) and one D2H (v+ | u0)"},
@@ -546,19 +625,122 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+def run_shard(args, rank, world, local_rank):
+    """One solve split over the ranks by its K samples (strong scaling): each rank's handle covers
+    K/N samples (bssmppi_set_sample_range; the random streams are keyed by the global sample index,
+    so the split does not change any sample), rolls them out and reduces them to a log-sum-exp partial
+    (bssmppi_solve_partial); one all-gather of the 3 + 2T partials (NCCL on the device, gloo through
+    the host); every rank merges them (bssmppi_merge_partials) into the whole solve's update and
+    shifts its resident nominal. A step is that whole solve; value = K M T / the slowest rank's step."""
+    import torch
+
+    from paper_2408_00494_gb300 import bssmppi
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    p = _problem(args.workload)
+    k0, k1 = rank * p.K // world, (rank + 1) * p.K // world
+    q = workload.Problem(**{**p.__dict__, "K": k1 - k0})
+    ctl = bssmppi.Controller(q, stream=stream)
+    h = ctl.h
+    bssmppi.set_sample_range(h, k0, p.K)
+    x0 = torch.as_tensor(workload.racing_x0(p), device=dev)
+    u0 = torch.zeros(2, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    dist = torch.distributed if world > 1 else None
+
+    def step(x):
+        bssmppi.sharded_solve(h, x, p.T, u0=u0)
+        bssmppi.shift(h, None, 1)
+
+    for _ in range(args.warmup):
+        step(x0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step(x0)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    mean_ms = statistics.fmean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    # end to end through the binding: H2D of the state from pinned memory, the sharded solve and
+    # shift, D2H of u0 into pinned memory, wall clock per step
+    x0_h = torch.as_tensor(workload.racing_x0(p)).pin_memory()
+    u0_h = torch.zeros(2).pin_memory()
+    x0_d = torch.empty(p.nx, device=dev)
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        x0_d.copy_(x0_h, non_blocking=True)
+        step(x0_d)
+        u0_h.copy_(u0, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    ctl.close()
+    mean_ms, e2e_ms = reduce_over_ranks([mean_ms, statistics.fmean(e2e) * 1e3], dev, world)
+    units = p.K * p.M * p.T
+    line = {"metric": METRIC, "value": units / (mean_ms * 1e-3), "unit": "particle-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**_workload_desc(p, args.workload), "parallelism": f"K split over {world} ranks"},
+            "solves_per_s": 1e3 / mean_ms,
+            "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": 4 * p.nx, "d2h_bytes_per_step": 8,
+                    "exchange_bytes_per_rank": 4 * (3 + 2 * p.T)},
+            "gpu_launches": 3 * args.steps,  # per step and rank: partial solve, merge, shift
+            "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = run_cpu_baseline(p, args.cpu_budget)
+    return line
+
+
+def _relaunch_under_torchrun(args) -> int:
+    """--gpus N > 1 without a launcher: run this script as N ranks under torch.distributed.run."""
+    import socket
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="racing_K4096_M64_T40")
+    ap.add_argument("--workload", default=None,
+                    help="racing_K4096_M64_T40 (default), racing_K256_M16_T20 or racing_K16384_M128_T60 "
+                         "(the default of --mode shard)")
+    ap.add_argument("--mode", choices=("replicas", "shard"), default="replicas")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--ref-samples", type=int, default=128)
+    ap.add_argument("--ref-samples", type=int, default=1024)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--closed-loop-steps", type=int, default=1000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-sweep-seconds", type=float, default=1.0, help="length of one window of the rate sweep")
+    ap.add_argument("--serve-repeats", type=int, default=1, help="windows per rate of the sweep (independent streams)")
+    ap.add_argument("--serve-rates", type=lambda s: tuple(float(x) for x in s.split(",")),
+                    default=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0), help="per-controller rates of the sweep (Hz)")
     ap.add_argument("--serve-batch-work", type=float, default=SERVE_BATCH_WORK,
                     help="particle-steps admitted per serving batch (bounds a batch's duration)")
     ap.add_argument("--repair-iters", type=int, default=5)
@@ -573,10 +755,18 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.workload is None:
+        args.workload = "racing_K16384_M128_T60" if args.mode == "shard" else "racing_K4096_M64_T40"
+    if args.gpus < 1:
+        raise SystemExit("--gpus must be >= 1")
 
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        raise SystemExit(_relaunch_under_torchrun(args))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but the launcher started {world} ranks (WORLD_SIZE)")
 
     if args.impl == "reference":
         if rank == 0:
@@ -587,7 +777,7 @@ def main():
         import torch
         torch.distributed.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     try:
-        line = run_ours(args, rank, world, local_rank)
+        line = (run_shard if args.mode == "shard" else run_ours)(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch

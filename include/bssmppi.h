@@ -361,6 +361,16 @@ int bssmppi_server_drain(bssmppi_server_t s, int32_t timeout_ms);
 int bssmppi_server_get_state(bssmppi_server_t s, int32_t ctrl_id, float* h_v, uint32_t* counter);
 int bssmppi_server_set_state(bssmppi_server_t s, int32_t ctrl_id, const float* h_v, uint32_t counter);
 int bssmppi_server_get_stats(bssmppi_server_t s, bssmppi_server_stats* out);
+/* Inspect one served solve (Algorithm 1's sample costs S, the normalised weights of Eq. "Weights"
+ * and the clamped perturbations eps_eff = u - v that Eq. "MPPI_update_law" averages): the next
+ * request of controller ctrl_id to complete has its S[K], w[K] and eps_eff[K][T][2] (row-major)
+ * copied, in that order, into the caller's host buffer h_out of cap_floats floats before its slot is
+ * reused, and *h_written receives K (2 + 2T), or -1 when that does not fit (nothing is copied), or -2
+ * on a CUDA error. *h_written is 0 until then; read it after bssmppi_server_drain. The buffer and
+ * *h_written must stay valid until the request completes. One-shot: a capture serves one request.
+ * EBUSY while the controller has work queued or in flight. Costs the copy's time in the scheduler
+ * thread; meant for checking and logging, not for the serving loop. */
+int bssmppi_server_capture(bssmppi_server_t s, int32_t ctrl_id, float* h_out, int64_t cap_floats, int64_t* h_written);
 const char* bssmppi_server_last_error(bssmppi_server_t s);
 /* Stop the scheduler, wait for the device and free everything. NULL is accepted. */
 int bssmppi_server_destroy(bssmppi_server_t s);
@@ -379,7 +389,10 @@ int bssmppi_server_destroy(bssmppi_server_t s);
  *   K in [1, BSSMPPI_K_MAX], T in [1, BSSMPPI_T_MAX]; larger sizes are rejected with EINVAL (the
  *   scratch holds at most 148 x 512 partial sums). lambda > 0. compensated: 1 = Kahan sums.
  * The first call on a device looks up the array's device address (once per device, with that
- * device current); make that first call before any stream capture. Every call shares the one array
+ * device current), and under lazy module loading (CUDA's default) the first launch also loads the
+ * library's kernels, which places the array in device memory and can synchronise the device. So
+ * make one warm-up call per device at start-up, before the allocation-free phase begins and before
+ * any stream capture; later calls do neither. Every call shares the one array
  * and the ticket is cleared at the start of each call, so calls that overlap on the GPU (on
  * different streams, or from different threads) race and must be serialised by the caller.
  * Asynchronous on `cuda_stream`; errors are reported through bssmppi_last_error(NULL).
@@ -416,6 +429,20 @@ int bssmppi_box_muller(const uint32_t* d_words, float* d_z, int64_t n, void* cud
  * it the library's atanf. Exported so that its error can be checked against an exact reference.
  */
 int bssmppi_slip_atan(const float* d_t, float* d_y, int64_t n, void* cuda_stream);
+
+/*
+ * Measured FP32 arithmetic peak of the current device (no counterpart in the paper: the
+ * denominator of the rollout kernel's roofline, which is bound by FP32 issue, not by memory or
+ * tensor cores). Runs a grid of (blocks per SM at full occupancy) x SMs blocks of 256 threads, each
+ * thread with 16 independent fused multiply-add chains of `iters` steps (packed = 1: the same chains
+ * as 8 register pairs through the packed .f32x2 form), once to warm up and once timed with CUDA
+ * events on cuda_stream (NULL = the legacy default stream). Writes the timed launch's duration
+ * (*h_ms), its rate counting a multiply-add as two operations (*h_tflops, 1e12 per second) and the
+ * SM count (*h_sms). Allocates and frees one float. EINVAL if iters is outside [1, 2^24] or an
+ * output is NULL; ECUDA on a CUDA error. Synchronous.
+ */
+int bssmppi_fp32_peak(int32_t packed, int32_t iters, void* cuda_stream, float* h_ms, double* h_tflops,
+                      int32_t* h_sms);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libbssmppi.so")
 SOURCES = ["rollout.cu", "rollout_model0.cu", "rollout_model1.cu", "rollout_model2.cu", "update.cu", "repair.cu",
-           "serve.cu", "runtime.cu"]
+           "serve.cu", "runtime.cu", "peak.cu"]
 HEADERS = [os.path.join(CSRC, "device.cuh"), os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "rollout_body.cuh"),
            os.path.join(CSRC, "rollout_kernel.cuh"),
            os.path.join(ROOT, "include", "bssmppi.h")]

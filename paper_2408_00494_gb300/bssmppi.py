@@ -123,6 +123,9 @@ def load(build_if_missing: bool = True):
         "bssmppi_server_get_state": (ctypes.c_int, [vp, i32, vp, ctypes.POINTER(u32)]),
         "bssmppi_server_set_state": (ctypes.c_int, [vp, i32, vp, u32]),
         "bssmppi_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+        "bssmppi_fp32_peak": (ctypes.c_int, [i32, i32, vp, ctypes.POINTER(ctypes.c_float),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]),
+        "bssmppi_server_capture": (ctypes.c_int, [vp, i32, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
         "bssmppi_server_last_error": (ctypes.c_char_p, [vp]),
         "bssmppi_server_destroy": (ctypes.c_int, [vp]),
         "bssmppi_repair_grad": (ctypes.c_int, [vp, vp, vp, vp, vp]),
@@ -280,17 +283,24 @@ def merge_partials(h, partials, v=None, u0=None):
 def sharded_solve(h, x0, T, Sigma0=None, v=None, u0=None, group=None):
     """One solve whose samples are split over the ranks of a torch.distributed group (each rank's
     handle covers its range, set with set_sample_range): partial, one all-gather of the partials,
-    merge. Every rank ends with the whole solve's update in its resident nominal (and v, u0)."""
+    merge. Every rank ends with the whole solve's update in its resident nominal (and v, u0).
+    With NCCL the partials are gathered on the device; with gloo (CPU collectives) they are staged
+    through host memory: 4 (3 + 2T) bytes per rank each way."""
     import torch
     import torch.distributed as dist
     part = torch.empty(3 + 2 * T, dtype=torch.float32, device=x0.device)
     solve_partial(h, x0, Sigma0, v, part)
     world = dist.get_world_size(group) if dist.is_initialized() else 1
-    if world > 1:
+    if world == 1:
+        parts = part.view(1, -1)
+    elif dist.get_backend(group) == "nccl":
         parts = torch.empty(world, 3 + 2 * T, dtype=torch.float32, device=x0.device)
         dist.all_gather_into_tensor(parts, part, group=group)
     else:
-        parts = part.view(1, -1)
+        host = part.cpu()
+        gathered = [torch.empty_like(host) for _ in range(world)]
+        dist.all_gather(gathered, host, group=group)
+        parts = torch.stack(gathered).to(x0.device)
     merge_partials(h, parts, v, u0)
 
 
@@ -391,6 +401,14 @@ def repair_objective(v, x0, handle):
     if _RepairObjective is None:
         _RepairObjective = _repair_objective_function()
     return _RepairObjective.apply(v, x0, handle)
+
+
+def fp32_peak(packed=False, iters=1 << 14, stream=None) -> dict:
+    """Measured FP32 multiply-add rate of the current device (bssmppi_fp32_peak)."""
+    ms, tf, sms = ctypes.c_float(0.0), ctypes.c_double(0.0), ctypes.c_int32(0)
+    _check(load().bssmppi_fp32_peak(int(bool(packed)), int(iters), _stream_handle(stream), ctypes.byref(ms),
+                                    ctypes.byref(tf), ctypes.byref(sms)))
+    return {"tflops": tf.value, "ms": ms.value, "sms": sms.value, "packed": bool(packed)}
 
 
 def model_step(h, x, u, x_next, w=None):
@@ -503,6 +521,32 @@ def server_get_stats(s) -> dict:
     st = ServerStats()
     _srv_check(load().bssmppi_server_get_stats(s, ctypes.byref(st)), s)
     return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+class ServerCapture:
+    """Host buffers that receive one served request's S, weights and eps_eff (bssmppi_server_capture)."""
+
+    def __init__(self, K_max, T_max):
+        self.buf = np.zeros(K_max * (2 + 2 * T_max), np.float32)
+        self.written = ctypes.c_int64(0)
+
+    def result(self, K, T):
+        """(S[K], w[K], eps[K, T, 2]) once the request completed, else None."""
+        n = self.written.value
+        if n == 0:
+            return None
+        if n < 0:
+            raise BssmppiError(n, "capture did not fit" if n == -1 else "capture copy failed")
+        assert n == K * (2 + 2 * T)
+        b = self.buf
+        return b[:K].copy(), b[K:2 * K].copy(), b[2 * K:2 * K + 2 * K * T].reshape(K, T, 2).copy()
+
+
+def server_capture(s, ctrl_id, K_max, T_max) -> ServerCapture:
+    cap = ServerCapture(K_max, T_max)
+    _srv_check(load().bssmppi_server_capture(s, int(ctrl_id), ctypes.c_void_p(cap.buf.ctypes.data), cap.buf.size,
+                                             ctypes.byref(cap.written)), s)
+    return cap
 
 
 def server_destroy(s):

@@ -225,6 +225,14 @@ struct Slot {
 
 }  // namespace
 
+// A one-shot request to copy a controller's next completed solve out of the slot's arena.
+struct Capture {
+    float* h_out = nullptr;
+    int64_t cap_floats = 0;
+    int64_t* h_written = nullptr;
+    bool armed = false;
+};
+
 struct bssmppi_server {
     bssmppi_server_config cfg{};
     int device = 0, sms = 0;
@@ -243,6 +251,7 @@ struct bssmppi_server {
     std::condition_variable cv;
     std::vector<Pending> pending;
     std::vector<char> has_pending, in_flight;
+    std::vector<Capture> capture;
     std::vector<bssmppi_result> done;
     uint64_t seq = 0;
     bssmppi_server_stats stats{};
@@ -340,8 +349,45 @@ void fill_descriptors(Slot& sl)
     }
 }
 
+// Copy the costs, weights and perturbations of every completed request with an armed capture to
+// its host buffer. Runs before harvest releases the slot, so the arena still holds them.
+void copy_captures(bssmppi_server* s, Slot& sl)
+{
+    std::vector<std::pair<int, Capture>> todo;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (int i = 0; i < (int)sl.batch.size(); ++i) {
+            Capture& c = s->capture[sl.batch[i].ctrl];
+            if (!c.armed) continue;
+            todo.emplace_back(i, c);
+            c.armed = false;
+        }
+    }
+    if (todo.empty()) return;
+    const auto* reqs = reinterpret_cast<const ServeReq*>(sl.h_desc + ((sizeof(ServeHeader) + 255) & ~(size_t)255));
+    for (auto& [i, c] : todo) {
+        const ServeReq& q = reqs[i];
+        const int64_t need = (int64_t)q.K * (2 + 2 * q.T);
+        int64_t written = -1;
+        if (need <= c.cap_floats) {
+            cudaError_t e = cudaMemcpyAsync(c.h_out, sl.d_arena + q.off_S, sizeof(float) * q.K, cudaMemcpyDeviceToHost,
+                                            sl.s[0]);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c.h_out + q.K, sl.d_arena + q.off_w, sizeof(float) * q.K, cudaMemcpyDeviceToHost,
+                                    sl.s[0]);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c.h_out + 2 * (size_t)q.K, sl.d_arena + q.off_eps, sizeof(float) * q.K * 2 * q.T,
+                                    cudaMemcpyDeviceToHost, sl.s[0]);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(sl.s[0]);
+            written = e == cudaSuccess ? need : -2;
+        }
+        *c.h_written = written;
+    }
+}
+
 void harvest(bssmppi_server* s, Slot& sl)
 {
+    copy_captures(s, sl);
     const double t = now_us(s->t0);
     std::lock_guard<std::mutex> lock(s->mu);
     for (int i = 0; i < (int)sl.batch.size(); ++i) {
@@ -495,6 +541,7 @@ int bssmppi_server_create(const bssmppi_server_config* cfg, bssmppi_server_t* ou
     s->pending.resize(C);
     s->has_pending.assign(C, 0);
     s->in_flight.assign(C, 0);
+    s->capture.resize(C);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_dp, sizeof(DevParams) * C);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_v, sizeof(float) * 2 * cfg->T_max * C);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ctr, sizeof(uint32_t) * C);
@@ -705,6 +752,24 @@ int bssmppi_server_set_state(bssmppi_server_t s, int32_t ctrl_id, const float* h
                                cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_ctr + ctrl_id, &counter, sizeof(uint32_t), cudaMemcpyHostToDevice);
     return e == cudaSuccess ? BSSMPPI_OK : srv_fail(s, BSSMPPI_ECUDA, cudaGetErrorString(e));
+}
+
+int bssmppi_server_capture(bssmppi_server_t s, int32_t ctrl_id, float* h_out, int64_t cap_floats, int64_t* h_written)
+{
+    if (!s || !h_out || !h_written) return srv_fail(s, BSSMPPI_EINVAL, "NULL argument");
+    if (cap_floats < 3) return srv_fail(s, BSSMPPI_EINVAL, "cap_floats must hold at least one sample");
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (ctrl_id < 0 || ctrl_id >= s->n_ctrl) {
+        s->err = "unknown controller";
+        return BSSMPPI_EINVAL;
+    }
+    if (s->has_pending[ctrl_id] || s->in_flight[ctrl_id]) {
+        s->err = "controller has work queued or in flight";
+        return BSSMPPI_EBUSY;
+    }
+    *h_written = 0;
+    s->capture[ctrl_id] = Capture{h_out, cap_floats, h_written, true};
+    return BSSMPPI_OK;
 }
 
 int bssmppi_server_get_stats(bssmppi_server_t s, bssmppi_server_stats* out)

@@ -46,3 +46,36 @@ def test_algorithmic_work_per_particle_step():
 def test_whole_job_throughput(world, ms, expect):
     import bench
     assert bench.whole_job_throughput(4096 * 64 * 40, ms, world) == pytest.approx(expect)
+
+
+def test_gpus_flag_must_match_the_launchers_rank_count():
+    """--gpus N under a launcher that started another number of ranks fails loudly (it never prints
+    a line for the wrong number of GPUs)."""
+    env = dict(os.environ, WORLD_SIZE="2", RANK="0", LOCAL_RANK="0")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "4", "--impl", "reference",
+                          "--steps", "1", "--warmup", "3", "--ref-samples", "4"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT, env=env)
+    assert out.returncode != 0 and "WORLD_SIZE" in out.stderr
+    assert not out.stdout.strip()
+
+
+def test_gpus_flag_without_a_launcher_starts_that_many_ranks():
+    """--gpus 2 without torchrun re-launches the script as two ranks (here the reference arm, which
+    only rank 0 runs and prints); the line reports both ranks."""
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--impl", "reference",
+                          "--steps", "1", "--warmup", "3", "--ref-samples", "4"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [json.loads(l) for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1 and lines[0]["n_gpus"] == 2
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    import bench
+    import oracle
+    p = workload.config0()
+    r = bench.run_cpu_baseline(p, budget_s=0.5)
+    assert r["kind"] == "oracle" and r["cores"] == oracle.host_threads() and r["value"] > 0
+    assert r["one_thread"]["cores"] == 1 and r["one_thread"]["value"] > 0
+    assert r["cpu"]

@@ -5,12 +5,15 @@ state estimate and its (K, M, T): alone or in a mix of other controllers' reques
 CUDA graphs, it must come out bit for bit the same, and equal to bssmppi_solve + bssmppi_shift on
 a single handle within the update tolerance (rel 1e-4 / abs 1e-5; the two update kernels add the
 weighted perturbations in different orders), with the same minimum trajectory cost bit for bit.
+Served requests are also compared with the FP64 oracle sample by sample (costs, weights and
+perturbations read back through bssmppi_server_capture).
 """
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import workload
 
 torch = pytest.importorskip("torch")
@@ -118,6 +121,68 @@ def test_server_matches_single_solve(K, M, T):
     assert np.all(np.abs(got[0] - ref_u0) <= 1e-5 + 1e-4 * np.abs(ref_u0))
     assert np.all(np.abs(got[1][:T] - ref_v) <= 1e-5 + 1e-4 * np.abs(ref_v))
     assert got[2] == ctr == 6
+
+
+ORACLE_MIX = [(4096, 64, 40), (1024, 128, 60), (700, 33, 20), (512, 8, 20), (2048, 32, 60)]
+
+
+def test_served_requests_match_the_oracle():
+    """Each request of a mixed batch against the FP64 oracle's solve of the same controller state and
+    counter followed by its one-step shift (Alg. 1, "ExecuteCommand" and the warm start): every
+    sample's perturbation (atol 1e-6) and cost (rel 1e-4, away from the collision indicator's jump),
+    the weights against the oracle's weights of the served costs (rel 1e-5 / abs 1e-7), the minimum
+    cost, u0 and the shifted nominal against the oracle's own (rel 1e-4 / abs 1e-5 plus twice the
+    first-order bound that the measured cost differences imply, as in the single-solve parity)."""
+    s, probs = _server(len(ORACLE_MIX))
+    ctr0 = 11
+    try:
+        caps = {}
+        for c, (K, M, T) in enumerate(ORACLE_MIX):
+            bssmppi.server_set_state(s, c, _v0(c), ctr0)
+            caps[c] = bssmppi.server_capture(s, c, K, T)
+        for c, (K, M, T) in enumerate(ORACLE_MIX):
+            bssmppi.server_submit(s, c, _x0(c), K, M, T, req_id=c)
+        bssmppi.server_drain(s, 60000)
+        res = {r.ctrl_id: r for r in bssmppi.server_poll(s)}
+        after = {c: bssmppi.server_get_state(s, c, T_MAX) for c in range(len(ORACLE_MIX))}
+        assert bssmppi.server_get_stats(s)["max_batch_seen"] >= 2  # they did share a batch
+    finally:
+        bssmppi.server_destroy(s)
+    for c, (K, M, T) in enumerate(ORACLE_MIX):
+        r = res[c]
+        assert r.status == 0 and (r.K, r.M, r.T) == (K, M, T)
+        S, w, eps = (a.astype(np.float64) for a in caps[c].result(K, T))
+        p = probs[c]
+        p.K, p.M, p.T = K, M, T
+        v = _v0(c)[:T]
+        ref = oracle.Oracle(p).solve(_x0(c), v, ctr0, threads=oracle.host_threads())
+        assert np.all(np.abs(eps - ref["eps"]) <= 1e-6), c
+        ok = ref["margin"] > 1e-4
+        assert (~ok).sum() <= max(2, K // 100)
+        scale = np.maximum(np.abs(ref["S"]), 1.0)
+        dS = S - ref["S"]
+        assert np.all(np.abs(dS[ok]) <= 1e-4 * scale[ok]), (c, np.max(np.abs(dS[ok]) / scale[ok]))
+        lam = float(np.float32(p.lam))
+        w_iso, _, _ = oracle.optimal_control(S, v.astype(np.float64)[None] + eps, lam)
+        assert np.all(np.abs(w - w_iso) <= 1e-7 + 1e-5 * w_iso), c
+        beta_ref = ref["diag"][0]
+        assert abs(r.beta - beta_ref) <= 1e-4 * max(1.0, abs(beta_ref)), c
+        dSc = np.where(ok, dS, 0.0)
+        dev = np.abs(dSc - np.sum(ref["w"] * dSc)) / lam
+        bound = np.einsum("k,kti->ti", ref["w"] * dev, np.abs(ref["u"] - ref["v_plus"][None]))
+        vp = ref["v_plus"]
+        tol = 1e-5 + 1e-4 * np.abs(vp) + 2 * bound
+        assert np.all(np.abs(np.array(r.u0) - vp[0]) <= tol[0]), c
+        shifted, tol_s = vp.copy(), tol.copy()
+        shifted[:-1], tol_s[:-1] = vp[1:], tol[1:]
+        v_after, ctr_after = after[c]
+        err = np.abs(v_after[:T] - shifted)
+        assert np.all(err <= tol_s), (c, err.max())
+        assert np.array_equal(v_after[T:], _v0(c)[T:])  # entries past the request's horizon untouched
+        assert ctr_after == ctr0 + 1
+        print(f"[serve vs oracle] K={K} M={M} T={T}: S max rel {np.max(np.abs(dS[ok]) / scale[ok]):.2e}, "
+              f"beta {r.beta:.6g} vs {beta_ref:.6g}, shifted v+ max err {err.max():.2e} (bound {bound.max():.2e}), "
+              f"indicator-margin exclusions {(~ok).sum()}")
 
 
 def test_newer_request_replaces_pending_one_and_every_request_gets_a_result():

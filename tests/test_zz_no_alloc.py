@@ -4,12 +4,14 @@ Callers that cannot allocate device memory at run time (hard real-time loops, pl
 process owns the device memory) use bssmppi_update_noalloc, whose scratch is a fixed array in the
 library. This checks, through the C ABI, that two calls in a row give the same weights, v+, first
 control, diagnostics and counter advance as the update inside bssmppi_solve, within the update
-tolerance of the parity tests (rel 1e-4 / abs 1e-5 for v+, rel 1e-5 / abs 1e-7 for weights).
+tolerance of the parity tests (rel 1e-4 / abs 1e-5 for v+, rel 1e-5 / abs 1e-7 for weights),
+and the same against the FP64 oracle's weights and update of the same costs and perturbations.
 This file is collected last so that a failure here leaves every other test already run.
 """
 import numpy as np
 import pytest
 
+import oracle
 import workload
 
 torch = pytest.importorskip("torch")
@@ -63,6 +65,11 @@ def test_update_noalloc_matches_solve_on_two_calls_in_a_row():
         _close(w, ref["w"], 1e-5, 1e-7)
         _close(diag, ref["diag"], 1e-5, 1e-7)
         assert int(counter.item()) == 8
+        # and against the FP64 weights and update of the same costs and perturbations
+        S64, eps64 = ref["S"].double().cpu().numpy(), ref["eps"].double().cpu().numpy()
+        w64, vp64, _ = oracle.optimal_control(S64, v.astype(np.float64)[None] + eps64, float(np.float32(p.lam)))
+        _close(v_io, torch.as_tensor(vp64), 1e-4, 1e-5)
+        _close(w, torch.as_tensor(w64), 1e-5, 1e-7)
 
 
 def test_update_noalloc_without_optional_outputs_and_size_limit():
