@@ -287,6 +287,44 @@ def _sweep_rate(bssmppi, n_ctrl, rate, seconds, repeats, batched, params, bw):
             "replaced_by_newer": shed, "shed_fraction": shed / max(1, submitted)}
 
 
+def solve_kernel_on_the_mix(bssmppi, prm0, K=8192, reps=20):
+    """The single-solve kernel's particle-steps/s on each (M, T) class of the serving mix at K=8192
+    (one solve + shift per launch, back to back), and the rate it would sustain on the mix's work:
+    the work-weighted harmonic mean over the uniform (K, M, T) classes. The server's saturation
+    throughput is compared with it."""
+    import ctypes
+
+    import torch
+
+    rates = {}
+    for M in workload.SERVE_M:
+        for T in workload.SERVE_T:
+            prm = bssmppi.Params()
+            ctypes.pointer(prm)[0] = prm0
+            prm.K, prm.M, prm.T = K, M, T
+            h = bssmppi.create(prm)
+            try:
+                x0 = torch.as_tensor(np.array([10.0, 0.0, 0.0, 0.0, 0.0, 5.0], np.float32), device="cuda")
+                for _ in range(3):
+                    bssmppi.solve_shift(h, x0, None, None, 1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(reps):
+                    bssmppi.solve_shift(h, x0, None, None, 1)
+                b.record()
+                torch.cuda.synchronize()
+                rates[(M, T)] = K * M * T * reps / (a.elapsed_time(b) * 1e-3)
+            finally:
+                bssmppi.destroy(h)
+    kbar = statistics.fmean(workload.SERVE_K)
+    work = {c: kbar * c[0] * c[1] for c in rates}
+    mix = sum(work.values()) / sum(work[c] / rates[c] for c in rates)
+    return {"K": K, "particle_steps_per_s_by_M_T": {f"M{m}_T{t}": r for (m, t), r in rates.items()},
+            "mix_particle_steps_per_s": mix,
+            "note": "work-weighted harmonic mean over the uniform (K, M, T) mix: the rate one solve at a time "
+                    "would sustain with every launch as full as K=8192 makes it"}
+
+
 def run_serving(args):
     """Serving: 512 controllers on independent tracks, Poisson arrivals at 20 Hz each, (K, M, T)
     drawn from {512, 2048, 4096, 8192} x {8, 32, 64, 128} x {20, 40, 60}; the batched server against
@@ -324,6 +362,7 @@ def run_serving(args):
                 break
         out[f"rate_sweep_{name}"] = sweep
         out[f"{name}_max_solves_per_s_with_p99_under_10ms"] = best
+    out["solve_kernel_on_the_mix"] = solve_kernel_on_the_mix(bssmppi, params[0])
     b, q = out["batched_max_solves_per_s_with_p99_under_10ms"], out["plain_max_solves_per_s_with_p99_under_10ms"]
     if b and q:
         out["batched_over_plain_at_p99_under_10ms"] = {

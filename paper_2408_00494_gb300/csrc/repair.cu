@@ -49,7 +49,10 @@ __device__ __forceinline__ void chan_merge(float& n, float& m, float& m2, float 
     n = nn;
 }
 
-template <int MODEL>
+// FS: the stride between the fields of a record (floats), a compile-time bound on M, so that every
+// field sits at a fixed offset from the record's base and each load or store needs no address
+// arithmetic of its own.
+template <int MODEL, int FS>
 __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevParams dp, const RepairIO io)
 {
     constexpr int NX = MODEL == 0 ? 6 : 4;
@@ -78,12 +81,15 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
 #pragma unroll
     for (int i = 0; i < NX; ++i) x0[i] = io.x0[i];
     const float s0 = (MODEL == 0) ? x0[5] : 0.0f;
-    // Records of the forward pass, component-major so each field of all particles is contiguous:
-    // record (t, j) = the state entering Euler substep j of step t, then (bicycle) that substep's
-    // tape. Xat(t, i) = component i of the state at the start of step t.
+    // Records of the forward pass, component-major so each field of a warp's particles is one
+    // contiguous 128-byte line: record s = t n_sub + j holds the state entering Euler substep j of
+    // step t, then (bicycle) that substep's tape; field i of particle q at rec(s)[i FS + q].
+    // Record t n_sub is the state at the start of step t, record T n_sub the final state.
     const int nsub = (MODEL == 0) ? dp.n_sub : 1;
     constexpr int R = (MODEL == 0) ? NX + kTapeFloats : NX;
-    auto Xs = [&](int t, int j, int i) -> float* { return io.X + (((size_t)t * nsub + j) * R + i) * M + n; };
+    const int nc = valid ? n : M - 1;  // lanes past M read a valid record; their results are masked
+    auto rec = [&](int sr) -> float* { return io.X + (size_t)sr * (R * FS); };
+    auto Xs = [&](int t, int j, int i) -> float* { return rec(t * nsub + j) + i * FS + n; };
     auto Xat = [&](int t, int i) -> float* { return Xs(t, 0, i); };
 
     for (int it = 0; it <= io.iters; ++it) {
@@ -139,7 +145,7 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
         // 1 + w + nw, ...; each lane merges particles lane, lane + 32, ... one by one, then Chan's
         // pairwise merge across the lanes.
         for (int t = 1 + wid; t <= T; t += nw) {
-            const float* ey = io.X + (((size_t)t * nsub) * R + EY) * M;
+            const float* ey = rec(t * nsub) + EY * FS;
             float cnt = 0.0f, mu = 0.0f, m2 = 0.0f;
             for (int q = lane; q < M; q += 32) chan_merge(cnt, mu, m2, 1.0f, ey[q], 0.0f);
 #pragma unroll
@@ -214,15 +220,17 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
             // the step boundaries too, so the L2 latency stays off the chain.
             const int S = T * nsub;
             auto load = [&](float (&r)[R], int sr) {
+                if (sr >= 0) {
+                    const float* p = rec(sr) + nc;
 #pragma unroll
-                for (int i = 0; i < R; ++i)
-                    r[i] = (valid && sr >= 0) ? io.X[((size_t)sr * R + i) * M + n] : (i < 6 ? x0[i] : 0.0f);
+                    for (int i = 0; i < R; ++i) r[i] = p[i * FS];
+                }
             };
             float r0[R], r1[R], r2[R], r3[R];
             load(r0, S - 1);
             load(r1, S - 2);
             load(r2, S - 3);
-            float ey_next = valid ? *Xat(T, EY) : 0.0f;  // e_y at the end of the step being entered
+            float ey_next = rec(S)[EY * FS + nc];  // e_y at the end of the step being entered
             int t = T - 1, j = nsub - 1;
             Control c;
             float gs = 0.0f, ga = 0.0f;
@@ -255,7 +263,7 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
             }
         } else {
             for (int t = T; t >= 1; --t) {
-                inject(t, valid ? *Xat(t, EY) : 0.0f);
+                inject(t, rec(t)[EY * FS + nc]);
                 float gs = 0.0f, ga = 0.0f;
                 double_integrator_step_vjp(dp, g, gs, ga);
                 store_du(t - 1, gs, ga);
@@ -284,11 +292,14 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
     }
 }
 
+// The field stride of the records: 64 floats up to 64 particles, else the largest M.
+static int repair_field_stride(const DevParams& dp) { return dp.M <= 64 ? 64 : kRepairMaxThreads; }
+
 size_t repair_scratch_floats(const DevParams& dp)
 {
     const size_t nsub = dp.nx == 6 ? (size_t)dp.n_sub : 1;
     const size_t record = dp.nx == 6 ? (size_t)dp.nx + kTapeFloats : (size_t)dp.nx;
-    return ((size_t)dp.T * nsub + 1) * record * dp.M;
+    return ((size_t)dp.T * nsub + 1) * record * repair_field_stride(dp);
 }
 
 static size_t repair_smem_bytes(const DevParams& dp)
@@ -302,8 +313,13 @@ cudaError_t repair_prepare(const DevParams& dp)
 {
     const size_t smem = repair_smem_bytes(dp);
     if (smem <= 48 * 1024) return cudaSuccess;
-    if (dp.nx == 6) return cudaFuncSetAttribute(repair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaFuncSetAttribute(repair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int fs = repair_field_stride(dp);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (dp.nx == 6)
+        return fs == 64 ? cudaFuncSetAttribute(repair_kernel<0, 64>, attr, (int)smem)
+                        : cudaFuncSetAttribute(repair_kernel<0, kRepairMaxThreads>, attr, (int)smem);
+    return fs == 64 ? cudaFuncSetAttribute(repair_kernel<1, 64>, attr, (int)smem)
+                    : cudaFuncSetAttribute(repair_kernel<1, kRepairMaxThreads>, attr, (int)smem);
 }
 
 cudaError_t repair_launch(const DevParams& dp, const float* x0, float* v, const uint32_t* ctr, float* X, float* grad,
@@ -313,8 +329,14 @@ cudaError_t repair_launch(const DevParams& dp, const float* x0, float* v, const 
     RepairIO io{x0, v, ctr, X, grad, J, iters, step};
     const int threads = ((dp.M + 31) / 32) * 32;
     const size_t smem = repair_smem_bytes(dp);
-    if (dp.nx == 6) repair_kernel<0><<<1, threads, smem, st>>>(dp, io);
-    else repair_kernel<1><<<1, threads, smem, st>>>(dp, io);
+    const bool narrow = repair_field_stride(dp) == 64;
+    if (dp.nx == 6) {
+        if (narrow) repair_kernel<0, 64><<<1, threads, smem, st>>>(dp, io);
+        else repair_kernel<0, kRepairMaxThreads><<<1, threads, smem, st>>>(dp, io);
+    } else {
+        if (narrow) repair_kernel<1, 64><<<1, threads, smem, st>>>(dp, io);
+        else repair_kernel<1, kRepairMaxThreads><<<1, threads, smem, st>>>(dp, io);
+    }
     return cudaGetLastError();
 }
 
