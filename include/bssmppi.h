@@ -310,7 +310,10 @@ int bssmppi_timing_read(bssmppi_t h, float* h_rollout_ms, float* h_update_ms, in
  * BSSMPPI_EBUSY). A scheduler thread admits requests in arrival order while the batch has room
  * and the slot's share of hbm_budget_bytes holds their buffers (K*T*2 + 2K floats each); requests
  * that arrive while a batch runs are admitted into the other slot and run beside it on the device.
- * Batches run as captured CUDA graphs (use_graphs = 1) of persistent batched kernels. With
+ * Batches run as captured CUDA graphs (use_graphs = 1) of persistent batched kernels. Controllers
+ * whose problem constants agree in everything but their seed and track form one constants class; a
+ * batch holds requests of one class (the oldest pending request's), whose constants the batched
+ * kernels take as a parameter, so requests of another class wait for a batch of their own. With
  * max_batch = 1 and slots = 1 the server runs one solve at a time (the one-launch-per-solve path).
  * ---------------------------------------------------------------------------------------------- */
 typedef struct bssmppi_server* bssmppi_server_t;

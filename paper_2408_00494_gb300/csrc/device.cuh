@@ -110,7 +110,9 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk0, 
 // word 2 = sample, word 3 = (stream << 28) | (solve counter & 0x0fffffff).
 enum : uint32_t { kStreamControl = 0u, kStreamDisturbance = 1u, kStreamInitial = 3u, kStreamResample = 4u };
 
-__device__ __forceinline__ uint4 draw_words(const DevParams& P, uint32_t step, uint32_t call, uint32_t particle,
+// PP: any parameter object with the Philox round keys rk0, rk1 (DevParams, or a serving item).
+template <typename PP>
+__device__ __forceinline__ uint4 draw_words(const PP& P, uint32_t step, uint32_t call, uint32_t particle,
                                             uint32_t sample, uint32_t stream, uint32_t ctr)
 {
     return philox4x32_10_rk(make_uint4(step | (call << 16), particle, sample, (stream << 28) | (ctr & 0x0fffffffu)),
@@ -136,8 +138,8 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 }
 
 // Standard normals of one draw (Gaussian pair i from call i/2, words 2(i%2), 2(i%2)+1).
-template <int NX>
-__device__ __forceinline__ void draw_normals(const DevParams& P, uint32_t step, uint32_t particle, uint32_t sample,
+template <int NX, typename PP>
+__device__ __forceinline__ void draw_normals(const PP& P, uint32_t step, uint32_t particle, uint32_t sample,
                                              uint32_t stream, uint32_t ctr, float (&z)[NX])
 {
     const uint4 w0 = draw_words(P, step, 0u, particle, sample, stream, ctr);
@@ -159,8 +161,8 @@ __device__ __forceinline__ void draw_normals(const DevParams& P, uint32_t step, 
 // (H = dist_half) share the counter whose word 1 is the lower index: its calls 0-2 give six Gaussian
 // pairs, pairs 0-2 to the lower particle and 3-5 to the upper one, so no word goes unused. Other
 // state counts draw per particle.
-template <int NX>
-__device__ __forceinline__ void draw_disturbance(const DevParams& P, uint32_t step, uint32_t particle, uint32_t sample,
+template <int NX, typename PP>
+__device__ __forceinline__ void draw_disturbance(const PP& P, uint32_t step, uint32_t particle, uint32_t sample,
                                                  uint32_t ctr, float (&z)[NX])
 {
     if constexpr (NX == 6) {
@@ -180,7 +182,8 @@ __device__ __forceinline__ void draw_disturbance(const DevParams& P, uint32_t st
 
 // The disturbances of both particles of one 6-state pair (lower index q, upper q + H) from their
 // shared counter: three calls instead of four.
-__device__ __forceinline__ void draw_disturbance_pair(const DevParams& P, uint32_t step, uint32_t q, uint32_t sample,
+template <typename PP>
+__device__ __forceinline__ void draw_disturbance_pair(const PP& P, uint32_t step, uint32_t q, uint32_t sample,
                                                       uint32_t ctr, float (&lo)[6], float (&hi)[6])
 {
     const uint4 w0 = draw_words(P, step, 0u, q, sample, kStreamDisturbance, ctr);
@@ -254,7 +257,9 @@ __device__ __forceinline__ void sincos_series(float x, float* s, float* c)
     }
 }
 
-__device__ __forceinline__ float track_curvature(const DevParams& P, const float* __restrict__ kap, float s)
+// PP: any parameter object with the track's track_scale and n_track_mask.
+template <typename PP>
+__device__ __forceinline__ float track_curvature(const PP& P, const float* __restrict__ kap, float s)
 {
     const float x = s * P.track_scale;
     const float fl = floorf(x);
@@ -266,7 +271,8 @@ __device__ __forceinline__ float track_curvature(const DevParams& P, const float
 
 // The same lookup from a table of (kappa_i, kappa_{i+1} - kappa_i) pairs (one 8-byte load; the
 // difference is the same FP32 subtraction, so the result is bit-identical).
-__device__ __forceinline__ float track_curvature(const DevParams& P, const float2* __restrict__ kap, float s)
+template <typename PP>
+__device__ __forceinline__ float track_curvature(const PP& P, const float2* __restrict__ kap, float s)
 {
     const float x = s * P.track_scale;
     const float fl = floorf(x);
@@ -362,9 +368,10 @@ __device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp,
 // derivative is summed at its own (small) magnitude before one fused multiply-add adds h times it
 // to the state: v_x' = v_x + h (a - D_f sin(delta)/m g_f + v_y r), and so on, with g_f, g_r the
 // tyre curves' values sin(C atan(B alpha)).
-template <typename V, typename Tab>
-__device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
-                                                const SubstepCtl<V>& u, V (&X)[6], V& sp, V& cp)
+// TP: the object holding the track's scale and mask (P itself, or a serving item).
+template <typename V, typename Tab, typename TP>
+__device__ __forceinline__ void bicycle_substep(const DevParams& P, const TP& trk, const Tab* __restrict__ kap,
+                                                float s0, const SubstepCtl<V>& u, V (&X)[6], V& sp, V& cp)
 {
     const V vx = X[0], vy = X[1], r = X[2];
     // v_x >= vx_floor >= 1 and 1 - kappa e_y is near 1, so the fast (2-ulp) quotients are safe.
@@ -381,7 +388,7 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const Tab* _
     const auto sn = [](float a) { return __sinf(a); };
     const V gf = each(vmul(fold<V>(P, kFoldTC), each(bf, at)), sn);   // F_f / D_f
     const V gr = each(vmul(fold<V>(P, kFoldTC), each(br, at)), sn);   // F_r / D_r
-    const V nk = each(X[5], [&](float a) { return -track_curvature(P, kap, s0 + a); });  // -kappa(s)
+    const V nk = each(X[5], [&](float a) { return -track_curvature(trk, kap, s0 + a); });  // -kappa(s)
     const V num = vfma(vx, cp, vmul(vmul(vy, sp), fold<V>(P, kFoldM1)));                // v_x cos - v_y sin
     const V den = vfma(nk, X[4], fold<V>(P, kFoldOne));                                 // 1 - kappa e_y
     const V sdot = each(num, den, [](float a, float b) { return __fdividef(a, b); });
@@ -447,9 +454,9 @@ __device__ __forceinline__ WheelsCtl<V> wheels_ctl(const DevParams& P, const Con
 //   v_x' = v_x + h (F_X / m + (D_xr / m) C + v_y r),   v_y' = v_y + h (F_Y / m - (D_r / m) D - v_x r),
 //   r' = r + h ((l_f / I_z) F_Y + (l_r D_r / I_z) D),   w_F' = w_F - (h R_w / I_w) F_xf,
 //   w_R' = w_R + h (tau_max a / I_w - (R_w D_xr / I_w) C).
-template <typename V, typename Tab>
-__device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __restrict__ kap, float s0,
-                                               const WheelsCtl<V>& u, V (&X)[8], V& sp, V& cp)
+template <typename V, typename Tab, typename TP>
+__device__ __forceinline__ void wheels_substep(const DevParams& P, const TP& trk, const Tab* __restrict__ kap,
+                                               float s0, const WheelsCtl<V>& u, V (&X)[8], V& sp, V& cp)
 {
     const V vx = X[0], vy = X[1], r = X[2], wf = X[3], wr = X[4];
     const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
@@ -468,7 +475,7 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const Tab* __
     const V C = vmul(gr, kr), D = vmul(gr, nar);
     const V FX = vfma(G2, u.nsn, vmul(G1, u.cs));
     const V FY = vfma(G1, u.sn, vmul(G2, u.cs));
-    const V nk = each(X[7], [&](float a) { return -track_curvature(P, kap, s0 + a); });     // -kappa(s)
+    const V nk = each(X[7], [&](float a) { return -track_curvature(trk, kap, s0 + a); });     // -kappa(s)
     const V num = vfma(vx, cp, vmul(vmul(vy, sp), fold<V>(P, kFoldM1)));
     const V den = vfma(nk, X[6], fold<V>(P, kFoldOne));
     const V sdot = each(num, den, [](float a, float b) { return __fdividef(a, b); });
@@ -615,12 +622,12 @@ __device__ __forceinline__ void model_step(const DevParams& P, const float* __re
         float sp, cp;
         sincos_series(x[3], &sp, &cp);
         const SubstepCtl<float> c = substep_ctl<float>(P, u);
-        for (int j = 0; j < P.n_sub; ++j) bicycle_substep(P, kap, s0, c, x, sp, cp);
+        for (int j = 0; j < P.n_sub; ++j) bicycle_substep(P, P, kap, s0, c, x, sp, cp);
     } else if constexpr (MODEL == 2) {
         float sp, cp;
         sincos_series(x[5], &sp, &cp);
         const WheelsCtl<float> c = wheels_ctl<float>(P, u);
-        for (int j = 0; j < P.n_sub; ++j) wheels_substep(P, kap, s0, c, x, sp, cp);
+        for (int j = 0; j < P.n_sub; ++j) wheels_substep(P, P, kap, s0, c, x, sp, cp);
     } else {
         double_integrator_step(P, u, x);
     }

@@ -34,40 +34,41 @@ struct RollIO {
 // var is produced for EY only unless all_var. With equal counts on every lane and no recording,
 // all means are merged; otherwise means outside dp.mean_mask (states no cost term weights) are not
 // merged across lanes and are left lane-local.
-template <int NX, int EY, int P, bool COMP>
-__device__ __forceinline__ void belief_moments(const DevParams& dp, const float (&x)[P][NX], int ls, int seg,
-                                               bool all_var, float (&mean)[NX], float (&var)[NX])
+// IT: the object holding the sample's sizes (M, uniform, Mf, invM, invM1): dp itself, or a serving item.
+template <int NX, int EY, int P, bool COMP, typename IT>
+__device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it, const float (&x)[P][NX], int ls,
+                                               int seg, bool all_var, float (&mean)[NX], float (&var)[NX])
 {
     if constexpr (COMP) {
         // Per lane: exact two-pass mean and M2 over its (at most P) particles.
         float cnt = 0.0f;
-        if (dp.uniform) {
+        if (it.uniform) {
             cnt = (float)P;
         } else {
 #pragma unroll
-            for (int p = 0; p < P; ++p) cnt += (ls + seg * p < dp.M) ? 1.0f : 0.0f;
+            for (int p = 0; p < P; ++p) cnt += (ls + seg * p < it.M) ? 1.0f : 0.0f;
         }
-        const float inv_cnt = dp.uniform ? (1.0f / (float)P) : (cnt > 0.0f ? 1.0f / cnt : 0.0f);
+        const float inv_cnt = it.uniform ? (1.0f / (float)P) : (cnt > 0.0f ? 1.0f / cnt : 0.0f);
         float m2[NX];
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
             float s = 0.0f;
 #pragma unroll
-            for (int p = 0; p < P; ++p) s += (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
+            for (int p = 0; p < P; ++p) s += (it.uniform || ls + seg * p < it.M) ? x[p][i] : 0.0f;
             mean[i] = s * inv_cnt;
             float q = 0.0f;
             if (i == EY || all_var) {
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     const float d = x[p][i] - mean[i];
-                    q += (dp.uniform || ls + seg * p < dp.M) ? d * d : 0.0f;
+                    q += (it.uniform || ls + seg * p < it.M) ? d * d : 0.0f;
                 }
             }
             m2[i] = q;
         }
         // Chan et al. pairwise merge across the segment; the formulas are symmetric in the two
         // partners, so both ends of every exchange compute bit-identical results.
-        if (dp.uniform && !all_var) {
+        if (it.uniform && !all_var) {
             // Equal counts on every lane: merging two halves of n each gives mean = (mean_a +
             // mean_b) / 2 and M2 = M2_a + M2_b + (mean_b - mean_a)^2 n / 2. The lanes carry the sums
             // 2^r mean after r merges instead (scaling by a power of two is exact, so every rounding
@@ -97,7 +98,7 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
 #pragma unroll
             for (int i = 0; i < NX; ++i) mean[i] = sm[i] * scale;
             m2[EY] = m2e;
-        } else if (dp.uniform) {
+        } else if (it.uniform) {
             for (int off = seg >> 1; off > 0; off >>= 1) {
                 const float half_n = 0.5f * cnt;
 #pragma unroll
@@ -134,7 +135,7 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
             }
         }
 #pragma unroll
-        for (int i = 0; i < NX; ++i) var[i] = m2[i] * dp.invM1;
+        for (int i = 0; i < NX; ++i) var[i] = m2[i] * it.invM1;
     } else {
         // Naive one-pass sums: mean = sum x / M, var = (sum x^2 - M mean^2) / (M - 1).
         float s[NX], q[NX];
@@ -144,7 +145,7 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
             q[i] = 0.0f;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float xv = (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
+                const float xv = (it.uniform || ls + seg * p < it.M) ? x[p][i] : 0.0f;
                 s[i] += xv;
                 if (i == EY || all_var) q[i] += xv * xv;
             }
@@ -159,8 +160,8 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const float 
         }
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
-            mean[i] = s[i] * dp.invM;
-            var[i] = (q[i] - dp.Mf * mean[i] * mean[i]) * dp.invM1;
+            mean[i] = s[i] * it.invM;
+            var[i] = (q[i] - it.Mf * mean[i] * mean[i]) * it.invM1;
         }
     }
 }
@@ -188,8 +189,8 @@ __device__ __forceinline__ void butterfly_sum(float (&v)[N], int seg)
 // covariance (packed lower triangle by rows), in two passes over the segment: the sums give the
 // means, then the centred products are summed. xor-butterfly sums are symmetric in the two partners,
 // so every lane of the segment ends with bit-identical moments.
-template <int NX, int P>
-__device__ __forceinline__ void belief_moments_full(const DevParams& dp, const float (&x)[P][NX], int ls, int seg,
+template <int NX, int P, typename IT>
+__device__ __forceinline__ void belief_moments_full(const IT& dp, const float (&x)[P][NX], int ls, int seg,
                                                     float (&mean)[NX], float (&C)[NX * (NX + 1) / 2])
 {
     float s[NX];
@@ -294,29 +295,35 @@ __host__ __device__ constexpr int roll_max_threads()
 // registers of their own. UTRIG: my_u holds (u_0, u_1, sin u_0, cos u_0) per step (T x 4), so the
 // steering angle's sine and cosine are taken once per step by the lanes that draw the controls
 // instead of by every lane in every step; otherwise T x 2.
-template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float, bool PACK = true, bool UTRIG = false>
-__device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO& io, const Tab* __restrict__ kap_s,
-                                               const float* __restrict__ v_s, float* __restrict__ my_u, int group,
-                                               uint32_t ctr, const ConSet* cs = nullptr)
+// IT: the object holding the per-solve fields (the sizes K, M, T, seg, spw, uniform, dist_half, M's
+// reciprocals, k_off), the Philox round keys and the track's scale and mask. The single-solve kernel
+// passes dp itself; the server passes a per-warp item in shared memory while dp, the constants its
+// batch's vehicles share, stays in kernel parameter space.
+template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float, bool PACK = true, bool UTRIG = false,
+          typename IT = DevParams>
+__device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it, const RollIO& io,
+                                               const Tab* __restrict__ kap_s, const float* __restrict__ v_s,
+                                               float* __restrict__ my_u, int group, uint32_t ctr,
+                                               const ConSet* cs = nullptr)
 {
     constexpr int NX = model_nx(MODEL);
     constexpr int EY = MODEL == 0 ? 4 : (MODEL == 2 ? 6 : 1);
     constexpr int SI = model_s_index(MODEL);  // path coordinate, carried relative to its start (or -1)
     const int lane = threadIdx.x & (kWarp - 1);
-    const int seg = dp.seg;
+    const int seg = it.seg;
     const int ls = lane & (seg - 1);
-    const int k = group * dp.spw + lane / seg;
-    const bool active = k < dp.K;
-    const int kc = active ? k : dp.K - 1;  // inactive segments shadow a valid sample, write nothing
-    const uint32_t kg = (uint32_t)(kc + dp.k_off);  // global sample index: the random streams' key
+    const int k = group * it.spw + lane / seg;
+    const bool active = k < it.K;
+    const int kc = active ? k : it.K - 1;  // inactive segments shadow a valid sample, write nothing
+    const uint32_t kg = (uint32_t)(kc + it.k_off);  // global sample index: the random streams' key
     const uint32_t kk = dp.crn ? 0u : kg;
 
     // (a1, a2) control noise eps ~ N(0, Sigma_eps) and clamped samples u = clamp(v + eps); the
     // lanes of the segment split the horizon. eps_eff = u - v feeds the update.
     constexpr bool TRIG = UTRIG && MODEL != 1;
     constexpr int UPS = UTRIG ? 4 : 2;  // floats of my_u per step
-    for (int t = ls; t < dp.T; t += seg) {
-        const uint4 w = draw_words(dp, (uint32_t)t, 0u, 0u, kg, kStreamControl, ctr);
+    for (int t = ls; t < it.T; t += seg) {
+        const uint4 w = draw_words(it, (uint32_t)t, 0u, 0u, kg, kStreamControl, ctr);
         const float2 z = box_muller(w.x, w.y);
         const float e0 = dp.Le00 * z.x;
         const float e1 = fmaf(dp.Le10, z.x, dp.Le11 * z.y);
@@ -326,7 +333,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         my_u[UPS * t] = u0;
         my_u[UPS * t + 1] = u1;
         if constexpr (TRIG) sincosf(u0, &my_u[UPS * t + 2], &my_u[UPS * t + 3]);
-        if (active) reinterpret_cast<float2*>(io.eps)[(size_t)k * dp.T + t] = make_float2(u0 - v0, u1 - v1);
+        if (active) reinterpret_cast<float2*>(io.eps)[(size_t)k * it.T + t] = make_float2(u0 - v0, u1 - v1);
     }
     __syncwarp();
 
@@ -353,7 +360,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             float xi[NX];
-            draw_normals<NX>(dp, 0u, (uint32_t)(ls + seg * p), kk, kStreamInitial, ctr, xi);
+            draw_normals<NX>(it, 0u, (uint32_t)(ls + seg * p), kk, kStreamInitial, ctr, xi);
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
                 float w = 0.0f;
@@ -390,14 +397,14 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
     if (dp.record && writer) {
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
-            io.mean[(size_t)k * (dp.T + 1) * NX + i] = mean[i];
-            io.var[(size_t)k * (dp.T + 1) * NX + i] = var0[i];
+            io.mean[(size_t)k * (it.T + 1) * NX + i] = mean[i];
+            io.var[(size_t)k * (it.T + 1) * NX + i] = var0[i];
         }
     }
 
     CompSum S;
     float S_naive = 0.0f;
-    for (int t = 0; t < dp.T; ++t) {
+    for (int t = 0; t < it.T; ++t) {
         // (a7) S += q(x_bar_t) + ctrl_w v_t^T Sigma_eps^-1 u_t + C_safe(z_t)
         const float u0 = my_u[UPS * t], u1 = my_u[UPS * t + 1];
         const float v0 = v_s[2 * t], v1 = v_s[2 * t + 1];
@@ -451,8 +458,8 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
             for (int j = 0; j < dp.n_sub; ++j) {
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    if constexpr (MODEL == 0) bicycle_substep(dp, kap_s, s0, sc, X[q], hs[q], hc[q]);
-                    else wheels_substep(dp, kap_s, s0, sc, X[q], hs[q], hc[q]);
+                    if constexpr (MODEL == 0) bicycle_substep(dp, it, kap_s, s0, sc, X[q], hs[q], hc[q]);
+                    else wheels_substep(dp, it, kap_s, s0, sc, X[q], hs[q], hc[q]);
                 }
             }
 #pragma unroll
@@ -475,7 +482,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
 #pragma unroll
             for (int p = 0; p < P / 2; ++p) {
                 float zl[NX], zh[NX];
-                draw_disturbance_pair(dp, (uint32_t)t, (uint32_t)(ls + seg * p), kk, ctr, zl, zh);
+                draw_disturbance_pair(it, (uint32_t)t, (uint32_t)(ls + seg * p), kk, ctr, zl, zh);
                 if (dp.lw_diag) {
                     add_diagonal<NX>(dp.Lw, zl, x[p]);
                     add_diagonal<NX>(dp.Lw, zh, x[p + P / 2]);
@@ -488,7 +495,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 float z[NX];
-                draw_disturbance<NX>(dp, (uint32_t)t, (uint32_t)(ls + seg * p), kk, ctr, z);
+                draw_disturbance<NX>(it, (uint32_t)t, (uint32_t)(ls + seg * p), kk, ctr, z);
                 if (dp.lw_diag) add_diagonal<NX>(dp.Lw, z, x[p]);
                 else add_correlated<NX>(dp.Lw, z, x[p]);
             }
@@ -498,7 +505,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
         float h_next = 0.0f;
         if constexpr (FULL) {
             float C[NX * (NX + 1) / 2];
-            belief_moments_full<NX, P>(dp, x, ls, seg, mean, C);
+            belief_moments_full<NX, P>(it, x, ls, seg, mean, C);
 #pragma unroll
             for (int i = 0; i < NX; ++i) var[i] = C[i * (i + 1) / 2 + i];
             if (general) {
@@ -508,25 +515,25 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const RollIO
                 if constexpr (SI >= 0) ma[SI] += s0;
                 h_next = general_barrier<NX>(*cs, ma, C);
             }
-            if (dp.resample && t + 1 < dp.T) {  // re-draw x^n_{t+1} ~ N(mean, cov) for the next step (stream 4)
+            if (dp.resample && t + 1 < it.T) {  // re-draw x^n_{t+1} ~ N(mean, cov) for the next step (stream 4)
                 cholesky_packed_psd<NX>(C);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     float xi[NX];
-                    draw_normals<NX>(dp, (uint32_t)(t + 1), (uint32_t)(ls + seg * p), kk, kStreamResample, ctr, xi);
+                    draw_normals<NX>(it, (uint32_t)(t + 1), (uint32_t)(ls + seg * p), kk, kStreamResample, ctr, xi);
 #pragma unroll
                     for (int i = 0; i < NX; ++i) x[p][i] = mean[i];
                     add_correlated<NX>(C, xi, x[p]);
                 }
             }
         } else {
-            belief_moments<NX, EY, P, COMP>(dp, x, ls, seg, dp.record != 0, mean, var);
+            belief_moments<NX, EY, P, COMP>(dp, it, x, ls, seg, dp.record != 0, mean, var);
         }
         if constexpr (SI >= 0) mean[SI] += s0;
         h_prev = h_cur;
         h_cur = general ? h_next : belief_barrier(dp, mean[EY], var[EY]);
         if (dp.record && writer) {
-            const size_t base = ((size_t)k * (dp.T + 1) + t + 1) * NX;
+            const size_t base = ((size_t)k * (it.T + 1) + t + 1) * NX;
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
                 io.mean[base + i] = mean[i];

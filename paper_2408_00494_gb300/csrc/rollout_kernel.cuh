@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(roll_max_threads<MODEL, P>()) rollout_kernel(c
     float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * 2 * TN;  // T x (u_0, u_1, sin u_0, cos u_0)
     const int n_groups = (dp.K + dp.spw - 1) / dp.spw;
     for (int group = blockIdx.x * wpb + warp; group < n_groups; group += gridDim.x * wpb)
-        rollout_group<MODEL, P, COMP, FULL, float2, true, true>(dp, io, kap_s, v_s, my_u, group, ctr, &cs);
+        rollout_group<MODEL, P, COMP, FULL, float2, true, true>(dp, dp, io, kap_s, v_s, my_u, group, ctr, &cs);
     __syncthreads();
 
     float* part = tail.part + (size_t)blockIdx.x * (3 + TN);

@@ -13,7 +13,11 @@
 //   H2D copy of the batch descriptors (fixed size)
 //   -> three persistent rollout kernels in parallel branches, one per particles-per-lane class
 //      (P = 1, 2, 4 for M <= 32, 64, 128); their warps pull (request, sample-group) items with an
-//      atomic counter and run the same per-group body as the single-solve kernel
+//      atomic counter and run the same per-group body as the single-solve kernel. The constants
+//      the batch's vehicles share (a batch holds controllers of one constants class) are a kernel
+//      parameter, so the body reads them as instruction operands and steps particle pairs with
+//      packed FP32 instructions as the single-solve kernel does; each warp keeps only its item's
+//      sizes, the controller's Philox keys and its track's scale in shared memory
 //   -> one block per request: weights, update, warm-start shift, counter
 //   -> D2H copy of the first controls (fixed size).
 // No kernel ever waits on the host or on another kernel.
@@ -58,17 +62,36 @@ struct ServeResult {
     float beta, eta;
 };
 
+// One work item's per-solve fields (the names the per-group body reads from its item object): the
+// request's sizes, the controller's Philox round keys and its track's scale and mask.
+struct __align__(16) ServeItem {
+    uint32_t rk0[10], rk1[10];
+    int K, M, T, seg, spw, uniform, dist_half, k_off;
+    float Mf, invM, invM1, track_scale;
+    int n_track_mask, pad[3];
+};
+
+// Largest sample count per warp of a particle class: 32 / seg, seg the smallest power of two >= M.
+__host__ __device__ constexpr int serve_spw_max(int cls) { return cls == 0 ? kServeSpwMax : 1; }
+
+// Blocks of kServeWarps warps per SM for the register bound: 6, 5 and 4 for 1, 2 and 4 particles
+// per lane (80, 102 and 128 registers), the tightest bounds at which the loop over work items
+// spills at most 8 bytes. (Two blocks more, the single-solve kernel's threads per SM, spilled 60-116
+// bytes and served 4 % fewer particle-steps per second at saturation.)
 template <int P>
-__global__ void __launch_bounds__(kServeWarps * kWarp, 4) serve_rollout_kernel(ServeHeader* hdr, const ServeReq* reqs,
-                                                                          const DevParams* ctrl_dp, float* arena,
-                                                                          const float* ctrl_v, const uint32_t* ctrl_ctr,
-                                                                          int cls, int T_max)
+__host__ __device__ constexpr int serve_min_blocks() { return P == 1 ? 6 : (P == 2 ? 5 : 4); }
+
+template <int P>
+__global__ void __launch_bounds__(kServeWarps * kWarp, serve_min_blocks<P>())
+    serve_rollout_kernel(const __grid_constant__ DevParams fleet, ServeHeader* hdr, const ServeReq* reqs,
+                         const DevParams* ctrl_dp, float* arena, const float* ctrl_v, const uint32_t* ctrl_ctr,
+                         int cls, int T_max)
 {
     extern __shared__ __align__(16) unsigned char serve_smem[];
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x & (kWarp - 1);
-    DevParams* dps = reinterpret_cast<DevParams*>(serve_smem) + warp;
-    float* ubuf = reinterpret_cast<float*>(reinterpret_cast<DevParams*>(serve_smem) + kServeWarps)
-                + (size_t)warp * kServeSpwMax * 2 * T_max;
+    ServeItem* it = reinterpret_cast<ServeItem*>(serve_smem) + warp;
+    float* ubuf = reinterpret_cast<float*>(reinterpret_cast<ServeItem*>(serve_smem) + kServeWarps)
+                + (size_t)warp * serve_spw_max(cls) * 2 * T_max;
     const int total = hdr->cls_groups[cls];
     const int rb = hdr->cls_begin[cls], rc = hdr->cls_count[cls];
     while (true) {
@@ -82,20 +105,25 @@ __global__ void __launch_bounds__(kServeWarps * kWarp, 4) serve_rollout_kernel(S
             if (reqs[mid].group_begin <= (int)item) lo = mid; else hi = mid - 1;
         }
         const ServeReq& rq = reqs[lo];
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(ctrl_dp + rq.ctrl);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(dps);
-        for (int i = lane; i < (int)(sizeof(DevParams) / 4); i += kWarp) dst[i] = src[i];
-        __syncwarp();
+        const DevParams& cd = ctrl_dp[rq.ctrl];
+        if (lane < 10) {
+            it->rk0[lane] = cd.rk0[lane];
+            it->rk1[lane] = cd.rk1[lane];
+        }
         if (lane == 0) {
-            dps->K = rq.K; dps->M = rq.M; dps->T = rq.T;
-            dps->seg = rq.seg; dps->spw = rq.spw; dps->uniform = rq.uniform; dps->dist_half = rq.dist_half;
-            dps->Mf = (float)rq.M; dps->invM = 1.0f / (float)rq.M; dps->invM1 = 1.0f / (float)(rq.M - 1);
+            it->K = rq.K; it->M = rq.M; it->T = rq.T;
+            it->seg = rq.seg; it->spw = rq.spw; it->uniform = rq.uniform; it->dist_half = rq.dist_half;
+            it->k_off = 0;
+            it->Mf = (float)rq.M; it->invM = 1.0f / (float)rq.M; it->invM1 = 1.0f / (float)(rq.M - 1);
+            it->track_scale = cd.track_scale;
+            it->n_track_mask = cd.n_track_mask;
         }
         __syncwarp();
         const float* v = ctrl_v + (size_t)rq.ctrl * 2 * T_max;
         RollIO io{rq.x0, nullptr, v, ctrl_ctr + rq.ctrl, arena + rq.off_S, arena + rq.off_eps, nullptr, nullptr};
         float* my_u = ubuf + (lane / rq.seg) * 2 * rq.T;
-        rollout_group<0, P, true, false, float, false>(*dps, io, dps->kappa, v, my_u, (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
+        rollout_group<0, P, true, false, float, true, false, ServeItem>(fleet, *it, io, cd.kappa, v, my_u,
+                                                                        (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
         __syncwarp();
     }
 }
@@ -200,7 +228,7 @@ double now_us(std::chrono::steady_clock::time_point t0)
 
 struct Pending {
     uint64_t id = 0;
-    int ctrl = 0, K = 0, M = 0, T = 0;
+    int ctrl = 0, K = 0, M = 0, T = 0, fleet = 0;
     float x0[6] = {};
     double t_submit = 0.0;
     uint64_t seq = 0;
@@ -218,6 +246,11 @@ struct Slot {
     size_t arena_floats = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t roll_node[kServeClasses] = {nullptr, nullptr, nullptr};  // the rollout kernels' nodes
+    cudaKernelNodeParams roll_kp[kServeClasses] = {};
+    int fleet = -1;        // constants class of the batch in the slot
+    DevParams fleet_params{};  // its constants, copied under the lock when the batch is formed
+    int graph_fleet = -1;  // constants class the graph's rollout nodes were last given
     bool busy = false;
     std::vector<Pending> batch;
     double t_launch = 0.0;
@@ -238,7 +271,12 @@ struct bssmppi_server {
     int device = 0, sms = 0;
     size_t desc_bytes = 0, res_bytes = 0;
     int roll_grid[kServeClasses] = {1, 1, 1};
-    size_t roll_smem = 0;
+    size_t roll_smem[kServeClasses] = {0, 0, 0};
+    // constants classes: controllers whose problem constants agree in everything but their Philox
+    // keys and track share a class; a batch holds one class, whose constants are the rollout
+    // kernels' parameter
+    std::vector<DevParams> fleets;
+    std::vector<int> fleet_of;
     // controller table
     std::vector<DevParams> h_dp;
     std::vector<float*> d_tracks;
@@ -294,12 +332,13 @@ cudaError_t issue_batch(bssmppi_server* s, Slot& sl)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.s[2], sl.fork, 0);
     if (e != cudaSuccess) return e;
     const int T_max = s->cfg.T_max;
-    serve_rollout_kernel<1><<<s->roll_grid[0], kServeWarps * kWarp, s->roll_smem, sl.s[0]>>>(
-        sl.d_hdr, sl.d_reqs, s->d_dp, sl.d_arena, s->d_v, s->d_ctr, 0, T_max);
-    serve_rollout_kernel<2><<<s->roll_grid[1], kServeWarps * kWarp, s->roll_smem, sl.s[1]>>>(
-        sl.d_hdr, sl.d_reqs, s->d_dp, sl.d_arena, s->d_v, s->d_ctr, 1, T_max);
-    serve_rollout_kernel<4><<<s->roll_grid[2], kServeWarps * kWarp, s->roll_smem, sl.s[2]>>>(
-        sl.d_hdr, sl.d_reqs, s->d_dp, sl.d_arena, s->d_v, s->d_ctr, 2, T_max);
+    const DevParams fleet = sl.fleet_params;
+    serve_rollout_kernel<1><<<s->roll_grid[0], kServeWarps * kWarp, s->roll_smem[0], sl.s[0]>>>(
+        fleet, sl.d_hdr, sl.d_reqs, s->d_dp, sl.d_arena, s->d_v, s->d_ctr, 0, T_max);
+    serve_rollout_kernel<2><<<s->roll_grid[1], kServeWarps * kWarp, s->roll_smem[1], sl.s[1]>>>(
+        fleet, sl.d_hdr, sl.d_reqs, s->d_dp, sl.d_arena, s->d_v, s->d_ctr, 1, T_max);
+    serve_rollout_kernel<4><<<s->roll_grid[2], kServeWarps * kWarp, s->roll_smem[2], sl.s[2]>>>(
+        fleet, sl.d_hdr, sl.d_reqs, s->d_dp, sl.d_arena, s->d_v, s->d_ctr, 2, T_max);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(sl.join1, sl.s[1]);
     if (e == cudaSuccess) e = cudaEventRecord(sl.join2, sl.s[2]);
@@ -310,6 +349,57 @@ cudaError_t issue_batch(bssmppi_server* s, Slot& sl)
                                                                      s->d_ctr, sl.d_res, T_max);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_res, sl.d_res, s->res_bytes, cudaMemcpyDeviceToHost, sl.s[0]);
+    return e;
+}
+
+// After capture: the graph's three rollout kernel nodes and their launch parameters.
+cudaError_t find_rollout_nodes(Slot& sl)
+{
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(sl.graph, nullptr, &n);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> nodes(n);
+    e = cudaGraphGetNodes(sl.graph, nodes.data(), &n);
+    const void* fn[kServeClasses] = {reinterpret_cast<const void*>(serve_rollout_kernel<1>),
+                                     reinterpret_cast<const void*>(serve_rollout_kernel<2>),
+                                     reinterpret_cast<const void*>(serve_rollout_kernel<4>)};
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        cudaGraphNodeType type;
+        e = cudaGraphNodeGetType(nodes[i], &type);
+        if (e != cudaSuccess || type != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+        for (int c = 0; c < kServeClasses && e == cudaSuccess; ++c)
+            if (kp.func == fn[c]) {
+                sl.roll_node[c] = nodes[i];
+                sl.roll_kp[c] = kp;
+            }
+    }
+    for (int c = 0; c < kServeClasses && e == cudaSuccess; ++c)
+        if (!sl.roll_node[c]) e = cudaErrorInvalidValue;
+    return e;
+}
+
+// Give the instantiated graph's rollout kernels the constants of the slot's batch class (applies
+// to this and later launches of the graph; launches already queued keep theirs).
+cudaError_t set_graph_fleet(bssmppi_server* s, Slot& sl)
+{
+    DevParams fleet = sl.fleet_params;
+    const DevParams* d_dp = s->d_dp;
+    float* arena = sl.d_arena;
+    const float* v = s->d_v;
+    const uint32_t* ctr = s->d_ctr;
+    int T_max = s->cfg.T_max;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < kServeClasses && e == cudaSuccess; ++c) {
+        int cls = c;
+        void* args[] = {&fleet, &sl.d_hdr, &sl.d_reqs, &d_dp, &arena, &v, &ctr, &cls, &T_max};
+        cudaKernelNodeParams kp = sl.roll_kp[c];
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        e = cudaGraphExecKernelNodeSetParams(sl.exec, sl.roll_node[c], &kp);
+    }
+    if (e == cudaSuccess) sl.graph_fleet = sl.fleet;
     return e;
 }
 
@@ -422,9 +512,12 @@ bool form_batch(bssmppi_server* s, Slot& sl)
     std::sort(order.begin(), order.end(), [&](int a, int b) { return s->pending[a].seq < s->pending[b].seq; });
     size_t used = 0;
     int64_t work = 0;
+    sl.fleet = order.empty() ? -1 : s->pending[order.front()].fleet;  // the oldest request's class
+    if (sl.fleet >= 0) sl.fleet_params = s->fleets[sl.fleet];
     for (int c : order) {
         if ((int)sl.batch.size() >= s->cfg.max_batch) break;
         const Pending& p = s->pending[c];
+        if (p.fleet != sl.fleet) continue;  // another constants class: waits for a batch of its own
         const size_t need = request_floats(p.K, p.T);
         if (used + need > sl.arena_floats) break;  // strict arrival order: the oldest waits for room
         const int64_t w = (int64_t)p.K * p.M * p.T;
@@ -467,7 +560,9 @@ void worker_loop(bssmppi_server* s)
             if (sl.busy || !form_batch(s, sl)) continue;
             fill_descriptors(sl);
             sl.t_launch = now_us(s->t0);
-            cudaError_t e = s->cfg.use_graphs ? cudaGraphLaunch(sl.exec, sl.s[0]) : issue_batch(s, sl);
+            cudaError_t e = cudaSuccess;
+            if (s->cfg.use_graphs && sl.graph_fleet != sl.fleet) e = set_graph_fleet(s, sl);
+            if (e == cudaSuccess) e = s->cfg.use_graphs ? cudaGraphLaunch(sl.exec, sl.s[0]) : issue_batch(s, sl);
             if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.s[0]);
             if (e != cudaSuccess) {
                 s->worker_error.store((int)e);
@@ -542,6 +637,7 @@ int bssmppi_server_create(const bssmppi_server_config* cfg, bssmppi_server_t* ou
     s->has_pending.assign(C, 0);
     s->in_flight.assign(C, 0);
     s->capture.resize(C);
+    s->fleet_of.assign(C, 0);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_dp, sizeof(DevParams) * C);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_v, sizeof(float) * 2 * cfg->T_max * C);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ctr, sizeof(uint32_t) * C);
@@ -550,17 +646,19 @@ int bssmppi_server_create(const bssmppi_server_config* cfg, bssmppi_server_t* ou
     const size_t hdr_bytes = (sizeof(ServeHeader) + 255) & ~(size_t)255;
     s->desc_bytes = hdr_bytes + sizeof(ServeReq) * cfg->max_batch;
     s->res_bytes = sizeof(ServeResult) * cfg->max_batch;
-    s->roll_smem = sizeof(DevParams) * kServeWarps + sizeof(float) * kServeWarps * kServeSpwMax * 2 * cfg->T_max;
-    if (e == cudaSuccess && s->roll_smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(serve_rollout_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->roll_smem);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(serve_rollout_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->roll_smem);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(serve_rollout_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->roll_smem);
-    }
+    for (int c = 0; c < kServeClasses; ++c)
+        s->roll_smem[c] = sizeof(ServeItem) * kServeWarps
+                        + sizeof(float) * kServeWarps * serve_spw_max(c) * 2 * cfg->T_max;
+    const auto smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(serve_rollout_kernel<1>, smem_attr, (int)s->roll_smem[0]);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(serve_rollout_kernel<2>, smem_attr, (int)s->roll_smem[1]);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(serve_rollout_kernel<4>, smem_attr, (int)s->roll_smem[2]);
     if (e == cudaSuccess) {
         int nb[3] = {0, 0, 0};
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], serve_rollout_kernel<1>, kServeWarps * kWarp, s->roll_smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], serve_rollout_kernel<2>, kServeWarps * kWarp, s->roll_smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[2], serve_rollout_kernel<4>, kServeWarps * kWarp, s->roll_smem);
+        const int tb = kServeWarps * kWarp;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], serve_rollout_kernel<1>, tb, s->roll_smem[0]);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], serve_rollout_kernel<2>, tb, s->roll_smem[1]);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[2], serve_rollout_kernel<4>, tb, s->roll_smem[2]);
         for (int i = 0; i < 3; ++i) s->roll_grid[i] = std::max(1, nb[i]) * s->sms;
     }
     const size_t arena_bytes = cfg->hbm_budget_bytes / cfg->slots;
@@ -590,6 +688,7 @@ int bssmppi_server_create(const bssmppi_server_config* cfg, bssmppi_server_t* ou
                 if (e == cudaSuccess) e = e_issue;
             }
             if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
+            if (e == cudaSuccess) e = find_rollout_nodes(sl);
         }
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -636,7 +735,25 @@ int bssmppi_server_add_controller(bssmppi_server_t s, const bssmppi_params* p, i
         if (d_track) cudaFree(d_track);
         return srv_fail(s, BSSMPPI_ECUDA, std::string("add_controller: ") + cudaGetErrorString(e));
     }
+    // its constants class: everything but the Philox keys, the track and the per-request sizes
+    DevParams key = d;
+    key.key0 = key.key1 = 0u;
+    std::memset(key.rk0, 0, sizeof(key.rk0));
+    std::memset(key.rk1, 0, sizeof(key.rk1));
+    key.kappa = nullptr;
+    key.track_scale = 0.0f;
+    key.n_track_mask = 0;
+    key.K = key.M = key.T = key.seg = key.spw = key.uniform = key.dist_half = key.k_off = key.K_norm = 0;
+    key.Mf = key.invM = key.invM1 = 0.0f;
     std::lock_guard<std::mutex> lock(s->mu);
+    int fleet = -1;
+    for (int f = 0; f < (int)s->fleets.size() && fleet < 0; ++f)
+        if (std::memcmp(&s->fleets[f], &key, sizeof(DevParams)) == 0) fleet = f;
+    if (fleet < 0) {
+        fleet = (int)s->fleets.size();
+        s->fleets.push_back(key);
+    }
+    s->fleet_of[id] = fleet;
     s->h_dp[id] = d;
     s->d_tracks[id] = d_track;
     s->n_ctrl = id + 1;
@@ -659,7 +776,7 @@ int bssmppi_server_submit(bssmppi_server_t s, int32_t ctrl_id, const float* h_x0
         return BSSMPPI_EINVAL;
     }
     Pending p;
-    p.id = req_id; p.ctrl = ctrl_id; p.K = K; p.M = M; p.T = T;
+    p.id = req_id; p.ctrl = ctrl_id; p.K = K; p.M = M; p.T = T; p.fleet = s->fleet_of[ctrl_id];
     std::memcpy(p.x0, h_x0, sizeof(p.x0));
     p.t_submit = now_us(s->t0);
     p.seq = s->seq++;

@@ -123,6 +123,59 @@ def test_server_matches_single_solve(K, M, T):
     assert got[2] == ctr == 6
 
 
+def test_two_constants_classes_batch_apart_and_match_their_single_solves():
+    """Controllers whose vehicles differ (here the mass) are batched by constants class: each
+    batch's rollout kernels take that class's constants as a parameter, and the graph's kernel
+    parameters are switched when a slot's class changes. Every request must still give, bit for bit,
+    what it gives alone, with and without graphs, and match bssmppi_solve + bssmppi_shift."""
+    n = 6
+    s = bssmppi.server_create(n, T_max=T_MAX)
+    probs = [_problem(i) for i in range(n)]
+    for i, p in enumerate(probs):
+        if i % 2:
+            p.mass = 1200.0  # a lighter vehicle: a second constants class
+        bssmppi.server_add_controller(s, bssmppi.make_params(p))
+    reqs = [(c, 1024 + 256 * c, (8, 32, 64, 128, 64, 32)[c], (20, 40, 60, 20, 40, 60)[c]) for c in range(n)]
+    try:
+        together = _run(s, reqs)
+        for _ in range(2):  # the classes alternate between batches: the graph's parameters follow
+            again = _run(s, reqs)
+            for c in together:
+                assert np.array_equal(again[c][0], together[c][0]) and np.array_equal(again[c][1], together[c][1])
+        for r in reqs[:3]:
+            alone = _run(s, [r])
+            assert np.array_equal(alone[r[0]][0], together[r[0]][0])
+            assert np.array_equal(alone[r[0]][1], together[r[0]][1])
+        assert bssmppi.server_get_stats(s)["batches"] >= 2 * 3 + 3
+    finally:
+        bssmppi.server_destroy(s)
+    s2 = bssmppi.server_create(n, T_max=T_MAX, use_graphs=False, slots=1)
+    try:
+        for p in probs:
+            bssmppi.server_add_controller(s2, bssmppi.make_params(p))
+        eager = _run(s2, reqs)
+    finally:
+        bssmppi.server_destroy(s2)
+    for c, K, M, T in reqs:
+        assert np.array_equal(eager[c][0], together[c][0]) and np.array_equal(eager[c][1], together[c][1])
+        p = probs[c]
+        p.K, p.M, p.T = K, M, T
+        h = bssmppi.Controller(p)
+        try:
+            bssmppi.set_counter(h.h, 5)
+            v = torch.as_tensor(_v0(c)[:T], device="cuda").contiguous()
+            u0 = torch.zeros(2, device="cuda")
+            bssmppi.solve(h.h, torch.as_tensor(_x0(c), device="cuda"), None, v, u0)
+            bssmppi.shift(h.h, v, 1)
+            torch.cuda.synchronize()
+            S = h.buffer(bssmppi.BUF_S).cpu().numpy()
+        finally:
+            h.close()
+        assert np.float32(together[c][3]) == S.min(), c
+        ref_v = v.cpu().numpy()
+        assert np.all(np.abs(together[c][1][:T] - ref_v) <= 1e-5 + 1e-4 * np.abs(ref_v)), c
+
+
 ORACLE_MIX = [(4096, 64, 40), (1024, 128, 60), (700, 33, 20), (512, 8, 20), (2048, 32, 60)]
 
 
