@@ -223,14 +223,16 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-SERVE_BATCH_WORK = 40_000_000  # particle-steps per batch: about 2 ms of GPU time
+SERVE_BATCH_WORK = 20_000_000  # particle-steps per batch: under 1 ms of GPU time
+SERVE_SLOTS = 8                # batches in flight
 
 
-def _serve_stream(bssmppi, n_ctrl, rate_hz, duration_s, seed, batched, probs_params, batch_work=SERVE_BATCH_WORK):
+def _serve_stream(bssmppi, n_ctrl, rate_hz, duration_s, seed, batched, probs_params, batch_work=SERVE_BATCH_WORK,
+                  slots=SERVE_SLOTS):
     """Replay a Poisson arrival stream against a server; returns latency/throughput statistics."""
     reqs = workload.serving_requests(n_ctrl=n_ctrl, rate_hz=rate_hz, duration_s=duration_s, seed=seed)
     if batched:
-        s = bssmppi.server_create(n_ctrl, max_batch=512, T_max=60, slots=2, use_graphs=True,
+        s = bssmppi.server_create(n_ctrl, max_batch=512, T_max=60, slots=slots, use_graphs=True,
                                   hbm_budget_bytes=2 << 30, max_batch_work=int(batch_work))
     else:
         s = bssmppi.server_create(n_ctrl, max_batch=1, T_max=60, slots=1, use_graphs=False,
@@ -267,11 +269,11 @@ def _serve_stream(bssmppi, n_ctrl, rate_hz, duration_s, seed, batched, probs_par
             "_class_latencies_ms": cls}
 
 
-def _sweep_rate(bssmppi, n_ctrl, rate, seconds, repeats, batched, params, bw):
+def _sweep_rate(bssmppi, n_ctrl, rate, seconds, repeats, batched, params, bw, slots=SERVE_SLOTS):
     """One rate of the sweep: `repeats` windows of `seconds` each on independent arrival streams
     (seeds 5, 6, ...). The K=4096, M=64, T=40 class's p99 is taken over the pooled latencies of all
     windows; throughput is reported as the mean and range over the windows."""
-    runs = [_serve_stream(bssmppi, n_ctrl, rate, seconds, 5 + r, batched, params, bw) for r in range(repeats)]
+    runs = [_serve_stream(bssmppi, n_ctrl, rate, seconds, 5 + r, batched, params, bw, slots) for r in range(repeats)]
     pooled = np.concatenate([r.pop("_class_latencies_ms") for r in runs])
     sps = [r["solves_per_s"] for r in runs]
     p99_each = [r["class_4096_64_40_latency_ms_p99"] for r in runs]
@@ -342,8 +344,9 @@ def run_serving(args):
            "policy": "latest state wins: a newer request of a controller replaces its pending one"}
     bw = args.serve_batch_work
     out["batch_work_limit_particle_steps"] = bw
+    out["slots"] = args.serve_slots
     for name, batched in (("batched", True), ("plain", False)):
-        r = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, batched, params, bw)
+        r = _serve_stream(bssmppi, n_ctrl, 20.0, args.serve_seconds, 4, batched, params, bw, args.serve_slots)
         r.pop("_class_latencies_ms")
         out[name] = r
     # rate sweep of both paths on the same arrival streams: the highest sustained solves/s at which
@@ -351,7 +354,8 @@ def run_serving(args):
     for name, batched in (("batched", True), ("plain", False)):
         sweep, best = [], None
         for rate in args.serve_rates:
-            r = _sweep_rate(bssmppi, n_ctrl, rate, args.serve_sweep_seconds, args.serve_repeats, batched, params, bw)
+            r = _sweep_rate(bssmppi, n_ctrl, rate, args.serve_sweep_seconds, args.serve_repeats, batched, params, bw,
+                            args.serve_slots)
             sweep.append(r)
             p99 = r["class_4096_64_40_latency_ms_p99"]
             if p99 is not None and p99 < 10.0 and r["shed_fraction"] <= 0.01:
@@ -777,9 +781,11 @@ def main():
     ap.add_argument("--closed-loop-steps", type=int, default=1000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-sweep-seconds", type=float, default=1.0, help="length of one window of the rate sweep")
+    ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS, help="batches the batched server keeps in flight (1-8)")
     ap.add_argument("--serve-repeats", type=int, default=1, help="windows per rate of the sweep (independent streams)")
     ap.add_argument("--serve-rates", type=lambda s: tuple(float(x) for x in s.split(",")),
-                    default=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0), help="per-controller rates of the sweep (Hz)")
+                    default=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 5.5, 6.0),
+                    help="per-controller rates of the sweep (Hz)")
     ap.add_argument("--serve-batch-work", type=float, default=SERVE_BATCH_WORK,
                     help="particle-steps admitted per serving batch (bounds a batch's duration)")
     ap.add_argument("--repair-iters", type=int, default=5)

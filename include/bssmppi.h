@@ -322,7 +322,7 @@ typedef struct bssmppi_server_config {
     int32_t max_controllers;   /* controller table size, 1..65536 */
     int32_t max_batch;         /* requests per batch, 1..4096 */
     int32_t T_max;             /* largest horizon of any request, 1..BSSMPPI_T_MAX */
-    int32_t slots;             /* 1 or 2 batches in flight */
+    int32_t slots;             /* batches in flight, 1..8 */
     int32_t use_graphs;        /* 1: replay one captured CUDA graph per batch */
     int32_t reserved;          /* must be 0 */
     size_t hbm_budget_bytes;   /* device memory for the in-flight requests' buffers (split over slots) */
@@ -345,7 +345,7 @@ typedef struct bssmppi_server_stats {
     double now_us;             /* server clock at the call */
 } bssmppi_server_stats;
 
-/* Create a server on the current device. Allocates the controller table, two slots' descriptors,
+/* Create a server on the current device. Allocates the controller table, the slots' descriptors,
  * results and HBM arenas, captures the batch graphs and starts the scheduler thread. */
 int bssmppi_server_create(const bssmppi_server_config* cfg, bssmppi_server_t* out);
 /* Register a controller (bicycle model, compensated; K, M, T of params are ignored: each request

@@ -5,9 +5,9 @@
 // arrive on any host thread; a newer request of a controller replaces its older pending one
 // (latest state wins). A scheduler thread forms batches in arrival order, admitting a request when
 // its controller has nothing in flight, the batch has room and the slot's HBM arena can hold its
-// buffers (perturbations K*T*2, costs K, weights K). Two slots alternate, each with its own
-// streams, arena and descriptors, so requests that arrive while one batch runs on the GPU are
-// admitted into the other and overlap with it on the device.
+// buffers (perturbations K*T*2, costs K, weights K). Up to four slots take turns, each with its own
+// streams, arena and descriptors, so requests that arrive while a batch runs on the GPU are
+// admitted into another slot and overlap with it on the device.
 //
 // A batch is one fixed sequence, captured once per slot as a CUDA graph and replayed:
 //   H2D copy of the batch descriptors (fixed size)
@@ -39,6 +39,7 @@
 namespace bss {
 
 constexpr int kServeClasses = 3;   // P = 1, 2, 4
+constexpr int kServeMaxSlots = 8;  // batches in flight at most
 constexpr int kServeWarps = 4;     // warps per block of the batched rollout
 constexpr int kServeSpwMax = 16;   // samples per warp when M = 2
 
@@ -293,7 +294,7 @@ struct bssmppi_server {
     std::vector<bssmppi_result> done;
     uint64_t seq = 0;
     bssmppi_server_stats stats{};
-    Slot slots[2];
+    Slot slots[kServeMaxSlots];
     int n_slots = 2;
     std::thread worker;
     std::atomic<bool> stop{false};
@@ -623,7 +624,7 @@ int bssmppi_server_create(const bssmppi_server_config* cfg, bssmppi_server_t* ou
     if (cfg->max_controllers < 1 || cfg->max_controllers > 65536) return srv_fail(nullptr, BSSMPPI_EINVAL, "max_controllers out of range [1, 65536]");
     if (cfg->max_batch < 1 || cfg->max_batch > 4096) return srv_fail(nullptr, BSSMPPI_EINVAL, "max_batch out of range [1, 4096]");
     if (cfg->T_max < 1 || cfg->T_max > BSSMPPI_T_MAX) return srv_fail(nullptr, BSSMPPI_EINVAL, "T_max out of range [1, 256]");
-    if (cfg->slots != 1 && cfg->slots != 2) return srv_fail(nullptr, BSSMPPI_EINVAL, "slots must be 1 or 2");
+    if (cfg->slots < 1 || cfg->slots > kServeMaxSlots) return srv_fail(nullptr, BSSMPPI_EINVAL, "slots out of range [1, 8]");
     if (cfg->hbm_budget_bytes < (size_t)(1 << 20)) return srv_fail(nullptr, BSSMPPI_EINVAL, "hbm_budget_bytes must be >= 1 MiB");
     auto* s = new bssmppi_server();
     s->cfg = *cfg;

@@ -92,6 +92,14 @@ def test_result_alone_equals_in_mix_and_without_graphs():
             assert np.array_equal(eager[c][0], together[c][0]) and np.array_equal(eager[c][1], together[c][1])
     finally:
         bssmppi.server_destroy(s2)
+    s4, _ = _server(len(MIX), slots=4, max_batch=2)  # four batches in flight, two requests each
+    try:
+        four = _run(s4, [(c, K, M, T) for c, (K, M, T) in enumerate(MIX)])
+        for c in four:
+            assert np.array_equal(four[c][0], together[c][0]) and np.array_equal(four[c][1], together[c][1])
+        assert bssmppi.server_get_stats(s4)["batches"] >= len(MIX) // 2
+    finally:
+        bssmppi.server_destroy(s4)
 
 
 @pytest.mark.parametrize("K,M,T", [(4096, 64, 40), (512, 8, 20), (1024, 128, 60), (700, 33, 20)])
@@ -280,6 +288,12 @@ def test_admission_respects_hbm_budget():
         assert 1 <= st["max_batch_seen"] <= 3 and st["batches"] >= 4
     finally:
         bssmppi.server_destroy(s)
+
+
+def test_server_rejects_bad_slot_counts():
+    for slots in (0, 9):
+        with pytest.raises(bssmppi.BssmppiError):
+            bssmppi.server_create(2, T_max=T_MAX, slots=slots)
 
 
 def test_server_rejects_bad_requests():
