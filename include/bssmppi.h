@@ -434,6 +434,22 @@ int bssmppi_box_muller(const uint32_t* d_words, float* d_z, int64_t n, void* cud
 int bssmppi_slip_atan(const float* d_t, float* d_y, int64_t n, void* cuda_stream);
 
 /*
+ * The tyre curve of the simplified Pacejka law as the bicycle substep evaluates it (Sec. V-A's
+ * vehicle model, reading R3: F_y = mu F_z sin(C atan(B alpha))): d_y[i] = sin(C atan(d_x[i])) for
+ * the handle's C, n values (x = B alpha); device arrays. For |x| <= 1 a degree-9 polynomial in x^2
+ * fitted to the curve on the host for that C; beyond, the library's atanf and the hardware sine.
+ * Exported so that its error can be checked against an exact reference. Asynchronous.
+ */
+int bssmppi_tyre_curve(bssmppi_t h, const float* d_x, float* d_y, int64_t n, void* cuda_stream);
+
+/*
+ * The coefficients c_0..c_9 (h_c, host, n >= 10 floats) of that polynomial for a tyre shape factor
+ * C > 0: sin(C atan x) = x sum_i c_i x^(2i) on |x| <= 1, interpolating at ten Chebyshev points in
+ * double precision. Host only (no device is needed). EINVAL for C <= 0 or n < 10.
+ */
+int bssmppi_tyre_curve_coefficients(double C, float* h_c, int32_t n);
+
+/*
  * Measured FP32 arithmetic peak of the current device (no counterpart in the paper: the
  * denominator of the rollout kernel's roofline, which is bound by FP32 issue, not by memory or
  * tensor cores). Runs a grid of (blocks per SM at full occupancy) x SMs blocks of 256 threads, each

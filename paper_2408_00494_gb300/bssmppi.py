@@ -134,6 +134,8 @@ def load(build_if_missing: bool = True):
         "bssmppi_philox4x32_10": (ctypes.c_int, [vp, u64, vp, i64, vp]),
         "bssmppi_box_muller": (ctypes.c_int, [vp, vp, i64, vp]),
         "bssmppi_slip_atan": (ctypes.c_int, [vp, vp, i64, vp]),
+        "bssmppi_tyre_curve": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+        "bssmppi_tyre_curve_coefficients": (ctypes.c_int, [ctypes.c_double, vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -424,6 +426,18 @@ def philox4x32_10(ctr, seed: int, out, stream=None):
 
 def box_muller(words, z, stream=None):
     _check(load().bssmppi_box_muller(_ptr(words), _ptr(z), words.numel() // 2, _stream_handle(stream)))
+
+
+def tyre_curve(h, x, y, stream=None):
+    """y = sin(C atan x) as the substep evaluates it, for the handle's tyre shape factor C."""
+    _check(load().bssmppi_tyre_curve(h, _ptr(x), _ptr(y), x.numel(), _stream_handle(stream)), h)
+
+
+def tyre_curve_coefficients(C) -> np.ndarray:
+    """c_0..c_9 of the tyre curve's polynomial for shape factor C (host only)."""
+    c = np.zeros(10, np.float32)
+    _check(load().bssmppi_tyre_curve_coefficients(float(C), ctypes.c_void_p(c.ctypes.data), 10))
+    return c
 
 
 def slip_atan(t, y, stream=None):

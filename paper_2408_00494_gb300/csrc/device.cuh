@@ -2,6 +2,8 @@
 // the vehicle model, and the particle-moment merges. FP32 throughout; no FP64 on the device.
 #pragma once
 
+#include <type_traits>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -20,11 +22,13 @@ __host__ __device__ constexpr int model_s_index(int model) { return model == 0 ?
 // -l_r D_r / I_z, then fixed numbers: 1, -1 and the heading-rotation series' 1/24, -1/2, 1/120,
 // -1/6.
 // The wheel-speed model adds R_w, D_xf = mu_x F_zf, D_f, 1/m, -1/m, D_xr / m, D_r / m, l_f / I_z,
-// l_r D_r / I_z, -h R_w / I_w and -R_w D_xr / I_w (kFoldW*).
+// l_r D_r / I_z, -h R_w / I_w and -R_w D_xr / I_w (kFoldW*). B^2 and the coefficients c_0..c_9 of
+// the tyre curve's polynomial (tyre_curve below) follow.
+constexpr int kTyreDeg = 9;  // degree in x^2 of the tyre curve's polynomial
 enum : int {
     kFoldH, kFoldNH, kFoldLf, kFoldNLr, kFoldTB, kFoldNTB, kFoldTC, kFoldNDrM, kFoldNLrDrIz,
     kFoldWRw, kFoldWDxf, kFoldWDf, kFoldWInvM, kFoldWNInvM, kFoldWDxrM, kFoldWDrM, kFoldWLfIz, kFoldWLrDrIz,
-    kFoldWNhRwIw, kFoldWNRwDxrIw,
+    kFoldWNhRwIw, kFoldWNRwDxrIw, kFoldTB2, kFoldTy0, kFoldTyLast = kFoldTy0 + kTyreDeg,
     kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldN
 };
 
@@ -57,8 +61,8 @@ struct DevParams {
     float lambda, inv_lambda, nu, one_m_gamma, ctrl_w, Csafe, Cobs, wT;
     float xg[8], Q[8], Qf[8];
     // wheel-speed model: mu_x F_z per axle, wheel radius, 1 / wheel inertia, full-throttle drive
-    // torque, slip-denominator speed floor, and C B (the slope of the tyre curve at zero slip)
-    float Dxf, Dxr, Rw, inv_Iw, tau_max, slip_floor, CB;
+    // torque, slip-denominator speed floor
+    float Dxf, Dxr, Rw, inv_Iw, tau_max, slip_floor;
     float track_scale;               // n_track / track_len
     float Mf, invM, invM1;           // M, 1/M, 1/(M-1)
     float Df_m, lfDf_Iz;             // D_f / m and l_f D_f / I_z (per-step force factors)
@@ -360,6 +364,32 @@ __device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp,
     sp = s;
 }
 
+// The tyre curve of the simplified Pacejka law, sin(C atan x) for x = B alpha. For |x| <= 1 it is
+// x p(x^2), p the degree-9 polynomial that interpolates sin(C atan sqrt z) / sqrt z at the ten
+// Chebyshev points of [0, 1] (fitted on the host for the problem's C in double precision; its
+// coefficients are of the order of C, so Horner's rule in FP32 stays within about 2e-7 of the curve,
+// as accurate as the hardware sine it replaces); beyond, the library's atanf and the hardware sine
+// (|C atan x| < C pi / 2 < pi keeps the sine inside the range where its absolute error is at most
+// 2^-21.4). The choice is made per particle; the warp enters the library route only when one of its
+// particles needs it, so the common case is one uniform branch.
+__device__ __forceinline__ float tyre_curve_library(const DevParams& P, float x) { return __sinf(P.tC * atanf(x)); }
+
+template <typename V>
+__device__ __forceinline__ V tyre_curve(const DevParams& P, V x)
+{
+    const V z = vmul(x, x);
+    V p = fold<V>(P, kFoldTyLast);
+#pragma unroll
+    for (int d = kTyreDeg - 1; d >= 0; --d) p = vfma(p, z, fold<V>(P, kFoldTy0 + d));
+    V g = vmul(x, p);
+    bool far;
+    if constexpr (std::is_same<V, float2>::value) far = fabsf(x.x) > 1.0f || fabsf(x.y) > 1.0f;
+    else far = fabsf(x) > 1.0f;
+    if (__any_sync(__activemask(), far))
+        g = each(x, g, [&](float xv, float gv) { return fabsf(xv) > 1.0f ? tyre_curve_library(P, xv) : gv; });
+    return g;
+}
+
 // One explicit-Euler substep of one particle (V = float) or of two particles side by side
 // (V = float2: one issued instruction does each multiply-add for both). The transcendentals,
 // quotients and the curvature lookup are taken per particle. (sp, cp) = (sin e_psi, cos e_psi) on
@@ -369,7 +399,10 @@ __device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp,
 // to the state: v_x' = v_x + h (a - D_f sin(delta)/m g_f + v_y r), and so on, with g_f, g_r the
 // tyre curves' values sin(C atan(B alpha)).
 // TP: the object holding the track's scale and mask (P itself, or a serving item).
-template <typename V, typename Tab, typename TP>
+// POLY: the tyre curve from its polynomial (tyre_curve); otherwise the library's atanf and the
+// hardware sine for every particle, which measured faster where four particles share a lane and in
+// the server's batched kernels.
+template <bool POLY = true, typename V, typename Tab, typename TP>
 __device__ __forceinline__ void bicycle_substep(const DevParams& P, const TP& trk, const Tab* __restrict__ kap,
                                                 float s0, const SubstepCtl<V>& u, V (&X)[6], V& sp, V& cp)
 {
@@ -378,16 +411,19 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const TP& tr
     const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
     const V tf = vmul(vfma(fold<V>(P, kFoldLf), r, vy), ivx);    // (v_y + l_f r) / v_x
     const V tr = vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx);   // (v_y - l_r r) / v_x
-    const auto at = [](float a) { return atanf(a); };
     const auto slip = [](float a) { return slip_atan(a); };
     const V af = vfma(each(tf, slip), fold<V>(P, kFoldM1), u.steer);  // alpha_f
     const V bf = vmul(fold<V>(P, kFoldTB), af);                        // B alpha_f
     const V br = vmul(fold<V>(P, kFoldNTB), each(tr, slip));           // B alpha_r
-    // |C atan(B alpha)| < C pi / 2 < pi: inside the range where the hardware sine's absolute error
-    // is at most 2^-21.4 of the unit amplitude (a relative force error of a few FP32 ulps).
-    const auto sn = [](float a) { return __sinf(a); };
-    const V gf = each(vmul(fold<V>(P, kFoldTC), each(bf, at)), sn);   // F_f / D_f
-    const V gr = each(vmul(fold<V>(P, kFoldTC), each(br, at)), sn);   // F_r / D_r
+    V gf, gr;  // F_f / D_f, F_r / D_r
+    if constexpr (POLY) {
+        gf = tyre_curve(P, bf);
+        gr = tyre_curve(P, br);
+    } else {
+        const auto lib = [&](float a) { return tyre_curve_library(P, a); };
+        gf = each(bf, lib);
+        gr = each(br, lib);
+    }
     const V nk = each(X[5], [&](float a) { return -track_curvature(trk, kap, s0 + a); });  // -kappa(s)
     const V num = vfma(vx, cp, vmul(vmul(vy, sp), fold<V>(P, kFoldM1)));                // v_x cos - v_y sin
     const V den = vfma(nk, X[4], fold<V>(P, kFoldOne));                                 // 1 - kappa e_y
@@ -413,18 +449,33 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const TP& tr
 // g = sin(C atan(B s)) on the combined slip s = sqrt(kappa^2 + alpha^2), split along the slip
 // direction and scaled by the friction ellipse's axes: F_x = mu_x F_z g kappa / s,
 // F_y = mu F_z g alpha / s. Rear-wheel drive torque tau_max * throttle; static axle loads.
-// g(s) / s for the squared combined slip sl2 = s^2, which tends to C B at zero slip. One reciprocal
-// square root gives both s = sl2 / sqrt(sl2) and 1 / s. |C atan(B s)| < C pi / 2 < pi keeps the
-// hardware sine inside its accurate range. (At sl2 = 0 the reciprocal square root is infinite and
-// the product not a number: the select returns C B there.)
+// g(s) / s for the squared combined slip sl2 = s^2, which tends to C B at zero slip. While
+// (B s)^2 <= 1 it is B p(B^2 sl2) with the tyre curve's polynomial (g(b) = b p(b^2), b = B s): no
+// square root, and C B at zero slip by itself. Beyond, one reciprocal square root gives both
+// s = sl2 / sqrt(sl2) and 1 / s for the library arctangent and the hardware sine (|C atan(B s)| <
+// C pi / 2 < pi keeps the sine inside its accurate range). The choice is made per particle.
+__device__ __forceinline__ float tyre_ratio_beyond(const DevParams& P, float sl2, float z, float r)
+{
+    if (z > 1.0f) {
+        const float rs = rsqrtf(sl2);
+        r = __sinf(P.tC * atanf(P.tB * (sl2 * rs))) * rs;
+    }
+    return r;
+}
+
 template <typename V>
 __device__ __forceinline__ V tyre_ratio(const DevParams& P, V sl2)
 {
-    const V rs = each(sl2, [](float a) { return rsqrtf(a); });
-    const V b = vmul(fold<V>(P, kFoldTB), vmul(sl2, rs));
-    const V c = vmul(fold<V>(P, kFoldTC), each(b, [](float a) { return atanf(a); }));
-    const V g = vmul(each(c, [](float a) { return __sinf(a); }), rs);
-    return each(sl2, g, [&](float q, float gq) { return q > 1e-12f ? gq : P.CB; });
+    const V z = vmul(fold<V>(P, kFoldTB2), sl2);  // (B s)^2
+    V p = fold<V>(P, kFoldTyLast);
+#pragma unroll
+    for (int d = kTyreDeg - 1; d >= 0; --d) p = vfma(p, z, fold<V>(P, kFoldTy0 + d));
+    const V r = vmul(fold<V>(P, kFoldTB), p);
+    if constexpr (std::is_same<V, float2>::value) {
+        return make_float2(tyre_ratio_beyond(P, sl2.x, z.x, r.x), tyre_ratio_beyond(P, sl2.y, z.y, r.y));
+    } else {
+        return tyre_ratio_beyond(P, sl2, z, r);
+    }
 }
 
 // Per-step factors of the wheel-speed substep: steer, cos delta, sin delta, -sin delta and

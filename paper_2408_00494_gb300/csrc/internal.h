@@ -49,6 +49,10 @@ cudaError_t model_step_launch(const DevParams& dp, const float* x, const float* 
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st);
 cudaError_t box_muller_launch(const uint32_t* words, float* z, int64_t n, cudaStream_t st);
 cudaError_t slip_atan_launch(const float* t, float* y, int64_t n, cudaStream_t st);
+cudaError_t tyre_curve_launch(const DevParams& dp, const float* x, float* y, int64_t n, cudaStream_t st);
+// Coefficients c_0..c_9 of p with sin(C atan x) = x p(x^2) on |x| <= 1 (host, double precision;
+// c holds kTyreDeg + 1 = 10 floats).
+void tyre_curve_fit(double C, float* c);
 
 // Weights + update: the number of blocks for K samples, and the launch.
 int update_blocks(int K);

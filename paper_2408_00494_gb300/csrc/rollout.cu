@@ -132,6 +132,20 @@ __global__ void slip_atan_kernel(const float* __restrict__ t, float* __restrict_
     if (i < n) y[i] = slip_atan(t[i]);
 }
 
+__global__ void tyre_curve_kernel(const DevParams dp, const float* __restrict__ x, float* __restrict__ y, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = tyre_curve(dp, x[i]);
+}
+
+cudaError_t tyre_curve_launch(const DevParams& dp, const float* x, float* y, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    tyre_curve_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(dp, x, y, n);
+    return cudaGetLastError();
+}
+
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;

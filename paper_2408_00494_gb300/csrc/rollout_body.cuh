@@ -295,12 +295,14 @@ __host__ __device__ constexpr int roll_max_threads()
 // registers of their own. UTRIG: my_u holds (u_0, u_1, sin u_0, cos u_0) per step (T x 4), so the
 // steering angle's sine and cosine are taken once per step by the lanes that draw the controls
 // instead of by every lane in every step; otherwise T x 2.
+// TYRE_POLY: the bicycle's tyre curve from its polynomial where one or two particles share a lane
+// (the library route at four and more, and wherever TYRE_POLY is off, measured faster there).
 // IT: the object holding the per-solve fields (the sizes K, M, T, seg, spw, uniform, dist_half, M's
 // reciprocals, k_off), the Philox round keys and the track's scale and mask. The single-solve kernel
 // passes dp itself; the server passes a per-warp item in shared memory while dp, the constants its
 // batch's vehicles share, stays in kernel parameter space.
 template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float, bool PACK = true, bool UTRIG = false,
-          typename IT = DevParams>
+          typename IT = DevParams, bool TYRE_POLY = true>
 __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it, const RollIO& io,
                                                const Tab* __restrict__ kap_s, const float* __restrict__ v_s,
                                                float* __restrict__ my_u, int group, uint32_t ctr,
@@ -458,7 +460,8 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
             for (int j = 0; j < dp.n_sub; ++j) {
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    if constexpr (MODEL == 0) bicycle_substep(dp, it, kap_s, s0, sc, X[q], hs[q], hc[q]);
+                    if constexpr (MODEL == 0)
+                        bicycle_substep<TYRE_POLY && P <= 2>(dp, it, kap_s, s0, sc, X[q], hs[q], hc[q]);
                     else wheels_substep(dp, it, kap_s, s0, sc, X[q], hs[q], hc[q]);
                 }
             }

@@ -201,6 +201,49 @@ void bss::set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
 // Validates the parameters and derives the kernels' constants: lane mapping (seg, spw, P),
 // Cholesky factors, Sigma_eps^-1, the back-off nu, the Philox round keys and the model constants.
+// The tyre curve's polynomial: p(z) interpolates q(z) = sin(C atan sqrt z) / sqrt z at the ten
+// Chebyshev points z_k = (1 + cos(pi (k + 1/2) / 10)) / 2 of [0, 1] (q is analytic there, with its
+// nearest singularity at z = -1, so the interpolant is within about 4e-8 of it). The Chebyshev
+// coefficients come from the discrete cosine sums; the three-term recurrence
+// T_{j+1} = 2u T_j - T_{j-1} turns them into powers of u = 2z - 1, and the binomial expansion into
+// powers of z. Everything is in double precision; the coefficients are rounded to FP32 at the end.
+void bss::tyre_curve_fit(double C, float* c)
+{
+    constexpr int N = kTyreDeg + 1;
+    const double pi = 3.14159265358979323846;
+    double f[N], a[N];
+    for (int k = 0; k < N; ++k) {
+        const double z = 0.5 * (1.0 + std::cos(pi * (k + 0.5) / N));
+        f[k] = std::sin(C * std::atan(std::sqrt(z))) / std::sqrt(z);
+    }
+    for (int j = 0; j < N; ++j) {
+        double sum = 0.0;
+        for (int k = 0; k < N; ++k) sum += f[k] * std::cos(pi * j * (k + 0.5) / N);
+        a[j] = (j == 0 ? 1.0 : 2.0) * sum / N;
+    }
+    double pu[N] = {}, t0[N] = {}, t1[N] = {}, t2[N];
+    t0[0] = 1.0;
+    t1[1] = 1.0;
+    for (int i = 0; i < N; ++i) pu[i] = a[0] * t0[i] + a[1] * t1[i];
+    for (int j = 2; j < N; ++j) {
+        for (int i = 0; i < N; ++i) t2[i] = (i > 0 ? 2.0 * t1[i - 1] : 0.0) - t0[i];
+        for (int i = 0; i < N; ++i) {
+            pu[i] += a[j] * t2[i];
+            t0[i] = t1[i];
+            t1[i] = t2[i];
+        }
+    }
+    double pz[N] = {};
+    for (int i = 0; i < N; ++i) {  // pu_i (2z - 1)^i = pu_i sum_m binom(i, m) 2^m z^m (-1)^(i - m)
+        double binom = 1.0;
+        for (int m = 0; m <= i; ++m) {
+            pz[m] += pu[i] * binom * std::ldexp(1.0, m) * (((i - m) & 1) ? -1.0 : 1.0);
+            binom = binom * (i - m) / (m + 1);
+        }
+    }
+    for (int i = 0; i < N; ++i) c[i] = (float)pz[i];
+}
+
 int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::string& why)
 {
     int rc = validate(p, why);
@@ -249,7 +292,6 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
         d.inv_Iw = 1.0f / p->wheel_inertia;
         d.tau_max = p->tau_max;
         d.slip_floor = p->slip_floor;
-        d.CB = p->tire_C * p->tire_B;
     }
     d.umin0 = p->u_min[0]; d.umin1 = p->u_min[1]; d.umax0 = p->u_max[0]; d.umax1 = p->u_max[1];
     d.Le00 = (float)Le[0]; d.Le10 = (float)Le[2]; d.Le11 = (float)Le[3];
@@ -300,6 +342,10 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
         d.fold[kFoldWNhRwIw] = (float)(-(double)d.h * p->wheel_radius / p->wheel_inertia);
         d.fold[kFoldWNRwDxrIw] = (float)(-(double)p->wheel_radius * d.Dxr / p->wheel_inertia);
     }
+    d.fold[kFoldTB2] = (float)((double)p->tire_B * p->tire_B);
+    float tyre[kTyreDeg + 1];
+    tyre_curve_fit(p->tire_C, tyre);
+    for (int i = 0; i <= kTyreDeg; ++i) d.fold[kFoldTy0 + i] = tyre[i];
     for (int i = kFoldOne; i < kFoldN; ++i) d.fold[i] = fold_fixed(i);
     for (int i = 0; i < kFoldN; ++i) d.fold2[i] = make_float2(d.fold[i], d.fold[i]);
     return BSSMPPI_OK;
@@ -773,6 +819,24 @@ int bssmppi_slip_atan(const float* d_t, float* d_y, int64_t n, void* cuda_stream
     if (n < 0 || (n > 0 && (!d_t || !d_y))) return fail(nullptr, BSSMPPI_EINVAL, "bad arrays");
     cudaError_t e = bss::slip_atan_launch(d_t, d_y, n, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(nullptr, e, "slip_atan");
+}
+
+int bssmppi_tyre_curve(bssmppi_t h, const float* d_x, float* d_y, int64_t n, void* cuda_stream)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "NULL handle");
+    if (n < 0 || (n > 0 && (!d_x || !d_y))) return fail(h, BSSMPPI_EINVAL, "tyre_curve: bad arguments");
+    cudaError_t e = bss::tyre_curve_launch(h->dp, d_x, d_y, n, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(h, e, "tyre_curve");
+}
+
+int bssmppi_tyre_curve_coefficients(double C, float* h_c, int32_t n)
+{
+    if (!h_c || n < bss::kTyreDeg + 1 || !(C > 0.0) || !std::isfinite(C))
+        return fail(nullptr, BSSMPPI_EINVAL, "tyre_curve_coefficients: needs C > 0 and room for 10 coefficients");
+    float c[bss::kTyreDeg + 1];
+    bss::tyre_curve_fit(C, c);
+    for (int i = 0; i <= bss::kTyreDeg; ++i) h_c[i] = c[i];
+    return BSSMPPI_OK;
 }
 
 }  // extern "C"

@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(kServeWarps * kWarp, serve_min_blocks<P>())
         const float* v = ctrl_v + (size_t)rq.ctrl * 2 * T_max;
         RollIO io{rq.x0, nullptr, v, ctrl_ctr + rq.ctrl, arena + rq.off_S, arena + rq.off_eps, nullptr, nullptr};
         float* my_u = ubuf + (lane / rq.seg) * 2 * rq.T;
-        rollout_group<0, P, true, false, float, true, false, ServeItem>(fleet, *it, io, cd.kappa, v, my_u,
-                                                                        (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
+        rollout_group<0, P, true, false, float, true, false, ServeItem, false>(
+            fleet, *it, io, cd.kappa, v, my_u, (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
         __syncwarp();
     }
 }

@@ -162,6 +162,30 @@ def test_slip_angle_arctangent_within_an_ulp():
     assert np.array_equal(y[:n], -y[n:2 * n])
 
 
+@pytest.mark.parametrize("C", [1.9, 1.6])
+def test_tyre_curve_against_fp64(C):
+    """The substep's tyre curve sin(C atan x): the polynomial on |x| <= 1 within 4e-7 of FP64 (and
+    odd bit for bit), the library route beyond within 2e-6 (atanf's 2 ulp times C, plus the hardware
+    sine's 2^-21.4)."""
+    p = workload.wheels_problem(8, 4, 3) if C == 1.6 else workload.config0()
+    assert abs(p.tire_C - C) < 1e-12
+    c = bssmppi.Controller(p)
+    pos = np.linspace(0.0, 1.0, 1 << 18, dtype=np.float32)
+    inner = np.concatenate([pos, -pos])
+    outer = np.concatenate([np.geomspace(1.0, 1e4, 1 << 14), -np.geomspace(1.0, 1e4, 1 << 14)]).astype(np.float32)
+    outer = outer[np.abs(outer) > 1.0]
+    x = np.concatenate([inner, outer])
+    y = torch.zeros(x.size, device="cuda")
+    bssmppi.tyre_curve(c.h, _dev(x), y)
+    c.close()
+    y = y.cpu().numpy().astype(np.float64)
+    ref = np.sin(float(np.float32(C)) * np.arctan(x.astype(np.float64)))
+    n = inner.size
+    assert np.abs(y[:n] - ref[:n]).max() <= 4e-7, np.abs(y[:n] - ref[:n]).max()
+    assert np.abs(y[n:] - ref[n:]).max() <= 2e-6, np.abs(y[n:] - ref[n:]).max()
+    assert np.array_equal(y[:n // 2], -y[n // 2:n])
+
+
 @pytest.mark.parametrize("model", ["bicycle", "double_integrator"])
 def test_model_step_matches_oracle(model):
     if model == "bicycle":

@@ -4,7 +4,8 @@ A request's result is a deterministic function of its controller's state (nomina
 state estimate and its (K, M, T): alone or in a mix of other controllers' requests, with or without
 CUDA graphs, it must come out bit for bit the same, and equal to bssmppi_solve + bssmppi_shift on
 a single handle within the update tolerance (rel 1e-4 / abs 1e-5; the two update kernels add the
-weighted perturbations in different orders), with the same minimum trajectory cost bit for bit.
+weighted perturbations in different orders), with the minimum trajectory cost within the cost
+tolerance (the two evaluate the tyre curve differently where fewer than four particles share a lane).
 Served requests are also compared with the FP64 oracle sample by sample (costs, weights and
 perturbations read back through bssmppi_server_capture).
 """
@@ -122,10 +123,13 @@ def test_server_matches_single_solve(K, M, T):
     S = c.buffer(bssmppi.BUF_S).cpu().numpy()
     c.close()
     ref_u0, ref_v = u0.cpu().numpy(), v.cpu().numpy()
-    # The rollouts are the same arithmetic: the server steps bicycle particles one at a time, the
-    # solve two at a time in packed FP32 pairs, and each half of a pair rounds as the single
-    # particle does. So the minimum trajectory cost agrees bit for bit.
-    assert np.float32(got[3]) == S.min()
+    # The rollouts are the same arithmetic except the tyre curve: the single-solve kernel takes it
+    # from its polynomial where one or two particles share a lane, the server from the library's
+    # arctangent and sine (both within 4e-7 of sin(C atan x)). So the minimum trajectory cost agrees
+    # within the cost tolerance of the parity tests, and bit for bit where four particles share a lane.
+    if M > 64:
+        assert np.float32(got[3]) == S.min()
+    assert abs(float(got[3]) - float(S.min())) <= 1e-4 * max(1.0, abs(float(S.min())))
     assert np.all(np.abs(got[0] - ref_u0) <= 1e-5 + 1e-4 * np.abs(ref_u0))
     assert np.all(np.abs(got[1][:T] - ref_v) <= 1e-5 + 1e-4 * np.abs(ref_v))
     assert got[2] == ctr == 6
@@ -179,7 +183,7 @@ def test_two_constants_classes_batch_apart_and_match_their_single_solves():
             S = h.buffer(bssmppi.BUF_S).cpu().numpy()
         finally:
             h.close()
-        assert np.float32(together[c][3]) == S.min(), c
+        assert abs(float(together[c][3]) - float(S.min())) <= 1e-4 * max(1.0, abs(float(S.min()))), c
         ref_v = v.cpu().numpy()
         assert np.all(np.abs(together[c][1][:T] - ref_v) <= 1e-5 + 1e-4 * np.abs(ref_v)), c
 
