@@ -656,6 +656,18 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0 and args.closed_loop_steps > 0:
         line["closed_loop"] = run_closed_loop(bssmppi, _problem(args.workload), dev, stream, args.closed_loop_steps)
+        # the same loop where the workload's own disturbance never brings the car near the wall:
+        # disturbance x6, half-width 2 m, goal 12 m/s (the lap study's track and costs), with the
+        # benchmark's 64 particles per sample and with 4
+        stress = {}
+        for M in (64, 4):
+            ps = workload.racing_problem(4096, M, 40, track_seed=1, noise_scale=6.0, lam=1.0, seed=1, w_T=2.0,
+                                         x_goal=(12.0, 0.0, 0.0, 0.0, 0.0, 0.0))
+            stress[f"M{M}"] = run_closed_loop(bssmppi, ps, dev, stream, args.closed_loop_steps)
+            stress[f"M{M}"].pop("plant", None)
+        stress["setting"] = ("K=4096, T=40, disturbance std x6 of the small workload's, w_T = 2 m, goal 12 m/s, "
+                             "track seed 1; plant as in closed_loop")
+        line["closed_loop_stress"] = stress
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = run_serving(args)
     if rank == 0 and args.km_sweep:
