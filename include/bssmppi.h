@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define BSSMPPI_ABI_VERSION 2u
+#define BSSMPPI_ABI_VERSION 3u
 #define BSSMPPI_NU 2          /* controls: [steer delta (rad), acceleration (m/s^2)] */
 #define BSSMPPI_NX_MAX 8          /* states: 6 (bicycle), 4 (double integrator), 8 (wheel speeds) */
 #define BSSMPPI_K_MAX (1 << 20)
@@ -93,7 +93,7 @@ typedef struct bssmppi_params {
     float wheel_radius, wheel_inertia, mu_x, tau_max, slip_floor;
     float u_min[2], u_max[2];  /* control bounds; sampled controls are clamped to them */
     float lambda;         /* temperature, > 0 */
-    float delta;          /* per-boundary chance level, 0 < delta < 0.5; nu = sqrt(2) erfinv(1 - 2 delta) */
+    float delta;          /* per-boundary chance level, 0 < delta < 0.5; nu from `backoff` below */
     float gamma;          /* DCBF decay rate, 0 < gamma < 1 */
     float ctrl_w;         /* weight of v_t^T Sigma_eps^-1 u_t in S */
     float C_safe;         /* weight C of the safe-condition violation cost */
@@ -114,6 +114,11 @@ typedef struct bssmppi_params {
                              re-drawn from N(mean_k, Sigma_k), the Monte-Carlo moments of step k (full
                              covariance, PSD Cholesky), with Philox stream 4. Needs compensated = 1; not
                              available to the shield repair or the server (BSSMPPI_ENOTSUP there). */
+    int32_t backoff;      /* back-off of the racing barrier (Remark 1): 0 Gaussian nu = sqrt(2) erfinv(1 - 2 delta),
+                             exact for a Gaussian belief; 1 Cantelli nu = sqrt((1 - delta) / delta), which holds
+                             for any belief with that mean and variance */
+    int32_t clamp_margin; /* 0: h = (w_T - nu sigma)^2 - mean_ey^2 as Eq. "DCBF" writes it (it grows again once
+                             nu sigma > w_T); 1: h = max(w_T - nu sigma, 0)^2 - mean_ey^2, non-increasing in sigma */
 } bssmppi_params;
 
 /*

@@ -46,6 +46,7 @@ class OrcProblem(ctypes.Structure):
         ("kappa", _dp), ("n_track", ctypes.c_int), ("track_len", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("crn_disturbance", ctypes.c_int), ("resample", ctypes.c_int),
         ("n_con", ctypes.c_int), ("con", ctypes.POINTER(OrcConstraint)),
+        ("backoff", ctypes.c_int), ("clamp_margin", ctypes.c_int),
     ]
 
 
@@ -127,6 +128,8 @@ class Oracle:
         p = OrcProblem()
         for name in ("K", "M", "T", "n_sub", "model", "ey_index", "crn_disturbance", "resample"):
             setattr(p, name, int(getattr(prob, name)))
+        p.backoff = int(getattr(prob, "backoff", 0))
+        p.clamp_margin = int(getattr(prob, "clamp_margin", 0))
         for name in ("dt", "mass", "Iz", "lf", "lr", "tire_B", "tire_C", "mu", "g", "vx_floor",
                      "wheel_radius", "wheel_inertia", "mu_x", "tau_max", "slip_floor",
                      "delta", "gamma", "ctrl_w", "C_safe", "C_obs", "w_T"):

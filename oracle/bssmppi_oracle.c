@@ -351,13 +351,21 @@ static void draw_disturbance(const orc_problem* p, int nx, uint32_t t, uint32_t 
 }
 
 /* Belief barrier, Eq. "DCBF": h = (w_T - nu sigma_y)^2 - mean_ey^2 with sigma_y^2 the (e_y, e_y)
- * entry of the covariance (eta = gradient of the boundary constraint = unit vector on e_y). */
+ * entry of the covariance (eta = gradient of the boundary constraint = unit vector on e_y). With
+ * clamp_margin the margin w_T - nu sigma_y is taken as 0 once the back-off exceeds the half-width. */
 static double belief_h(const orc_problem* p, double nu, const double* mean, const double* cov, int nx)
 {
     int e = p->ey_index;
     double sig = sqrt(fmax(cov[e * nx + e], 0.0));
     double b = p->w_T - nu * sig;
+    if (p->clamp_margin && b < 0.0) b = 0.0;
     return b * b - mean[e] * mean[e];
+}
+
+/* Remark 1: the back-off of the racing barrier for the chance level delta. */
+static double racing_nu(const orc_problem* p)
+{
+    return p->backoff ? orc_backoff_cantelli(p->delta) : orc_backoff_gaussian(p->delta);
 }
 
 /* c_i(x) of one constraint and its gradient eta = grad c_i(x) (Assumption 1). */
@@ -440,7 +448,7 @@ int orc_rollout_threads(const orc_problem* p, const double* x0, const double* Si
     double det = p->Sigma_eps[0] * p->Sigma_eps[3] - p->Sigma_eps[1] * p->Sigma_eps[2];
     Sinv[0] = p->Sigma_eps[3] / det; Sinv[1] = -p->Sigma_eps[1] / det;
     Sinv[2] = -p->Sigma_eps[2] / det; Sinv[3] = p->Sigma_eps[0] / det;
-    const double nu = orc_backoff_gaussian(p->delta);
+    const double nu = racing_nu(p);
 
     /* The samples are independent until the weights (Algorithm 1 rolls each one out on its own),
      * so with n_threads > 1 (and an OpenMP build) threads take whole samples; every sample's
@@ -668,7 +676,7 @@ double orc_repair_objective(const orc_problem* p, const double* x0, const double
     if (p->model == 2 || M < 2 || T < 1) return NAN;
     double L_w[64];
     cholesky_psd(nx, p->Sigma_w, L_w);
-    const double nu = orc_backoff_gaussian(p->delta);
+    const double nu = racing_nu(p);
     double* X = (double*)malloc(sizeof(double) * (size_t)(T + 1) * M * nx);
     double* mean = (double*)calloc((size_t)(T + 1), sizeof(double));
     double* sig = (double*)calloc((size_t)(T + 1), sizeof(double));
@@ -702,6 +710,7 @@ double orc_repair_objective(const orc_problem* p, const double* x0, const double
         mean[t + 1] = mu_e;
         sig[t + 1] = sqrt(q / (M - 1));
         double b = p->w_T - nu * sig[t + 1];
+        if (p->clamp_margin && b < 0.0) b = 0.0;
         hz[t + 1] = b * b - mu_e * mu_e;
     }
     double J = 0.0;
@@ -720,7 +729,9 @@ double orc_repair_objective(const orc_problem* p, const double* x0, const double
             if (t + 1 <= T && arg[t + 1] > 0.0) gh += p->C_safe * (1.0 - p->gamma);
             if (gh != 0.0) {
                 double dh_dmean = -2.0 * mean[t];
-                double dh_dsig = -2.0 * nu * (p->w_T - nu * sig[t]);
+                double margin = p->w_T - nu * sig[t];
+                if (p->clamp_margin && margin < 0.0) margin = 0.0;  /* the clamped margin has no slope in sigma */
+                double dh_dsig = -2.0 * nu * margin;
                 for (int n = 0; n < M; ++n) {
                     double en = X[((size_t)t * M + n) * nx + e];
                     double g = dh_dmean / M;

@@ -59,6 +59,8 @@ typedef struct orc_problem {
                              re-drawn from N(xbar_k, Sigma_k) (stream 4); 0: persistent particles */
     int n_con;            /* 0: the racing barrier of Eq. "DCBF"; > 0: the general set, Eq. "DCBFchoice" */
     const orc_constraint* con;
+    int backoff;          /* racing barrier's nu (Remark 1): 0 Gaussian, 1 Cantelli */
+    int clamp_margin;     /* 1: h = max(w_T - nu sigma, 0)^2 - mean_ey^2; 0: as Eq. "DCBF" writes it */
 } orc_problem;
 
 /* Per-solve outputs; any pointer may be NULL. Sizes: S[K], u[K*T*2] (clamped samples), w[K]

@@ -47,6 +47,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("crn_disturbance", ctypes.c_int32), ("compensated", ctypes.c_int32),
         ("record_moments", ctypes.c_int32), ("resample", ctypes.c_int32),
+        ("backoff", ctypes.c_int32), ("clamp_margin", ctypes.c_int32),
     ]
 
 
@@ -212,6 +213,8 @@ def make_params(prob, record_moments: bool = False, compensated: bool | None = N
     p.compensated = int(prob.compensated if compensated is None else compensated)
     p.record_moments = int(record_moments)
     p.resample = int(getattr(prob, "resample", 0))
+    p.backoff = int(getattr(prob, "backoff", 0))
+    p.clamp_margin = int(getattr(prob, "clamp_margin", 0))
     return p
 
 

@@ -51,6 +51,7 @@ struct DevParams {
     int K_norm;       // samples of the whole (possibly sharded) solve: K unless sharded
     int lw_diag;      // 1: Sigma_w is diagonal, so its Cholesky factor is (the disturbance needs nx products)
     int dist_half;    // H = 2^ceil(log2 M) / 2: particles n and n + H share a disturbance counter (6 states)
+    int clamp_margin; // 1: the racing barrier's margin w_T - nu sigma is clamped at 0
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];       // Philox round keys k + r W (the key schedule, precomputed)
     float dt, h, inv_m, inv_Iz, lf, lr, tB, tC, Df, Dr, vx_floor;
@@ -702,7 +703,8 @@ __device__ __forceinline__ float state_cost(const DevParams& P, const float* W, 
 // Belief barrier h = (w_T - nu sigma)^2 - m_ey^2.
 __device__ __forceinline__ float belief_barrier(const DevParams& P, float mean_ey, float var_ey)
 {
-    const float b = P.wT - P.nu * sqrtf(fmaxf(var_ey, 0.0f));
+    float b = P.wT - P.nu * sqrtf(fmaxf(var_ey, 0.0f));
+    if (P.clamp_margin) b = fmaxf(b, 0.0f);
     return b * b - mean_ey * mean_ey;
 }
 

@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
             float h_prev = belief_barrier(dp, mean_s[0], 0.0f);
             float J = 0.0f;
             for (int t = 1; t <= T; ++t) {
-                const float b = dp.wT - dp.nu * sig_s[t];
+                float b = dp.wT - dp.nu * sig_s[t];
+                if (dp.clamp_margin) b = fmaxf(b, 0.0f);
                 const float h = b * b - mean_s[t] * mean_s[t];
                 const float a = fmaf(dp.one_m_gamma, h_prev, -h);
                 arg_s[t] = a;
@@ -191,7 +192,9 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
                 const float mt = mean_s[t], st = sig_s[t];
                 float term = -2.0f * mt * dp.invM;
                 if (st > 0.0f) {
-                    const float dh_dsig = -2.0f * dp.nu * (dp.wT - dp.nu * st);
+                    float margin = dp.wT - dp.nu * st;
+                    if (dp.clamp_margin) margin = fmaxf(margin, 0.0f);  // a clamped margin has no slope in sigma
+                    const float dh_dsig = -2.0f * dp.nu * margin;
                     term += dh_dsig * (ey_t - mt) * dp.invM1 / st;
                 }
                 g[EY] += gh * term;

@@ -271,6 +271,14 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     d.n_sub = p->model == BSSMPPI_MODEL_DOUBLE_INT4 ? 1 : p->n_sub;
     d.ey = p->ey_index; d.crn = p->crn_disturbance ? 1 : 0; d.record = p->record_moments ? 1 : 0;
     d.resample = p->resample ? 1 : 0;
+    if (p->backoff != BSSMPPI_BACKOFF_GAUSSIAN && p->backoff != BSSMPPI_BACKOFF_CANTELLI) {
+        why = "backoff must be 0 (Gaussian) or 1 (Cantelli)";
+        return BSSMPPI_EINVAL;
+    }
+    if (p->clamp_margin != 0 && p->clamp_margin != 1) {
+        why = "clamp_margin must be 0 or 1";
+        return BSSMPPI_EINVAL;
+    }
     d.k_off = 0;
     d.K_norm = p->K;
     d.key0 = (uint32_t)(p->seed & 0xffffffffu); d.key1 = (uint32_t)(p->seed >> 32);
@@ -308,7 +316,10 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
         }
     d.lambda = p->lambda;
     d.inv_lambda = 1.0f / p->lambda;
-    d.nu = (float)(std::sqrt(2.0) * inverse_erf(1.0 - 2.0 * (double)p->delta));
+    d.nu = p->backoff == BSSMPPI_BACKOFF_CANTELLI
+             ? (float)std::sqrt((1.0 - (double)p->delta) / (double)p->delta)
+             : (float)(std::sqrt(2.0) * inverse_erf(1.0 - 2.0 * (double)p->delta));
+    d.clamp_margin = p->clamp_margin ? 1 : 0;
     d.one_m_gamma = 1.0f - p->gamma;
     d.ctrl_w = p->ctrl_w; d.Csafe = p->C_safe; d.Cobs = p->C_obs; d.wT = p->w_T;
     d.mean_mask = 0;

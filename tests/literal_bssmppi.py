@@ -113,7 +113,10 @@ def solve(P, x0, v, ctr):
     nu = P["nu"]
 
     def h_of(mean, cov):
-        return (P["w_T"] - nu * math.sqrt(max(cov[e][e], 0.0))) ** 2 - mean[e] ** 2
+        margin = P["w_T"] - nu * math.sqrt(max(cov[e][e], 0.0))
+        if P.get("clamp_margin") and margin < 0.0:
+            margin = 0.0
+        return margin ** 2 - mean[e] ** 2
 
     def cost(W, mean):
         c = sum(W[i] * (mean[i] - P["x_goal"][i]) ** 2 for i in range(nx))
@@ -174,4 +177,5 @@ def problem_dict(prob, nu):
         gamma=f(prob.gamma), ctrl_w=f(prob.ctrl_w), C_safe=f(prob.C_safe), C_obs=f(prob.C_obs),
         w_T=f(prob.w_T), x_goal=[f(x) for x in prob.x_goal], Q=[f(x) for x in prob.Q],
         Qf=[f(x) for x in prob.Qf], ey_index=prob.ey_index, kappa=[float(k) for k in prob.kappa],
-        track_len=f(prob.track_len), seed=int(prob.seed), crn=int(prob.crn_disturbance), nu=nu)
+        track_len=f(prob.track_len), seed=int(prob.seed), crn=int(prob.crn_disturbance), nu=nu,
+        clamp_margin=int(getattr(prob, "clamp_margin", 0)))

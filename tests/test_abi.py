@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_params_layout_and_version():
     L = bssmppi.load()
-    assert L.bssmppi_abi_version() == 2
+    assert L.bssmppi_abi_version() == 3
     assert L.bssmppi_params_size() == ctypes.sizeof(bssmppi.Params)
 
 
@@ -58,6 +58,11 @@ def test_invalid_parameters_rejected_on_host():
     prm = bssmppi.make_params(p)
     prm.Sigma_w[0] = -1.0
     assert L.bssmppi_create(ctypes.byref(prm), None, ctypes.byref(ctypes.c_void_p())) == -1
+    for field, bad in (("backoff", 2), ("backoff", -1), ("clamp_margin", 3)):
+        prm = bssmppi.make_params(p)
+        setattr(prm, field, bad)
+        assert L.bssmppi_create(ctypes.byref(prm), None, ctypes.byref(ctypes.c_void_p())) == -1, field
+        assert field in bssmppi.last_error(None)
     for resample, compensated in ((2, 1), (1, 0)):  # re-sampling runs with compensated reductions only
         prm = bssmppi.make_params(p)
         prm.resample, prm.compensated = resample, compensated

@@ -325,6 +325,23 @@ def test_solve_degenerate_settings(case):
         assert ess >= bound * (1 - 1e-5)
 
 
+@pytest.mark.parametrize("backoff,clamp", [(1, 0), (0, 1), (1, 1)])
+def test_solve_backoff_and_clamped_margin(backoff, clamp):
+    """Remark 1's Cantelli back-off and the clamped barrier margin max(w_T - nu sigma, 0) against the
+    oracle: a 1 m half-width with a lateral disturbance of 0.1 m per step, so that Cantelli's
+    back-off (nu = 4.36) passes the half-width within the horizon and the clamp decides h."""
+    p = workload.config0()
+    p.K, p.M, p.T = 256, 32, 20
+    p.w_T, p.backoff, p.clamp_margin = 1.0, backoff, clamp
+    p.Sigma_w = np.diag(np.array([0.02, 0.02, 0.01, 0.002, 0.1, 0.0]) ** 2)
+    x0 = workload.random_state(p, 41)
+    x0[3], x0[4] = 0.0, 0.0
+    g, ref = check_solve(p, x0, workload.random_nominal(p, 41), ctr=12)
+    if backoff:
+        nu = float(np.sqrt((1 - np.float32(p.delta)) / np.float32(p.delta)))
+        assert np.any(nu * np.sqrt(ref["cov"][:, :, 4, 4]) > 1.0)  # the margin is negative somewhere
+
+
 def test_solve_ragged_K_and_long_horizon():
     p = workload.config1()
     p.K, p.M, p.T = 1001, 64, 40

@@ -19,6 +19,15 @@ from paper_2408_00494_gb300 import bssmppi  # noqa: E402
 
 
 def _case(model):
+    if model == "racing_cantelli_clamped":
+        # Cantelli's back-off (nu = 4.36) on a 0.8 m half-width: nu sigma passes w_T on 17 of the 40
+        # steps, so the clamped margin (and its zero slope in sigma) carries much of the penalty
+        p = workload.config1()
+        p.K, p.w_T, p.backoff, p.clamp_margin = 64, 0.8, 1, 1
+        x0 = np.array([10.0, 0.1, 0.05, 0.05, 0.6, 5.0], np.float32)
+        v = np.zeros((p.T, 2), np.float32)
+        v[:, 0] = 0.043
+        return p, x0, v
     if model == "racing":
         p = workload.config1()
         p.K = 64
@@ -41,10 +50,10 @@ def _gpu_grad(c, x0, v):
     return float(J.item()), g.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("model", ["racing", "double_integrator"])
+@pytest.mark.parametrize("model", ["racing", "double_integrator", "racing_cantelli_clamped"])
 def test_repair_gradient_matches_oracle_adjoint_and_finite_differences(model):
     p, x0, v = _case(model)
-    ctr = 17
+    ctr = 19 if model == "racing_cantelli_clamped" else 17
     o = oracle.Oracle(p)
     J_ref, g_ref, args = o.repair_objective(x0, v.astype(np.float64), ctr, grad=True, want_args=True)
     assert J_ref > 0.0 and np.min(np.abs(args[1:])) > 1e-2

@@ -201,6 +201,34 @@ def test_oracle_matches_literal_brute_force(case):
     np.testing.assert_allclose(r["w"], W, rtol=1e-10, atol=1e-15)
 
 
+@pytest.mark.parametrize("backoff,clamp", [(1, 0), (0, 1), (1, 1)])
+def test_backoff_and_clamped_margin_match_the_literal_restatement(backoff, clamp):
+    """Remark 1's Cantelli back-off nu = sqrt((1 - delta) / delta) (computed here from delta, not by
+    the oracle) and the clamped margin max(w_T - nu sigma, 0) against the pure-Python restatement,
+    on a case where the back-off exceeds the half-width at some steps (large disturbance, narrow
+    track), so the clamp is active."""
+    p = workload.config0()
+    p.K, p.M, p.T = 3, 4, 4
+    p.backoff, p.clamp_margin = backoff, clamp
+    p.w_T = 0.4
+    p.Sigma_w = np.diag(np.array([0.02, 0.02, 0.01, 0.002, 0.3, 0.0]) ** 2)
+    x0 = workload.random_state(p, 9)
+    x0[4] = 0.1
+    v = workload.random_nominal(p, 10)
+    r = oracle.Oracle(p).solve(x0, v, ctr=31, want_cov=True)
+    d = float(np.float32(p.delta))
+    nu = math.sqrt((1.0 - d) / d) if backoff else oracle.backoff_gaussian(d)
+    P = lit.problem_dict(p, nu)
+    S, U, MEAN, COV, VP, W = lit.solve(P, [float(x) for x in x0], v.astype(float).tolist(), 31)
+    np.testing.assert_allclose(r["S"], S, rtol=1e-11)
+    np.testing.assert_allclose(r["v_plus"], VP, rtol=1e-11, atol=1e-14)
+    sig = np.sqrt(r["cov"][:, :, 4, 4])
+    assert np.any(nu * sig > float(np.float32(p.w_T)))  # the back-off passes the half-width somewhere
+    if clamp:  # there the barrier is minus the squared mean, exactly
+        wide = nu * sig >= float(np.float32(p.w_T))
+        np.testing.assert_array_equal(r["h"][wide], -r["mean"][:, :, 4][wide] ** 2)
+
+
 def _repair_case(model):
     if model == "racing":
         p = workload.config0()

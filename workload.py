@@ -112,6 +112,8 @@ class Problem:
     resample: int = 0                # 1: re-draw particles from N(mean, cov) before every step (Alg. 2 literal)
     constraints: tuple = ()          # general constraint set (halfspace()/disk() entries); () = racing barrier
     compensated: int = 1
+    backoff: int = 0                 # racing barrier's nu: 0 Gaussian, 1 Cantelli (Remark 1)
+    clamp_margin: int = 0            # 1: h = max(w_T - nu sigma, 0)^2 - mean_ey^2
 
     @property
     def nx(self) -> int:
