@@ -80,3 +80,16 @@ def test_no_cpu_fallback_without_gpu():
     rc = L.bssmppi_create(ctypes.byref(prm), None, ctypes.byref(h))
     assert rc == -3  # ECUDA: the library refuses to run anywhere but on a CUDA device
     assert "CUDA" in bssmppi.last_error(None) or "device" in bssmppi.last_error(None)
+
+
+def test_measurement_and_checking_entry_points_validate_arguments_on_host():
+    """Argument errors come back as EINVAL before any CUDA call, so they need no GPU."""
+    L = bssmppi.load()
+    ms, tf, sms = ctypes.c_float(), ctypes.c_double(), ctypes.c_int32()
+    for iters in (0, (1 << 24) + 1):
+        rc = L.bssmppi_fp32_peak(0, iters, None, ctypes.byref(ms), ctypes.byref(tf), ctypes.byref(sms))
+        assert rc == -1 and "iters" in bssmppi.last_error(None)
+    assert L.bssmppi_fp32_peak(0, 16, None, None, ctypes.byref(tf), ctypes.byref(sms)) == -1
+    assert L.bssmppi_tyre_curve(None, None, None, 4, None) == -1
+    c = (ctypes.c_float * 10)()
+    assert L.bssmppi_tyre_curve_coefficients(1.9, c, 9) == -1  # room for fewer than ten coefficients

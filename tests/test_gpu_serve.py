@@ -250,6 +250,31 @@ def test_served_requests_match_the_oracle():
               f"indicator-margin exclusions {(~ok).sum()}")
 
 
+def test_capture_that_does_not_fit_copies_nothing():
+    """A capture buffer smaller than K (2 + 2T) floats reports -1 and is left untouched; the request
+    itself completes normally, and a later capture of the controller works."""
+    s, _ = _server(1)
+    try:
+        bssmppi.server_set_state(s, 0, _v0(0), 3)
+        small = bssmppi.server_capture(s, 0, 64, 20)  # room for K = 64, T = 20
+        small.buf[:] = 7.0
+        bssmppi.server_submit(s, 0, _x0(0), 512, 16, 20, req_id=1)
+        bssmppi.server_drain(s, 60000)
+        res = bssmppi.server_poll(s)
+        assert [r.status for r in res] == [0]
+        assert small.written.value == -1 and np.all(small.buf == 7.0)
+        with pytest.raises(bssmppi.BssmppiError):
+            small.result(512, 20)
+        ok = bssmppi.server_capture(s, 0, 512, 20)
+        bssmppi.server_submit(s, 0, _x0(0), 512, 16, 20, req_id=2)
+        bssmppi.server_drain(s, 60000)
+        bssmppi.server_poll(s)
+        S, w, eps = ok.result(512, 20)
+        assert abs(float(w.sum()) - 1.0) < 1e-5 and np.all(np.isfinite(S)) and eps.shape == (512, 20, 2)
+    finally:
+        bssmppi.server_destroy(s)
+
+
 def test_newer_request_replaces_pending_one_and_every_request_gets_a_result():
     s, _ = _server(2, max_batch=1, slots=1)
     try:
