@@ -16,6 +16,26 @@ constexpr int kNxMax = 8;
 __host__ __device__ constexpr int model_nx(int model) { return model == 0 ? 6 : (model == 2 ? 8 : 4); }
 __host__ __device__ constexpr int model_s_index(int model) { return model == 0 ? 5 : (model == 2 ? 7 : -1); }
 
+// Sets of states as bit masks (bit i: state i). A rollout compiled for a fixed set of cost-weighted
+// states (the racing cost weights v_x, e_psi and e_y of the bicycle) merges and costs only those
+// belief means; mask 0 stands for a set known at run time only.
+constexpr int kRacingCostMask = (1 << 0) | (1 << 3) | (1 << 4);
+__host__ __device__ constexpr int mask_count(int m)
+{
+    int n = 0;
+    for (int i = 0; i < 32; ++i) n += (m >> i) & 1;
+    return n;
+}
+__host__ __device__ constexpr int mask_nth(int m, int j)  // index of the j-th set bit of m (-1: none)
+{
+    for (int i = 0; i < 32; ++i)
+        if ((m >> i) & 1) {
+            if (j == 0) return i;
+            --j;
+        }
+    return -1;
+}
+
 // Everything a solve's kernels need, derived on the host at create time and passed by value
 // (kernel parameter space), so several controllers can run concurrently without global state.
 // Constant operands of the bicycle substep: the model's h, -h, l_f, -l_r, B, -B, C, -D_r / m,
@@ -687,17 +707,20 @@ __device__ __forceinline__ void model_step(const DevParams& P, const float* __re
 
 // ---------------------------------------------------------------------------------------------
 // Running / terminal cost on the belief mean: (m - x_g)^T W (m - x_g) + C_obs 1[|m_ey| > w_T].
+// MM != 0: only the states of MM carry weight (W_i = 0 elsewhere, so the skipped terms add exact
+// zeros) and only their means are read.
 // ---------------------------------------------------------------------------------------------
-template <int NX>
+template <int NX, int EY, int MM = 0>
 __device__ __forceinline__ float state_cost(const DevParams& P, const float* W, const float (&m)[NX])
 {
     float c = 0.0f;
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
+        if (MM != 0 && !((MM >> i) & 1)) continue;
         const float d = m[i] - P.xg[i];
         c = fmaf(W[i] * d, d, c);
     }
-    return c + (fabsf(m[P.ey]) > P.wT ? P.Cobs : 0.0f);
+    return c + (fabsf(m[EY]) > P.wT ? P.Cobs : 0.0f);
 }
 
 // Belief barrier h = (w_T - nu sigma)^2 - m_ey^2.

@@ -18,6 +18,7 @@ struct RollLaunch {
     int grid = 1;      // blocks (at most one per SM)
     int wpb = 1;       // warps per block
     size_t smem = 0;   // dynamic shared memory per block
+    int cost_mask = 0; // states the kernel merges and costs, fixed at compile time (0: set at run time)
 };
 constexpr int kTailMaxBlocks = 256;  // grid bound of the fused rollout (one block per SM)
 

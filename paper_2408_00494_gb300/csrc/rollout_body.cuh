@@ -31,14 +31,17 @@ struct RollIO {
 
 // Moments of the M particles of one sample. x[p] is particle ls + seg p (valid iff < M).
 // mean[i] = particle mean, var[i] = unbiased variance 1/(M-1) sum (x - mean)^2 (Algorithm 2);
-// var is produced for EY only unless all_var. With equal counts on every lane and no recording,
-// all means are merged; otherwise means outside dp.mean_mask (states no cost term weights) are not
-// merged across lanes and are left lane-local.
+// var is produced for EY only unless all_var. Means outside the merged set are left lane-local (or,
+// with MM != 0, untouched). The merged set: MM when it is nonzero (a kernel compiled for a fixed
+// set of cost-weighted states, never recording); otherwise every state with equal counts on every
+// lane and no recording, else dp.mean_mask (the states some cost term weights).
 // IT: the object holding the sample's sizes (M, uniform, Mf, invM, invM1): dp itself, or a serving item.
-template <int NX, int EY, int P, bool COMP, typename IT>
+template <int NX, int EY, int P, bool COMP, int MM, typename IT>
 __device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it, const float (&x)[P][NX], int ls,
                                                int seg, bool all_var, float (&mean)[NX], float (&var)[NX])
 {
+    static_assert(MM == 0 || ((MM >> EY) & 1), "the barrier reads the mean of e_y");
+    const int mmask = MM != 0 ? MM : dp.mean_mask;
     if constexpr (COMP) {
         // Per lane: exact two-pass mean and M2 over its (at most P) particles.
         float cnt = 0.0f;
@@ -52,6 +55,8 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it
         float m2[NX];
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
+            m2[i] = 0.0f;
+            if (MM != 0 && !((MM >> i) & 1)) continue;
             float s = 0.0f;
 #pragma unroll
             for (int p = 0; p < P; ++p) s += (it.uniform || ls + seg * p < it.M) ? x[p][i] : 0.0f;
@@ -72,38 +77,53 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it
             // Equal counts on every lane: merging two halves of n each gives mean = (mean_a +
             // mean_b) / 2 and M2 = M2_a + M2_b + (mean_b - mean_a)^2 n / 2. The lanes carry the sums
             // 2^r mean after r merges instead (scaling by a power of two is exact, so every rounding
-            // is the same), which saves a multiply per value and round; all means are merged,
-            // two states per packed add, and M2 for e_y only.
-            float sm[NX];
+            // is the same), which saves a multiply per value and round; the merged means are added
+            // two per packed add, and M2 for e_y only. A full warp's five rounds are unrolled, with
+            // their scales and counts as constants.
+            constexpr int UM = MM != 0 ? MM : (1 << NX) - 1;
+            constexpr int NM = mask_count(UM);
+            constexpr int JE = mask_count(UM & ((1 << EY) - 1));  // position of e_y among the merged
+            float sm[NM];
 #pragma unroll
-            for (int i = 0; i < NX; ++i) sm[i] = mean[i];
-            float m2e = m2[EY], scale = 1.0f;
-            for (int off = seg >> 1; off > 0; off >>= 1) {
-                float sb[NX];
+            for (int j = 0; j < NM; ++j) sm[j] = mean[mask_nth(UM, j)];
+            float m2e = m2[EY];
+            auto merge_round = [&](int off, float scale, float half_n) {
+                float sb[NM];
 #pragma unroll
-                for (int i = 0; i < NX; ++i) sb[i] = __shfl_xor_sync(0xffffffffu, sm[i], off);
-                const float d = (sb[EY] - sm[EY]) * scale;
+                for (int j = 0; j < NM; ++j) sb[j] = __shfl_xor_sync(0xffffffffu, sm[j], off);
+                const float d = (sb[JE] - sm[JE]) * scale;
                 const float m2b = __shfl_xor_sync(0xffffffffu, m2e, off);
-                m2e = fmaf(d * d, 0.5f * cnt, m2e + m2b);
+                m2e = fmaf(d * d, half_n, m2e + m2b);
 #pragma unroll
-                for (int i = 0; i + 1 < NX; i += 2) {
-                    const float2 a = __fadd2_rn(make_float2(sm[i], sm[i + 1]), make_float2(sb[i], sb[i + 1]));
-                    sm[i] = a.x;
-                    sm[i + 1] = a.y;
+                for (int j = 0; j + 1 < NM; j += 2) {
+                    const float2 a = __fadd2_rn(make_float2(sm[j], sm[j + 1]), make_float2(sb[j], sb[j + 1]));
+                    sm[j] = a.x;
+                    sm[j + 1] = a.y;
                 }
-                if constexpr (NX % 2 == 1) sm[NX - 1] = __fadd_rn(sm[NX - 1], sb[NX - 1]);
-                scale *= 0.5f;
-                cnt *= 2.0f;
+                if constexpr (NM % 2 == 1) sm[NM - 1] = __fadd_rn(sm[NM - 1], sb[NM - 1]);
+            };
+            float scale;
+            if (seg == kWarp) {
+#pragma unroll
+                for (int r = 0; r < 5; ++r) merge_round(16 >> r, 1.0f / (float)(1 << r), 0.5f * (float)(P << r));
+                scale = 1.0f / (float)kWarp;
+            } else {
+                scale = 1.0f;
+                for (int off = seg >> 1; off > 0; off >>= 1) {
+                    merge_round(off, scale, 0.5f * cnt);
+                    scale *= 0.5f;
+                    cnt *= 2.0f;
+                }
             }
 #pragma unroll
-            for (int i = 0; i < NX; ++i) mean[i] = sm[i] * scale;
+            for (int j = 0; j < NM; ++j) mean[mask_nth(UM, j)] = sm[j] * scale;
             m2[EY] = m2e;
         } else if (it.uniform) {
             for (int off = seg >> 1; off > 0; off >>= 1) {
                 const float half_n = 0.5f * cnt;
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
-                    if (!((dp.mean_mask >> i) & 1)) continue;  // a mean no cost term reads
+                    if (!((mmask >> i) & 1)) continue;  // a mean no cost term reads
                     const float mb = __shfl_xor_sync(0xffffffffu, mean[i], off);
                     if (i == EY || all_var) {
                         const float d = mb - mean[i];
@@ -122,7 +142,7 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it
                 const float fa = cnt * inv, fb = cb * inv, fab = cnt * cb * inv;
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
-                    if (!((dp.mean_mask >> i) & 1)) continue;
+                    if (!((mmask >> i) & 1)) continue;
                     const float mb = __shfl_xor_sync(0xffffffffu, mean[i], off);
                     if (i == EY || all_var) {
                         const float d = mb - mean[i];
@@ -135,7 +155,8 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it
             }
         }
 #pragma unroll
-        for (int i = 0; i < NX; ++i) var[i] = m2[i] * it.invM1;
+        for (int i = 0; i < NX; ++i)
+            if (MM == 0 || ((MM >> i) & 1)) var[i] = m2[i] * it.invM1;
     } else {
         // Naive one-pass sums: mean = sum x / M, var = (sum x^2 - M mean^2) / (M - 1).
         float s[NX], q[NX];
@@ -143,6 +164,7 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it
         for (int i = 0; i < NX; ++i) {
             s[i] = 0.0f;
             q[i] = 0.0f;
+            if (MM != 0 && !((MM >> i) & 1)) continue;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const float xv = (it.uniform || ls + seg * p < it.M) ? x[p][i] : 0.0f;
@@ -153,13 +175,14 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it
         for (int off = seg >> 1; off > 0; off >>= 1) {
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
-                if (!((dp.mean_mask >> i) & 1)) continue;
+                if (!((mmask >> i) & 1)) continue;
                 s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
                 if (i == EY || all_var) q[i] += __shfl_xor_sync(0xffffffffu, q[i], off);
             }
         }
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
+            if (MM != 0 && !((MM >> i) & 1)) continue;
             mean[i] = s[i] * it.invM;
             var[i] = (q[i] - it.Mf * mean[i] * mean[i]) * it.invM1;
         }
@@ -301,8 +324,10 @@ __host__ __device__ constexpr int roll_max_threads()
 // reciprocals, k_off), the Philox round keys and the track's scale and mask. The single-solve kernel
 // passes dp itself; the server passes a per-warp item in shared memory while dp, the constants its
 // batch's vehicles share, stays in kernel parameter space.
+// MM: 0, or the fixed set of states the cost weights (a mask holding e_y; the caller guarantees that
+// Q and Qf vanish outside it and that nothing is recorded): only those means are merged and costed.
 template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float, bool PACK = true, bool UTRIG = false,
-          typename IT = DevParams, bool TYRE_POLY = true>
+          typename IT = DevParams, bool TYRE_POLY = true, int MM = 0>
 __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it, const RollIO& io,
                                                const Tab* __restrict__ kap_s, const float* __restrict__ v_s,
                                                float* __restrict__ my_u, int group, uint32_t ctr,
@@ -311,6 +336,8 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
     constexpr int NX = model_nx(MODEL);
     constexpr int EY = MODEL == 0 ? 4 : (MODEL == 2 ? 6 : 1);
     constexpr int SI = model_s_index(MODEL);  // path coordinate, carried relative to its start (or -1)
+    static_assert(MM == 0 || !FULL, "the full belief merges every mean");
+    constexpr bool RECORDS = MM == 0;         // a fixed cost set runs without recording
     const int lane = threadIdx.x & (kWarp - 1);
     const int seg = it.seg;
     const int ls = lane & (seg - 1);
@@ -396,7 +423,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
     }
     float h_prev = h_cur;
     const bool writer = active && ls == 0;
-    if (dp.record && writer) {
+    if (RECORDS && dp.record && writer) {
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
             io.mean[(size_t)k * (it.T + 1) * NX + i] = mean[i];
@@ -415,9 +442,9 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
         float q;
         if constexpr (FULL) {
             q = general ? quad_cost<NX>(dp, dp.Q, mean) + (any_constraint_broken<NX>(*cs, mean) ? dp.Cobs : 0.0f)
-                        : state_cost<NX>(dp, dp.Q, mean);
+                        : state_cost<NX, EY>(dp, dp.Q, mean);
         } else {
-            q = state_cost<NX>(dp, dp.Q, mean);
+            q = state_cost<NX, EY, MM>(dp, dp.Q, mean);
         }
         const float term = q + ctrl + csafe;
         if constexpr (COMP) S.add(term); else S_naive += term;
@@ -530,12 +557,12 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
                 }
             }
         } else {
-            belief_moments<NX, EY, P, COMP>(dp, it, x, ls, seg, dp.record != 0, mean, var);
+            belief_moments<NX, EY, P, COMP, MM>(dp, it, x, ls, seg, RECORDS && dp.record != 0, mean, var);
         }
-        if constexpr (SI >= 0) mean[SI] += s0;
+        if constexpr (SI >= 0 && (MM == 0 || ((MM >> SI) & 1))) mean[SI] += s0;
         h_prev = h_cur;
         h_cur = general ? h_next : belief_barrier(dp, mean[EY], var[EY]);
-        if (dp.record && writer) {
+        if (RECORDS && dp.record && writer) {
             const size_t base = ((size_t)k * (it.T + 1) + t + 1) * NX;
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
@@ -548,9 +575,9 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
     float qT;
     if constexpr (FULL) {
         qT = general ? quad_cost<NX>(dp, dp.Qf, mean) + (any_constraint_broken<NX>(*cs, mean) ? dp.Cobs : 0.0f)
-                     : state_cost<NX>(dp, dp.Qf, mean);
+                     : state_cost<NX, EY>(dp, dp.Qf, mean);
     } else {
-        qT = state_cost<NX>(dp, dp.Qf, mean);
+        qT = state_cost<NX, EY, MM>(dp, dp.Qf, mean);
     }
     const float term = qT + dp.Csafe * fmaxf(fmaf(dp.one_m_gamma, h_prev, -h_cur), 0.0f);
     float total;

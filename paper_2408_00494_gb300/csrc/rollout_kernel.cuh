@@ -277,8 +277,9 @@ __device__ __noinline__ void block_partial(const int K, const int T, const int s
 // "MPPI update law") follow the last group without a second launch: every block publishes the
 // log-sum-exp partial of its own samples (block_partial), and the last block to arrive (atomic
 // ticket) merges the partials in block order and writes v+ = v + N / eta, u0, the normalised weights,
-// the diagnostics and the counter (tail_merge). No block waits for another.
-template <int MODEL, int P, bool COMP, bool FULL>
+// the diagnostics and the counter (tail_merge). No block waits for another. MM: the cost's states
+// when fixed at compile time (rollout_group), else 0.
+template <int MODEL, int P, bool COMP, bool FULL, int MM = 0>
 __global__ void __launch_bounds__(roll_max_threads<MODEL, P>()) rollout_kernel(const DevParams dp, const RollIO io,
                                                                        const TailIO tail, const ConSet cs)
 {
@@ -311,7 +312,8 @@ __global__ void __launch_bounds__(roll_max_threads<MODEL, P>()) rollout_kernel(c
     float* my_u = u_s + (warp * dp.spw + lane / dp.seg) * 2 * TN;  // T x (u_0, u_1, sin u_0, cos u_0)
     const int n_groups = (dp.K + dp.spw - 1) / dp.spw;
     for (int group = blockIdx.x * wpb + warp; group < n_groups; group += gridDim.x * wpb)
-        rollout_group<MODEL, P, COMP, FULL, float2, true, true>(dp, dp, io, kap_s, v_s, my_u, group, ctr, &cs);
+        rollout_group<MODEL, P, COMP, FULL, float2, true, true, DevParams, true, MM>(dp, dp, io, kap_s, v_s, my_u,
+                                                                                   group, ctr, &cs);
     __syncthreads();
 
     float* part = tail.part + (size_t)blockIdx.x * (3 + TN);
@@ -328,25 +330,25 @@ __global__ void __launch_bounds__(roll_max_threads<MODEL, P>()) rollout_kernel(c
                      red, fac_s, red_e, red_q, bc_s);
 }
 
-template <int MODEL, int P, bool COMP, bool FULL>
+template <int MODEL, int P, bool COMP, bool FULL, int MM>
 inline cudaError_t launch_one(const DevParams& dp, const RollIO& io, const TailIO& tail, const ConSet& cs,
                               const RollLaunch& L, cudaStream_t st)
 {
     if (L.grid > kTailMaxBlocks) return cudaErrorInvalidValue;
-    rollout_kernel<MODEL, P, COMP, FULL><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io, tail, cs);
+    rollout_kernel<MODEL, P, COMP, FULL, MM><<<L.grid, L.wpb * kWarp, L.smem, st>>>(dp, io, tail, cs);
     return cudaGetLastError();
 }
 
-template <int MODEL, bool COMP, bool FULL>
+template <int MODEL, bool COMP, bool FULL, int MM = 0>
 inline cudaError_t launch_model(const DevParams& dp, const RollIO& io, const TailIO& tail, const ConSet& cs, int P,
                                 const RollLaunch& L, cudaStream_t st)
 {
     switch (P) {
-    case 1: return launch_one<MODEL, 1, COMP, FULL>(dp, io, tail, cs, L, st);
-    case 2: return launch_one<MODEL, 2, COMP, FULL>(dp, io, tail, cs, L, st);
-    case 4: return launch_one<MODEL, 4, COMP, FULL>(dp, io, tail, cs, L, st);
+    case 1: return launch_one<MODEL, 1, COMP, FULL, MM>(dp, io, tail, cs, L, st);
+    case 2: return launch_one<MODEL, 2, COMP, FULL, MM>(dp, io, tail, cs, L, st);
+    case 4: return launch_one<MODEL, 4, COMP, FULL, MM>(dp, io, tail, cs, L, st);
     case 8:
-        if constexpr (MODEL != 2) return launch_one<MODEL, 8, COMP, FULL>(dp, io, tail, cs, L, st);
+        if constexpr (MODEL != 2) return launch_one<MODEL, 8, COMP, FULL, MM>(dp, io, tail, cs, L, st);
         else return cudaErrorInvalidValue;  // the wheel-speed model takes M <= 128
     default: return cudaErrorInvalidValue;
     }
@@ -356,10 +358,10 @@ inline cudaError_t launch_model(const DevParams& dp, const RollIO& io, const Tai
 // kernel, ceil(groups / (SMs w)) rounds of max(w, kSatWarps) warp-times each, among the w that fit
 // on an SM (fewer than kSatWarps warps leave issue slots idle on latency).
 constexpr int kSatWarps = 16;
-template <int MODEL, int P, bool COMP, bool FULL>
+template <int MODEL, int P, bool COMP, bool FULL, int MM>
 inline cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
 {
-    auto kern = rollout_kernel<MODEL, P, COMP, FULL>;
+    auto kern = rollout_kernel<MODEL, P, COMP, FULL, MM>;
     int dev = 0, sms = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -398,18 +400,19 @@ inline cudaError_t plan_one(const DevParams& dp, RollLaunch& L)
     L.wpb = best_w;
     L.grid = (int)std::min<long>(sms, (groups + best_w - 1) / best_w);
     L.smem = rollout_smem_bytes(dp, best_w);
+    L.cost_mask = MM;
     return cudaSuccess;
 }
 
-template <int MODEL, bool COMP, bool FULL>
+template <int MODEL, bool COMP, bool FULL, int MM = 0>
 inline cudaError_t plan_model(const DevParams& dp, int P, RollLaunch& L)
 {
     switch (P) {
-    case 1: return plan_one<MODEL, 1, COMP, FULL>(dp, L);
-    case 2: return plan_one<MODEL, 2, COMP, FULL>(dp, L);
-    case 4: return plan_one<MODEL, 4, COMP, FULL>(dp, L);
+    case 1: return plan_one<MODEL, 1, COMP, FULL, MM>(dp, L);
+    case 2: return plan_one<MODEL, 2, COMP, FULL, MM>(dp, L);
+    case 4: return plan_one<MODEL, 4, COMP, FULL, MM>(dp, L);
     case 8:
-        if constexpr (MODEL != 2) return plan_one<MODEL, 8, COMP, FULL>(dp, L);
+        if constexpr (MODEL != 2) return plan_one<MODEL, 8, COMP, FULL, MM>(dp, L);
         else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }

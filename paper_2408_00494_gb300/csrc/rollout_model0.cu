@@ -3,10 +3,18 @@
 
 namespace bss {
 
+// The compensated racing-barrier variant has a second build for costs that weight only v_x, e_psi
+// and e_y (the racing cost), used when nothing is recorded: it merges and costs those three means only.
+static bool racing_cost_only(const DevParams& dp)
+{
+    return !dp.record && (dp.mean_mask & ~kRacingCostMask) == 0;
+}
+
 template <>
 cudaError_t prepare_model<0>(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L)
 {
     if (full) return plan_model<0, true, true>(dp, P, L);
+    if (comp && racing_cost_only(dp)) return plan_model<0, true, false, kRacingCostMask>(dp, P, L);
     return comp ? plan_model<0, true, false>(dp, P, L) : plan_model<0, false, false>(dp, P, L);
 }
 
@@ -15,6 +23,10 @@ cudaError_t launch_model_variant<0>(const DevParams& dp, const RollIO& io, const
                                      bool comp, bool full, const RollLaunch& L, cudaStream_t st)
 {
     if (full) return launch_model<0, true, true>(dp, io, tail, cs, P, L, st);
+    if (L.cost_mask != 0) {  // planned for the racing cost: valid only while the parameters still allow it
+        if (!comp || L.cost_mask != kRacingCostMask || !racing_cost_only(dp)) return cudaErrorInvalidValue;
+        return launch_model<0, true, false, kRacingCostMask>(dp, io, tail, cs, P, L, st);
+    }
     return comp ? launch_model<0, true, false>(dp, io, tail, cs, P, L, st)
                 : launch_model<0, false, false>(dp, io, tail, cs, P, L, st);
 }

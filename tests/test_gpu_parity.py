@@ -234,6 +234,50 @@ def test_solve_particle_counts(M):
     check_solve(p, workload.random_state(p, M), workload.random_nominal(p, M), ctr=M)
 
 
+def check_unrecorded(prob, x0, v, ctr):
+    """A solve that keeps no moments (the launch the benchmark and the controllers use) against the
+    oracle: every sample's perturbations and cost, the weights from the GPU's costs, and v+ and u0
+    isolated and end to end."""
+    g = gpu_solve(prob, x0, v, ctr, record=False)
+    ref = oracle.Oracle(prob).solve(x0, v, ctr, threads=oracle.host_threads())
+    assert_close(g["eps"], ref["eps"], 0.0, 1e-6, "eps_eff")
+    ok = ref["margin"] > 1e-4
+    assert (~ok).sum() <= max(2, prob.K // 100), f"{(~ok).sum()} samples within 1e-4 of the wall"
+    scale = np.maximum(np.abs(ref["S"]), 1.0)
+    dS = g["S"] - ref["S"]
+    assert np.all(np.abs(dS[ok]) <= 1e-4 * scale[ok]), f"S: max rel err {np.max(np.abs(dS[ok]) / scale[ok]):.3e}"
+    lam = float(np.float32(prob.lam))
+    w_iso, vp_iso, _ = oracle.optimal_control(g["S"], v.astype(np.float64)[None] + g["eps"], lam)
+    assert_close(g["w"], w_iso, 1e-5, 1e-7, "weights (from GPU costs)")
+    assert_close(g["v_plus"], vp_iso, 1e-4, 1e-5, "v+ (from GPU costs and eps)")
+    assert_close(g["u0"], vp_iso[0], 1e-4, 1e-5, "u0")
+    dSc = np.where(ok, dS, 0.0)
+    dev = np.abs(dSc - np.sum(ref["w"] * dSc)) / lam
+    bound = np.einsum("k,kti->ti", ref["w"] * dev, np.abs(ref["u"] - ref["v_plus"][None]))
+    err = np.abs(g["v_plus"] - ref["v_plus"])
+    assert np.all(err <= 1e-5 + 1e-4 * np.abs(ref["v_plus"]) + 2 * bound), f"v+ e2e max err {err.max():.3e}"
+    assert g["counter"] == ctr + 1
+
+
+@pytest.mark.parametrize("M", [2, 16, 50, 64, 96, 256])
+@pytest.mark.parametrize("compensated", [1, 0])
+def test_unrecorded_solve_particle_counts(M, compensated):
+    """Without recording, a cost that weights only v_x, e_psi and e_y (the racing cost) runs a build
+    that merges those three means only (compensated), or the run-time set of the plain sums (naive):
+    segments narrower than a warp, full warps, ragged lanes and one to eight particles per lane."""
+    p = workload.config0()
+    p.K, p.M, p.T, p.compensated = 200, M, 12, compensated
+    check_unrecorded(p, workload.random_state(p, 300 + M), workload.random_nominal(p, 300 + M), ctr=M + 5)
+
+
+def test_unrecorded_solve_with_every_state_weighted():
+    """A cost that weights every state (the build with the run-time set of merged means)."""
+    p = workload.config0()
+    p.K, p.M, p.T = 200, 64, 12
+    p.Q = p.Qf = (1.0, 0.5, 0.2, 1.0, 0.1, 1e-4)
+    check_unrecorded(p, workload.random_state(p, 41), workload.random_nominal(p, 41), ctr=9)
+
+
 @pytest.mark.parametrize("model,K,M,T", [("double_integrator", 70, 2, 256), ("bicycle", 70, 2, 64),
                                          ("bicycle", 40, 256, 6), ("bicycle", 33, 3, 7)])
 def test_solve_extreme_shapes(model, K, M, T):
