@@ -123,8 +123,13 @@ __global__ void __launch_bounds__(kServeWarps * kWarp, serve_min_blocks<P>())
         const float* v = ctrl_v + (size_t)rq.ctrl * 2 * T_max;
         RollIO io{rq.x0, nullptr, v, ctrl_ctr + rq.ctrl, arena + rq.off_S, arena + rq.off_eps, nullptr, nullptr};
         float* my_u = ubuf + (lane / rq.seg) * 2 * rq.T;
-        rollout_group<0, P, true, false, float, true, false, ServeItem, false>(
-            fleet, *it, io, cd.kappa, v, my_u, (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
+        // a class whose cost weights only v_x, e_psi and e_y merges and costs those means only
+        if ((fleet.mean_mask & ~kRacingCostMask) == 0)
+            rollout_group<0, P, true, false, float, true, false, ServeItem, false, kRacingCostMask>(
+                fleet, *it, io, cd.kappa, v, my_u, (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
+        else
+            rollout_group<0, P, true, false, float, true, false, ServeItem, false>(
+                fleet, *it, io, cd.kappa, v, my_u, (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
         __syncwarp();
     }
 }

@@ -136,16 +136,20 @@ def test_server_matches_single_solve(K, M, T):
 
 
 def test_two_constants_classes_batch_apart_and_match_their_single_solves():
-    """Controllers whose vehicles differ (here the mass) are batched by constants class: each
-    batch's rollout kernels take that class's constants as a parameter, and the graph's kernel
-    parameters are switched when a slot's class changes. Every request must still give, bit for bit,
-    what it gives alone, with and without graphs, and match bssmppi_solve + bssmppi_shift."""
+    """Controllers whose vehicles or costs differ (here the mass, and for one controller cost weights
+    on every state, whose class takes the kernel path that merges every mean) are batched by
+    constants class: each batch's rollout kernels take that class's constants as a parameter, and
+    the graph's kernel parameters are switched when a slot's class changes. Every request must still
+    give, bit for bit, what it gives alone, with and without graphs, and match bssmppi_solve +
+    bssmppi_shift."""
     n = 6
     s = bssmppi.server_create(n, T_max=T_MAX)
     probs = [_problem(i) for i in range(n)]
     for i, p in enumerate(probs):
         if i % 2:
             p.mass = 1200.0  # a lighter vehicle: a second constants class
+        if i == 5:
+            p.Q = p.Qf = (1.0, 0.5, 0.2, 1.0, 0.1, 1e-4)  # every state weighted: a third class
         bssmppi.server_add_controller(s, bssmppi.make_params(p))
     reqs = [(c, 1024 + 256 * c, (8, 32, 64, 128, 64, 32)[c], (20, 40, 60, 20, 40, 60)[c]) for c in range(n)]
     try:
