@@ -39,8 +39,8 @@ __host__ __device__ constexpr int mask_nth(int m, int j)  // index of the j-th s
 // Everything a solve's kernels need, derived on the host at create time and passed by value
 // (kernel parameter space), so several controllers can run concurrently without global state.
 // Constant operands of the bicycle substep: the model's h, -h, l_f, -l_r, B, -B, C, -D_r / m,
-// -l_r D_r / I_z, then fixed numbers: 1, -1 and the heading-rotation series' 1/24, -1/2, 1/120,
-// -1/6.
+// -l_r D_r / I_z, then fixed numbers: 1, -1, the heading-rotation series' 1/24, -1/2, 1/120,
+// -1/6 and the slip-angle arctangent's coefficients (slip_atan below), highest degree first.
 // The wheel-speed model adds R_w, D_xf = mu_x F_zf, D_f, 1/m, -1/m, D_xr / m, D_r / m, l_f / I_z,
 // l_r D_r / I_z, -h R_w / I_w and -R_w D_xr / I_w (kFoldW*). B^2 and the coefficients c_0..c_9 of
 // the tyre curve's polynomial (tyre_curve below) follow.
@@ -49,14 +49,22 @@ enum : int {
     kFoldH, kFoldNH, kFoldLf, kFoldNLr, kFoldTB, kFoldNTB, kFoldTC, kFoldNDrM, kFoldNLrDrIz,
     kFoldWRw, kFoldWDxf, kFoldWDf, kFoldWInvM, kFoldWNInvM, kFoldWDxrM, kFoldWDrM, kFoldWLfIz, kFoldWLrDrIz,
     kFoldWNhRwIw, kFoldWNRwDxrIw, kFoldTB2, kFoldTy0, kFoldTyLast = kFoldTy0 + kTyreDeg,
-    kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldN
+    kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldSa0, kFoldSaLast = kFoldSa0 + 4, kFoldN
 };
+
+// Coefficients of the slip-angle arctangent's polynomial p (slip_atan), highest degree first.
+__host__ __device__ constexpr float slip_atan_coef(int i)
+{
+    return i == 0 ? -5.1325989538e-2f : i == 1 ? 1.0160016107e-1f : i == 2 ? -1.4175010834e-1f
+         : i == 3 ? 1.9994226694e-1f : -3.3333234306e-1f;
+}
 
 // The fixed numbers among them (i >= kFoldOne).
 __host__ __device__ constexpr float fold_fixed(int i)
 {
     return i == kFoldOne ? 1.0f : i == kFoldM1 ? -1.0f : i == kFoldC24 ? 4.1666667e-2f : i == kFoldMHalf ? -0.5f
-         : i == kFoldC120 ? 8.3333333e-3f : i == kFoldM6 ? -1.6666667e-1f : 0.0f;
+         : i == kFoldC120 ? 8.3333333e-3f : i == kFoldM6 ? -1.6666667e-1f
+         : (i >= kFoldSa0 && i <= kFoldSaLast) ? slip_atan_coef(i - kFoldSa0) : 0.0f;
 }
 
 struct DevParams {
@@ -342,14 +350,33 @@ __device__ __forceinline__ float slip_atan(float t)
 {
     if (fabsf(t) <= 0.5f) {
         const float z = __fmul_rn(t, t);
-        float p = -5.1325989538e-2f;
-        p = fmaf(p, z, 1.0160016107e-1f);
-        p = fmaf(p, z, -1.4175010834e-1f);
-        p = fmaf(p, z, 1.9994226694e-1f);
-        p = fmaf(p, z, -3.3333234306e-1f);
+        float p = slip_atan_coef(0);
+#pragma unroll
+        for (int i = 1; i < 5; ++i) p = fmaf(p, z, slip_atan_coef(i));
         return fmaf(__fmul_rn(t, z), p, t);
     }
     return atanf(t);
+}
+
+// slip_atan of one particle, or of two side by side: the polynomial for both with packed
+// instructions (each half rounds as slip_atan does), then the library's atanf for a particle beyond
+// |t| = 1/2, entered by the warp only when one of its particles needs it.
+template <typename V>
+__device__ __forceinline__ V slip_atan_v(const DevParams& P, V t)
+{
+    if constexpr (std::is_same<V, float>::value) {
+        return slip_atan(t);
+    } else {
+        const V z = vmul(t, t);
+        V p = fold<V>(P, kFoldSa0);
+#pragma unroll
+        for (int i = kFoldSa0 + 1; i <= kFoldSaLast; ++i) p = vfma(p, z, fold<V>(P, i));
+        V y = vfma(vmul(t, z), p, t);
+        const bool far = fabsf(t.x) > 0.5f || fabsf(t.y) > 0.5f;
+        if (__any_sync(__activemask(), far))
+            y = each(t, y, [](float tv, float yv) { return fabsf(tv) <= 0.5f ? yv : atanf(tv); });
+        return y;
+    }
 }
 
 // Per-step factors (the control is the same for every particle of a sample): steer, a,
@@ -432,10 +459,9 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const TP& tr
     const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
     const V tf = vmul(vfma(fold<V>(P, kFoldLf), r, vy), ivx);    // (v_y + l_f r) / v_x
     const V tr = vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx);   // (v_y - l_r r) / v_x
-    const auto slip = [](float a) { return slip_atan(a); };
-    const V af = vfma(each(tf, slip), fold<V>(P, kFoldM1), u.steer);  // alpha_f
-    const V bf = vmul(fold<V>(P, kFoldTB), af);                        // B alpha_f
-    const V br = vmul(fold<V>(P, kFoldNTB), each(tr, slip));           // B alpha_r
+    const V af = vfma(slip_atan_v(P, tf), fold<V>(P, kFoldM1), u.steer);  // alpha_f
+    const V bf = vmul(fold<V>(P, kFoldTB), af);                            // B alpha_f
+    const V br = vmul(fold<V>(P, kFoldNTB), slip_atan_v(P, tr));           // B alpha_r
     V gf, gr;  // F_f / D_f, F_r / D_r
     if constexpr (POLY) {
         gf = tyre_curve(P, bf);
