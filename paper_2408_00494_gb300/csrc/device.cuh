@@ -40,7 +40,8 @@ __host__ __device__ constexpr int mask_nth(int m, int j)  // index of the j-th s
 // (kernel parameter space), so several controllers can run concurrently without global state.
 // Constant operands of the bicycle substep: the model's h, -h, l_f, -l_r, B, -B, C, -D_r / m,
 // -l_r D_r / I_z, then fixed numbers: 1, -1, the heading-rotation series' 1/24, -1/2, 1/120,
-// -1/6 and the slip-angle arctangent's coefficients (slip_atan below), highest degree first.
+// -1/6, the slip-angle arctangent's coefficients (slip_atan below), highest degree first, and the
+// heading series' 1/9!, -1/7!, -1/10!, 1/8! and -1/6! (sincos_series).
 // The wheel-speed model adds R_w, D_xf = mu_x F_zf, D_f, 1/m, -1/m, D_xr / m, D_r / m, l_f / I_z,
 // l_r D_r / I_z, -h R_w / I_w and -R_w D_xr / I_w (kFoldW*). B^2 and the coefficients c_0..c_9 of
 // the tyre curve's polynomial (tyre_curve below) follow.
@@ -49,7 +50,8 @@ enum : int {
     kFoldH, kFoldNH, kFoldLf, kFoldNLr, kFoldTB, kFoldNTB, kFoldTC, kFoldNDrM, kFoldNLrDrIz,
     kFoldWRw, kFoldWDxf, kFoldWDf, kFoldWInvM, kFoldWNInvM, kFoldWDxrM, kFoldWDrM, kFoldWLfIz, kFoldWLrDrIz,
     kFoldWNhRwIw, kFoldWNRwDxrIw, kFoldTB2, kFoldTy0, kFoldTyLast = kFoldTy0 + kTyreDeg,
-    kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldSa0, kFoldSaLast = kFoldSa0 + 4, kFoldN
+    kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldSa0, kFoldSaLast = kFoldSa0 + 4,
+    kFoldS9, kFoldS7, kFoldC10, kFoldC8, kFoldC6, kFoldN
 };
 
 // Coefficients of the slip-angle arctangent's polynomial p (slip_atan), highest degree first.
@@ -64,7 +66,9 @@ __host__ __device__ constexpr float fold_fixed(int i)
 {
     return i == kFoldOne ? 1.0f : i == kFoldM1 ? -1.0f : i == kFoldC24 ? 4.1666667e-2f : i == kFoldMHalf ? -0.5f
          : i == kFoldC120 ? 8.3333333e-3f : i == kFoldM6 ? -1.6666667e-1f
-         : (i >= kFoldSa0 && i <= kFoldSaLast) ? slip_atan_coef(i - kFoldSa0) : 0.0f;
+         : (i >= kFoldSa0 && i <= kFoldSaLast) ? slip_atan_coef(i - kFoldSa0)
+         : i == kFoldS9 ? 2.7557319e-6f : i == kFoldS7 ? -1.9841270e-4f : i == kFoldC10 ? -2.7557319e-7f
+         : i == kFoldC8 ? 2.4801587e-5f : i == kFoldC6 ? -1.3888889e-3f : 0.0f;
 }
 
 struct DevParams {
@@ -274,16 +278,16 @@ __device__ __forceinline__ void sincos_series(float x, float* s, float* c)
 {
     if (fabsf(x) <= 0.78539816f) {
         const float x2 = x * x;
-        float ps = 2.7557319e-6f;           //  1/9!
-        ps = fmaf(ps, x2, -1.9841270e-4f);  // -1/7!
-        ps = fmaf(ps, x2, 8.3333333e-3f);   //  1/5!
-        ps = fmaf(ps, x2, -1.6666667e-1f);  // -1/3!
+        float ps = fold_fixed(kFoldS9);           //  1/9!
+        ps = fmaf(ps, x2, fold_fixed(kFoldS7));   // -1/7!
+        ps = fmaf(ps, x2, fold_fixed(kFoldC120)); //  1/5!
+        ps = fmaf(ps, x2, fold_fixed(kFoldM6));   // -1/3!
         *s = fmaf(ps * x2, x, x);
-        float pc = -2.7557319e-7f;          // -1/10!
-        pc = fmaf(pc, x2, 2.4801587e-5f);   //  1/8!
-        pc = fmaf(pc, x2, -1.3888889e-3f);  // -1/6!
-        pc = fmaf(pc, x2, 4.1666667e-2f);   //  1/4!
-        pc = fmaf(pc, x2, -0.5f);           // -1/2!
+        float pc = fold_fixed(kFoldC10);          // -1/10!
+        pc = fmaf(pc, x2, fold_fixed(kFoldC8));   //  1/8!
+        pc = fmaf(pc, x2, fold_fixed(kFoldC6));   // -1/6!
+        pc = fmaf(pc, x2, fold_fixed(kFoldC24));  //  1/4!
+        pc = fmaf(pc, x2, -0.5f);                 // -1/2!
         *c = fmaf(pc, x2, 1.0f);
     } else {
         sincosf(x, s, c);
@@ -358,24 +362,35 @@ __device__ __forceinline__ float slip_atan(float t)
     return atanf(t);
 }
 
-// slip_atan of one particle, or of two side by side: the polynomial for both with packed
-// instructions (each half rounds as slip_atan does), then the library's atanf for a particle beyond
-// |t| = 1/2, entered by the warp only when one of its particles needs it.
+// |x| > lim for one particle's value, or for either of a pair's.
+__device__ __forceinline__ bool beyond(float x, float lim) { return fabsf(x) > lim; }
+__device__ __forceinline__ bool beyond(float2 x, float lim) { return fabsf(x.x) > lim || fabsf(x.y) > lim; }
+
+// slip_atan of the front and rear slip arguments of one particle, or of two particles side by side:
+// for pairs, the polynomial for all four with packed instructions (each half rounds as slip_atan
+// does), then the library's atanf for an argument beyond |t| = 1/2, entered by the warp only when
+// one of its particles needs it (one vote for both tyres).
 template <typename V>
-__device__ __forceinline__ V slip_atan_v(const DevParams& P, V t)
+__device__ __forceinline__ void slip_atans(const DevParams& P, V tf, V tr, V& yf, V& yr)
 {
     if constexpr (std::is_same<V, float>::value) {
-        return slip_atan(t);
+        yf = slip_atan(tf);
+        yr = slip_atan(tr);
     } else {
-        const V z = vmul(t, t);
-        V p = fold<V>(P, kFoldSa0);
+        const auto poly = [&](V t) {
+            const V z = vmul(t, t);
+            V p = fold<V>(P, kFoldSa0);
 #pragma unroll
-        for (int i = kFoldSa0 + 1; i <= kFoldSaLast; ++i) p = vfma(p, z, fold<V>(P, i));
-        V y = vfma(vmul(t, z), p, t);
-        const bool far = fabsf(t.x) > 0.5f || fabsf(t.y) > 0.5f;
-        if (__any_sync(__activemask(), far))
-            y = each(t, y, [](float tv, float yv) { return fabsf(tv) <= 0.5f ? yv : atanf(tv); });
-        return y;
+            for (int i = kFoldSa0 + 1; i <= kFoldSaLast; ++i) p = vfma(p, z, fold<V>(P, i));
+            return vfma(vmul(t, z), p, t);
+        };
+        yf = poly(tf);
+        yr = poly(tr);
+        if (__any_sync(__activemask(), beyond(tf, 0.5f) || beyond(tr, 0.5f))) {
+            const auto fix = [](float tv, float yv) { return fabsf(tv) <= 0.5f ? yv : atanf(tv); };
+            yf = each(tf, yf, fix);
+            yr = each(tr, yr, fix);
+        }
     }
 }
 
@@ -412,6 +427,34 @@ __device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp,
     sp = s;
 }
 
+// sincos_series of one particle's heading, or of two particles' side by side: for pairs, both
+// series with packed instructions (each half rounds as sincos_series does), then the library's
+// sincosf for a heading beyond pi/4, entered by the warp only when one of its particles needs it.
+template <typename V>
+__device__ __forceinline__ void sincos_series_v(const DevParams& P, V x, V& s, V& c)
+{
+    if constexpr (std::is_same<V, float>::value) {
+        sincos_series(x, &s, &c);
+    } else {
+        const V x2 = vmul(x, x);
+        V ps = fold<V>(P, kFoldS9);
+        ps = vfma(ps, x2, fold<V>(P, kFoldS7));
+        ps = vfma(ps, x2, fold<V>(P, kFoldC120));
+        ps = vfma(ps, x2, fold<V>(P, kFoldM6));
+        s = vfma(vmul(ps, x2), x, x);
+        V pc = fold<V>(P, kFoldC10);
+        pc = vfma(pc, x2, fold<V>(P, kFoldC8));
+        pc = vfma(pc, x2, fold<V>(P, kFoldC6));
+        pc = vfma(pc, x2, fold<V>(P, kFoldC24));
+        pc = vfma(pc, x2, fold<V>(P, kFoldMHalf));
+        c = vfma(pc, x2, fold<V>(P, kFoldOne));
+        if (__any_sync(__activemask(), beyond(x, 0.78539816f))) {
+            if (fabsf(x.x) > 0.78539816f) sincosf(x.x, &s.x, &c.x);
+            if (fabsf(x.y) > 0.78539816f) sincosf(x.y, &s.y, &c.y);
+        }
+    }
+}
+
 // The tyre curve of the simplified Pacejka law, sin(C atan x) for x = B alpha. For |x| <= 1 it is
 // x p(x^2), p the degree-9 polynomial that interpolates sin(C atan sqrt z) / sqrt z at the ten
 // Chebyshev points of [0, 1] (fitted on the host for the problem's C in double precision; its
@@ -423,19 +466,35 @@ __device__ __forceinline__ void rotate_heading_v(const DevParams& P, V d, V& sp,
 __device__ __forceinline__ float tyre_curve_library(const DevParams& P, float x) { return __sinf(P.tC * atanf(x)); }
 
 template <typename V>
-__device__ __forceinline__ V tyre_curve(const DevParams& P, V x)
+__device__ __forceinline__ V tyre_poly(const DevParams& P, V x)
 {
     const V z = vmul(x, x);
     V p = fold<V>(P, kFoldTyLast);
 #pragma unroll
     for (int d = kTyreDeg - 1; d >= 0; --d) p = vfma(p, z, fold<V>(P, kFoldTy0 + d));
-    V g = vmul(x, p);
-    bool far;
-    if constexpr (std::is_same<V, float2>::value) far = fabsf(x.x) > 1.0f || fabsf(x.y) > 1.0f;
-    else far = fabsf(x) > 1.0f;
-    if (__any_sync(__activemask(), far))
+    return vmul(x, p);
+}
+
+template <typename V>
+__device__ __forceinline__ V tyre_curve(const DevParams& P, V x)
+{
+    V g = tyre_poly(P, x);
+    if (__any_sync(__activemask(), beyond(x, 1.0f)))
         g = each(x, g, [&](float xv, float gv) { return fabsf(xv) > 1.0f ? tyre_curve_library(P, xv) : gv; });
     return g;
+}
+
+// The front and rear tyre curves of one substep, with one vote of the warp for the library route.
+template <typename V>
+__device__ __forceinline__ void tyre_curves(const DevParams& P, V xf, V xr, V& gf, V& gr)
+{
+    gf = tyre_poly(P, xf);
+    gr = tyre_poly(P, xr);
+    if (__any_sync(__activemask(), beyond(xf, 1.0f) || beyond(xr, 1.0f))) {
+        const auto fix = [&](float xv, float gv) { return fabsf(xv) > 1.0f ? tyre_curve_library(P, xv) : gv; };
+        gf = each(xf, gf, fix);
+        gr = each(xr, gr, fix);
+    }
 }
 
 // One explicit-Euler substep of one particle (V = float) or of two particles side by side
@@ -459,13 +518,14 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const TP& tr
     const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
     const V tf = vmul(vfma(fold<V>(P, kFoldLf), r, vy), ivx);    // (v_y + l_f r) / v_x
     const V tr = vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx);   // (v_y - l_r r) / v_x
-    const V af = vfma(slip_atan_v(P, tf), fold<V>(P, kFoldM1), u.steer);  // alpha_f
-    const V bf = vmul(fold<V>(P, kFoldTB), af);                            // B alpha_f
-    const V br = vmul(fold<V>(P, kFoldNTB), slip_atan_v(P, tr));           // B alpha_r
+    V atf, atr;
+    slip_atans(P, tf, tr, atf, atr);
+    const V af = vfma(atf, fold<V>(P, kFoldM1), u.steer);  // alpha_f
+    const V bf = vmul(fold<V>(P, kFoldTB), af);            // B alpha_f
+    const V br = vmul(fold<V>(P, kFoldNTB), atr);          // B alpha_r
     V gf, gr;  // F_f / D_f, F_r / D_r
     if constexpr (POLY) {
-        gf = tyre_curve(P, bf);
-        gr = tyre_curve(P, br);
+        tyre_curves(P, bf, br, gf, gr);
     } else {
         const auto lib = [&](float a) { return tyre_curve_library(P, a); };
         gf = each(bf, lib);

@@ -476,13 +476,11 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
                 if constexpr (PAIRS) {
 #pragma unroll
                     for (int i = 0; i < NX; ++i) X[q][i] = make_float2(x[2 * q][i], x[2 * q + 1][i]);
-                    sincos_series(x[2 * q][HI], &hs[q].x, &hc[q].x);
-                    sincos_series(x[2 * q + 1][HI], &hs[q].y, &hc[q].y);
                 } else {
 #pragma unroll
                     for (int i = 0; i < NX; ++i) X[q][i] = x[q][i];
-                    sincos_series(x[q][HI], &hs[q], &hc[q]);
                 }
+                sincos_series_v(dp, X[q][HI], hs[q], hc[q]);
             }
             for (int j = 0; j < dp.n_sub; ++j) {
 #pragma unroll
