@@ -93,7 +93,9 @@ __device__ __forceinline__ void belief_moments(const DevParams& dp, const IT& it
                 for (int j = 0; j < NM; ++j) sb[j] = __shfl_xor_sync(0xffffffffu, sm[j], off);
                 const float d = (sb[JE] - sm[JE]) * scale;
                 const float m2b = __shfl_xor_sync(0xffffffffu, m2e, off);
-                m2e = fmaf(d * d, half_n, m2e + m2b);
+                // d^2 rounded on its own: where half_n is a constant 1 the compiler would
+                // otherwise fuse d * d into the sum and change the rounding
+                m2e = fmaf(__fmul_rn(d, d), half_n, m2e + m2b);
 #pragma unroll
                 for (int j = 0; j + 1 < NM; j += 2) {
                     const float2 a = __fadd2_rn(make_float2(sm[j], sm[j + 1]), make_float2(sb[j], sb[j + 1]));
