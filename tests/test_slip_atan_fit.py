@@ -13,10 +13,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _kernel_coefficients():
     src = open(os.path.join(ROOT, "paper_2408_00494_gb300", "csrc", "device.cuh")).read()
-    body = src[src.index("float slip_atan(float t)"):]
-    body = body[: body.index("return atanf(t);")]
+    body = src[src.index("float slip_atan_coef(int i)"):]
+    body = body[: body.index("}")]
     lits = [float(x) for x in re.findall(r"(-?\d\.\d+e-?\d+)f", body)]
-    # Horner order in the source: c_4 first, then c_3 .. c_0
+    # Horner order in the source (the coefficient function slip_atan reads): c_4 first, then c_3 .. c_0
     assert len(lits) == 5
     return np.array(lits[::-1])
 
