@@ -448,7 +448,26 @@ int bssmppi_slip_atan(const float* d_t, float* d_y, int64_t n, void* cuda_stream
 int bssmppi_tyre_curve(bssmppi_t h, const float* d_x, float* d_y, int64_t n, void* cuda_stream);
 
 /*
- * The coefficients c_0..c_9 (h_c, host, n >= 10 floats) of that polynomial for a tyre shape factor
+ * The rear tyre's curve as the bicycle substep evaluates it where one or two particles share a lane
+ * (Sec. V-A's vehicle model, readings R3 and R4: the rear slip angle is -atan t for the slip argument
+ * t = (v_y - l_r r) / v_x, so F_y,r / D_r = sin(C atan(-B atan t))): d_y[i] for d_t[i], the handle's
+ * B and C, n values; device arrays, taken in pairs through the packed form as in the solve. For
+ * |t| <= tau (tau = tan(1/B), or 1/2 if that is less) a degree-9 polynomial in (t / tau)^2 fitted
+ * on the host; beyond, slip_atan and the library's atanf and hardware sine. Exported so that its
+ * error can be checked against an exact reference. Asynchronous.
+ */
+int bssmppi_rear_tyre(bssmppi_t h, const float* d_t, float* d_y, int64_t n, void* cuda_stream);
+
+/*
+ * The coefficients c_0..c_9 (h_c, host, n >= 10 floats) of the rear tyre's polynomial for B > 0 and
+ * C > 0 and its domain's half-width (*h_tau): sin(C atan(-B atan t)) = x sum_i c_i x^(2i) with
+ * x = t / tau on |t| <= tau, interpolating at ten Chebyshev points in double precision. Host only.
+ * EINVAL for B <= 0, C <= 0, n < 10 or a NULL output.
+ */
+int bssmppi_rear_tyre_coefficients(double B, double C, float* h_c, int32_t n, double* h_tau);
+
+/*
+ * The coefficients c_0..c_9 (h_c, host, n >= 10 floats) of the tyre curve's polynomial for a tyre shape factor
  * C > 0: sin(C atan x) = x sum_i c_i x^(2i) on |x| <= 1, interpolating at ten Chebyshev points in
  * double precision. Host only (no device is needed). EINVAL for C <= 0 or n < 10.
  */

@@ -137,6 +137,8 @@ def load(build_if_missing: bool = True):
         "bssmppi_slip_atan": (ctypes.c_int, [vp, vp, i64, vp]),
         "bssmppi_tyre_curve": (ctypes.c_int, [vp, vp, vp, i64, vp]),
         "bssmppi_tyre_curve_coefficients": (ctypes.c_int, [ctypes.c_double, vp, i32]),
+        "bssmppi_rear_tyre": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+        "bssmppi_rear_tyre_coefficients": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -434,6 +436,20 @@ def box_muller(words, z, stream=None):
 def tyre_curve(h, x, y, stream=None):
     """y = sin(C atan x) as the substep evaluates it, for the handle's tyre shape factor C."""
     _check(load().bssmppi_tyre_curve(h, _ptr(x), _ptr(y), x.numel(), _stream_handle(stream)), h)
+
+
+def rear_tyre(h, t, y, stream=None):
+    """y = sin(C atan(-B atan t)), the rear tyre's curve at slip argument t as the substep evaluates it."""
+    _check(load().bssmppi_rear_tyre(h, _ptr(t), _ptr(y), t.numel(), _stream_handle(stream)), h)
+
+
+def rear_tyre_coefficients(B, C):
+    """(c_0..c_9, tau) of the rear tyre's polynomial in x = t / tau for B and C (host only)."""
+    c = np.zeros(10, np.float32)
+    tau = ctypes.c_double(0.0)
+    _check(load().bssmppi_rear_tyre_coefficients(float(B), float(C), ctypes.c_void_p(c.ctypes.data), 10,
+                                                 ctypes.byref(tau)))
+    return c, tau.value
 
 
 def tyre_curve_coefficients(C) -> np.ndarray:

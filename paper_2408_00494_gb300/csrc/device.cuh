@@ -44,12 +44,14 @@ __host__ __device__ constexpr int mask_nth(int m, int j)  // index of the j-th s
 // heading series' 1/9!, -1/7!, -1/10!, 1/8! and -1/6! (sincos_series).
 // The wheel-speed model adds R_w, D_xf = mu_x F_zf, D_f, 1/m, -1/m, D_xr / m, D_r / m, l_f / I_z,
 // l_r D_r / I_z, -h R_w / I_w and -R_w D_xr / I_w (kFoldW*). B^2 and the coefficients c_0..c_9 of
-// the tyre curve's polynomial (tyre_curve below) follow.
+// the tyre curve's polynomial (tyre_curve below) follow, then 1 / tau and the coefficients of the
+// rear tyre's polynomial (rear_tyre below).
 constexpr int kTyreDeg = 9;  // degree in x^2 of the tyre curve's polynomial
 enum : int {
     kFoldH, kFoldNH, kFoldLf, kFoldNLr, kFoldTB, kFoldNTB, kFoldTC, kFoldNDrM, kFoldNLrDrIz,
     kFoldWRw, kFoldWDxf, kFoldWDf, kFoldWInvM, kFoldWNInvM, kFoldWDxrM, kFoldWDrM, kFoldWLfIz, kFoldWLrDrIz,
     kFoldWNhRwIw, kFoldWNRwDxrIw, kFoldTB2, kFoldTy0, kFoldTyLast = kFoldTy0 + kTyreDeg,
+    kFoldRInv, kFoldRy0, kFoldRyLast = kFoldRy0 + kTyreDeg,
     kFoldOne, kFoldM1, kFoldC24, kFoldMHalf, kFoldC120, kFoldM6, kFoldSa0, kFoldSaLast = kFoldSa0 + 4,
     kFoldS9, kFoldS7, kFoldC10, kFoldC8, kFoldC6, kFoldN
 };
@@ -333,6 +335,11 @@ template <typename F> __device__ __forceinline__ float2 each(float2 a, float2 b,
 {
     return make_float2(f(a.x, b.x), f(a.y, b.y));
 }
+template <typename F> __device__ __forceinline__ float each(float a, float b, float c, F f) { return f(a, b, c); }
+template <typename F> __device__ __forceinline__ float2 each(float2 a, float2 b, float2 c, F f)
+{
+    return make_float2(f(a.x, b.x, c.x), f(a.y, b.y, c.y));
+}
 template <typename V> __device__ __forceinline__ V splat(float a);
 template <> __device__ __forceinline__ float splat<float>(float a) { return a; }
 template <> __device__ __forceinline__ float2 splat<float2>(float a) { return make_float2(a, a); }
@@ -413,6 +420,25 @@ __device__ __forceinline__ SubstepCtl<V> substep_ctl(const DevParams& P, const C
     return c;
 }
 
+// slip_atan of one slip argument per particle (a pair side by side: packed polynomial, then the
+// library's atanf for a particle beyond |t| = 1/2, entered by the warp only when one needs it).
+template <typename V>
+__device__ __forceinline__ V slip_atan_v(const DevParams& P, V t)
+{
+    if constexpr (std::is_same<V, float>::value) {
+        return slip_atan(t);
+    } else {
+        const V z = vmul(t, t);
+        V p = fold<V>(P, kFoldSa0);
+#pragma unroll
+        for (int i = kFoldSa0 + 1; i <= kFoldSaLast; ++i) p = vfma(p, z, fold<V>(P, i));
+        V y = vfma(vmul(t, z), p, t);
+        if (__any_sync(__activemask(), beyond(t, 0.5f)))
+            y = each(t, y, [](float tv, float yv) { return fabsf(tv) <= 0.5f ? yv : atanf(tv); });
+        return y;
+    }
+}
+
 // The heading's sine and cosine carried across the substeps of one step: seeded from the series at
 // the step's first substep, then rotated by each substep's increment d = h e_psi' (|d| << 1:
 // sin d and cos d from three-term series, errors below |d|^7/7! and |d|^6/6!).
@@ -484,17 +510,49 @@ __device__ __forceinline__ V tyre_curve(const DevParams& P, V x)
     return g;
 }
 
-// The front and rear tyre curves of one substep, with one vote of the warp for the library route.
+// The rear tyre's curve as one function of its slip argument t = (v_y - l_r r) / v_x, whose slip
+// angle is -atan t: g_r(t) = sin(C atan(-B atan t)). For |t| <= tau, tau = tan(1/B) (where
+// |B atan t| <= 1) or 1/2 if less, it is x q(x^2) with x = t / tau and q the degree-9 polynomial that
+// interpolates g_r(tau x) / x at ten Chebyshev points of x^2 in [0, 1], fitted on the host for the
+// problem's B and C like the tyre curve's (one polynomial where the slip angle's and the tyre
+// curve's took two). Beyond, the slip angle from slip_atan and the curve by the library route.
 template <typename V>
-__device__ __forceinline__ void tyre_curves(const DevParams& P, V xf, V xr, V& gf, V& gr)
+__device__ __forceinline__ V rear_tyre_poly(const DevParams& P, V x)
+{
+    const V z = vmul(x, x);
+    V p = fold<V>(P, kFoldRyLast);
+#pragma unroll
+    for (int d = kTyreDeg - 1; d >= 0; --d) p = vfma(p, z, fold<V>(P, kFoldRy0 + d));
+    return vmul(x, p);
+}
+__device__ __forceinline__ float rear_tyre_beyond(const DevParams& P, float t)
+{
+    return tyre_curve_library(P, __fmul_rn(-P.tB, slip_atan(t)));
+}
+
+// The front tyre's curve at x_f = B alpha_f and the rear tyre's at its slip argument t_r, with one
+// vote of the warp for the library routes. The choice is made per particle.
+template <typename V>
+__device__ __forceinline__ void front_rear_tyres(const DevParams& P, V xf, V tr, V& gf, V& gr)
 {
     gf = tyre_poly(P, xf);
-    gr = tyre_poly(P, xr);
+    const V xr = vmul(tr, fold<V>(P, kFoldRInv));
+    gr = rear_tyre_poly(P, xr);
     if (__any_sync(__activemask(), beyond(xf, 1.0f) || beyond(xr, 1.0f))) {
-        const auto fix = [&](float xv, float gv) { return fabsf(xv) > 1.0f ? tyre_curve_library(P, xv) : gv; };
-        gf = each(xf, gf, fix);
-        gr = each(xr, gr, fix);
+        gf = each(xf, gf, [&](float x, float g) { return fabsf(x) > 1.0f ? tyre_curve_library(P, x) : g; });
+        gr = each(xr, tr, gr, [&](float x, float t, float g) { return fabsf(x) > 1.0f ? rear_tyre_beyond(P, t) : g; });
     }
+}
+
+// The rear tyre's curve of one particle or a pair, as the substep evaluates it (checking kernels).
+template <typename V>
+__device__ __forceinline__ V rear_tyre(const DevParams& P, V tr)
+{
+    const V xr = vmul(tr, fold<V>(P, kFoldRInv));
+    V gr = rear_tyre_poly(P, xr);
+    if (__any_sync(__activemask(), beyond(xr, 1.0f)))
+        gr = each(xr, tr, gr, [&](float x, float t, float g) { return fabsf(x) > 1.0f ? rear_tyre_beyond(P, t) : g; });
+    return gr;
 }
 
 // One explicit-Euler substep of one particle (V = float) or of two particles side by side
@@ -518,15 +576,16 @@ __device__ __forceinline__ void bicycle_substep(const DevParams& P, const TP& tr
     const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
     const V tf = vmul(vfma(fold<V>(P, kFoldLf), r, vy), ivx);    // (v_y + l_f r) / v_x
     const V tr = vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx);   // (v_y - l_r r) / v_x
-    V atf, atr;
-    slip_atans(P, tf, tr, atf, atr);
-    const V af = vfma(atf, fold<V>(P, kFoldM1), u.steer);  // alpha_f
-    const V bf = vmul(fold<V>(P, kFoldTB), af);            // B alpha_f
-    const V br = vmul(fold<V>(P, kFoldNTB), atr);          // B alpha_r
     V gf, gr;  // F_f / D_f, F_r / D_r
     if constexpr (POLY) {
-        tyre_curves(P, bf, br, gf, gr);
+        const V af = vfma(slip_atan_v(P, tf), fold<V>(P, kFoldM1), u.steer);  // alpha_f
+        front_rear_tyres(P, vmul(fold<V>(P, kFoldTB), af), tr, gf, gr);        // at B alpha_f, t_r
     } else {
+        V atf, atr;
+        slip_atans(P, tf, tr, atf, atr);
+        const V af = vfma(atf, fold<V>(P, kFoldM1), u.steer);  // alpha_f
+        const V bf = vmul(fold<V>(P, kFoldTB), af);            // B alpha_f
+        const V br = vmul(fold<V>(P, kFoldNTB), atr);          // B alpha_r
         const auto lib = [&](float a) { return tyre_curve_library(P, a); };
         gf = each(bf, lib);
         gr = each(br, lib);

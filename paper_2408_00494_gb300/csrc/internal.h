@@ -54,6 +54,10 @@ cudaError_t tyre_curve_launch(const DevParams& dp, const float* x, float* y, int
 // Coefficients c_0..c_9 of p with sin(C atan x) = x p(x^2) on |x| <= 1 (host, double precision;
 // c holds kTyreDeg + 1 = 10 floats).
 void tyre_curve_fit(double C, float* c);
+// The rear tyre's polynomial in x = t / tau (rear_tyre in device.cuh): tau for B, and c_0..c_9 for B, C.
+double rear_tyre_tau(double B);
+void rear_tyre_fit(double B, double C, float* c);
+cudaError_t rear_tyre_launch(const DevParams& dp, const float* t, float* y, int64_t n, cudaStream_t st);
 
 // Weights + update: the number of blocks for K samples, and the launch.
 int update_blocks(int K);

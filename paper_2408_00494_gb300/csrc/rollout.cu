@@ -146,6 +146,29 @@ cudaError_t tyre_curve_launch(const DevParams& dp, const float* x, float* y, int
     return cudaGetLastError();
 }
 
+// Pairs of values through the packed form (the single-solve kernel's two particles per lane); an odd
+// last value alone.
+__global__ void rear_tyre_kernel(const DevParams dp, const float* __restrict__ t, float* __restrict__ y, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * i + 1 < n) {
+        const float2 g = rear_tyre(dp, make_float2(t[2 * i], t[2 * i + 1]));
+        y[2 * i] = g.x;
+        y[2 * i + 1] = g.y;
+    } else if (2 * i < n) {
+        y[2 * i] = rear_tyre(dp, t[2 * i]);
+    }
+}
+
+cudaError_t rear_tyre_launch(const DevParams& dp, const float* t, float* y, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t pairs = (n + 1) / 2;
+    rear_tyre_kernel<<<(unsigned)((pairs + threads - 1) / threads), threads, 0, st>>>(dp, t, y, n);
+    return cudaGetLastError();
+}
+
 cudaError_t philox_launch(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;

@@ -132,6 +132,9 @@ int validate(const bssmppi_params* p, std::string& why)
     if (p->model != BSSMPPI_MODEL_BICYCLE6 && p->model != BSSMPPI_MODEL_DOUBLE_INT4 && p->model != BSSMPPI_MODEL_WHEELS8)
         return bad("unknown model");
     if (p->model == BSSMPPI_MODEL_BICYCLE6 && p->ey_index != 4) return bad("bicycle model constrains e_y: ey_index must be 4");
+    if (p->model != BSSMPPI_MODEL_DOUBLE_INT4 &&
+        (!(p->tire_B > 0.0f) || !(p->tire_C > 0.0f) || !std::isfinite(p->tire_B) || !std::isfinite(p->tire_C)))
+        return bad("the tyre curve needs finite B > 0 and C > 0");
     if (p->model == BSSMPPI_MODEL_WHEELS8 && p->ey_index != 6) return bad("wheel-speed model constrains e_y: ey_index must be 6");
     if (p->model == BSSMPPI_MODEL_WHEELS8 && p->M > 128) return bad("the wheel-speed model takes M <= 128");
     if (p->model == BSSMPPI_MODEL_WHEELS8 &&
@@ -199,22 +202,26 @@ void release(bssmppi_ctx* h)
 
 void bss::set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
-// Validates the parameters and derives the kernels' constants: lane mapping (seg, spw, P),
-// Cholesky factors, Sigma_eps^-1, the back-off nu, the Philox round keys and the model constants.
-// The tyre curve's polynomial: p(z) interpolates q(z) = sin(C atan sqrt z) / sqrt z at the ten
-// Chebyshev points z_k = (1 + cos(pi (k + 1/2) / 10)) / 2 of [0, 1] (q is analytic there, with its
-// nearest singularity at z = -1, so the interpolant is within about 4e-8 of it). The Chebyshev
+// The even-polynomial interpolation behind both tyre fits: c_0..c_9 such that f(x) ~ sum_i c_i x^(2i)
+// on |x| <= 1, f even (given as g(x) = f(x) for x in (0, 1]). p(z) interpolates q(z) = f(sqrt z) at
+// the ten Chebyshev points z_k = (1 + cos(pi (k + 1/2) / 10)) / 2 of [0, 1]. The Chebyshev
 // coefficients come from the discrete cosine sums; the three-term recurrence
 // T_{j+1} = 2u T_j - T_{j-1} turns them into powers of u = 2z - 1, and the binomial expansion into
 // powers of z. Everything is in double precision; the coefficients are rounded to FP32 at the end.
-void bss::tyre_curve_fit(double C, float* c)
+// The tyre curve's q(z) = sin(C atan sqrt z) / sqrt z is analytic on [0, 1] with its nearest
+// singularity at z = -1, so the interpolant is within about 4e-8 of it. The rear tyre's, in x = t / tau
+// with tau = tan(1/B) (or 1/2 if less), q(z) = sin(C atan(-B atan(tau sqrt z))) / sqrt z, has its
+// nearest singularity where B atan(tau x) = +-i, at z = -tanh(1/B)^2 / tau^2 (about -0.99 at B = 10),
+// no nearer in relative terms.
+template <typename G>
+static void even_poly_fit(G g, float* c)
 {
-    constexpr int N = kTyreDeg + 1;
+    constexpr int N = bss::kTyreDeg + 1;
     const double pi = 3.14159265358979323846;
     double f[N], a[N];
     for (int k = 0; k < N; ++k) {
         const double z = 0.5 * (1.0 + std::cos(pi * (k + 0.5) / N));
-        f[k] = std::sin(C * std::atan(std::sqrt(z))) / std::sqrt(z);
+        f[k] = g(std::sqrt(z));
     }
     for (int j = 0; j < N; ++j) {
         double sum = 0.0;
@@ -244,6 +251,25 @@ void bss::tyre_curve_fit(double C, float* c)
     for (int i = 0; i < N; ++i) c[i] = (float)pz[i];
 }
 
+void bss::tyre_curve_fit(double C, float* c)
+{
+    even_poly_fit([&](double x) { return std::sin(C * std::atan(x)) / x; }, c);
+}
+
+double bss::rear_tyre_tau(double B)
+{
+    const double half = 0.5;
+    return 1.0 / B < std::atan(half) ? std::tan(1.0 / B) : half;
+}
+
+void bss::rear_tyre_fit(double B, double C, float* c)
+{
+    const double tau = rear_tyre_tau(B);
+    even_poly_fit([&](double x) { return std::sin(C * std::atan(-B * std::atan(tau * x))) / x; }, c);
+}
+
+// Validates the parameters and derives the kernels' constants: lane mapping (seg, spw, P),
+// Cholesky factors, Sigma_eps^-1, the back-off nu, the Philox round keys and the model constants.
 int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::string& why)
 {
     int rc = validate(p, why);
@@ -357,6 +383,9 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     float tyre[kTyreDeg + 1];
     tyre_curve_fit(p->tire_C, tyre);
     for (int i = 0; i <= kTyreDeg; ++i) d.fold[kFoldTy0 + i] = tyre[i];
+    rear_tyre_fit(p->tire_B, p->tire_C, tyre);
+    for (int i = 0; i <= kTyreDeg; ++i) d.fold[kFoldRy0 + i] = tyre[i];
+    d.fold[kFoldRInv] = (float)(1.0 / rear_tyre_tau(p->tire_B));
     for (int i = kFoldOne; i < kFoldN; ++i) d.fold[i] = fold_fixed(i);
     for (int i = 0; i < kFoldN; ++i) d.fold2[i] = make_float2(d.fold[i], d.fold[i]);
     return BSSMPPI_OK;
@@ -838,6 +867,25 @@ int bssmppi_tyre_curve(bssmppi_t h, const float* d_x, float* d_y, int64_t n, voi
     if (n < 0 || (n > 0 && (!d_x || !d_y))) return fail(h, BSSMPPI_EINVAL, "tyre_curve: bad arguments");
     cudaError_t e = bss::tyre_curve_launch(h->dp, d_x, d_y, n, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(h, e, "tyre_curve");
+}
+
+int bssmppi_rear_tyre(bssmppi_t h, const float* d_t, float* d_y, int64_t n, void* cuda_stream)
+{
+    if (!h) return fail(nullptr, BSSMPPI_EINVAL, "NULL handle");
+    if (n < 0 || (n > 0 && (!d_t || !d_y))) return fail(h, BSSMPPI_EINVAL, "rear_tyre: bad arguments");
+    cudaError_t e = bss::rear_tyre_launch(h->dp, d_t, d_y, n, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? BSSMPPI_OK : cuda_fail(h, e, "rear_tyre");
+}
+
+int bssmppi_rear_tyre_coefficients(double B, double C, float* h_c, int32_t n, double* h_tau)
+{
+    if (!h_c || !h_tau || n < bss::kTyreDeg + 1 || !(B > 0.0) || !(C > 0.0) || !std::isfinite(B) || !std::isfinite(C))
+        return fail(nullptr, BSSMPPI_EINVAL, "rear_tyre_coefficients: needs B, C > 0 and room for 10 coefficients");
+    float c[bss::kTyreDeg + 1];
+    bss::rear_tyre_fit(B, C, c);
+    for (int i = 0; i <= bss::kTyreDeg; ++i) h_c[i] = c[i];
+    *h_tau = bss::rear_tyre_tau(B);
+    return BSSMPPI_OK;
 }
 
 int bssmppi_tyre_curve_coefficients(double C, float* h_c, int32_t n)

@@ -91,5 +91,6 @@ def test_measurement_and_checking_entry_points_validate_arguments_on_host():
         assert rc == -1 and "iters" in bssmppi.last_error(None)
     assert L.bssmppi_fp32_peak(0, 16, None, None, ctypes.byref(tf), ctypes.byref(sms)) == -1
     assert L.bssmppi_tyre_curve(None, None, None, 4, None) == -1
+    assert L.bssmppi_rear_tyre(None, None, None, 4, None) == -1
     c = (ctypes.c_float * 10)()
     assert L.bssmppi_tyre_curve_coefficients(1.9, c, 9) == -1  # room for fewer than ten coefficients

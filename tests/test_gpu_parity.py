@@ -186,6 +186,35 @@ def test_tyre_curve_against_fp64(C):
     assert np.array_equal(y[:n // 2], -y[n // 2:n])
 
 
+@pytest.mark.parametrize("which", ["bicycle", "wheels"])
+def test_rear_tyre_against_fp64(which):
+    """The substep's rear tyre curve sin(C atan(-B atan t)) as one polynomial in t / tau, taken in
+    packed pairs as the solve takes them: within 4e-7 of FP64 on |t| < tau (and odd bit for bit); the
+    route beyond (slip_atan, then the library's atanf and hardware sine) within 3e-6 (B times the
+    slip angle's ulp through the tyre curve, plus atanf's and the sine's errors); pairs with one
+    value on each side take each value's own route."""
+    p = workload.config0() if which == "bicycle" else workload.wheels_problem(8, 4, 3)
+    B, C = float(np.float32(p.tire_B)), float(np.float32(p.tire_C))
+    _, tau = bssmppi.rear_tyre_coefficients(B, C)
+    pos = np.linspace(0.0, tau * (1.0 - 1e-6), 1 << 18).astype(np.float32)
+    inner = np.concatenate([pos, -pos])
+    far = np.concatenate([np.geomspace(tau * 1.0001, 1e4, 1 << 14), -np.geomspace(tau * 1.0001, 1e4, 1 << 14)])
+    far = far.astype(np.float32)
+    mixed = np.stack([pos[::16][:far.size // 2], far[:far.size // 2]], axis=1).reshape(-1)
+    t = np.concatenate([inner, far, mixed])
+    c = bssmppi.Controller(p)
+    y = torch.zeros(t.size, device="cuda")
+    bssmppi.rear_tyre(c.h, _dev(t), y)
+    c.close()
+    y = y.cpu().numpy().astype(np.float64)
+    ref = np.sin(C * np.arctan(-B * np.arctan(t.astype(np.float64))))
+    n, m = inner.size, inner.size + far.size
+    assert np.abs(y[:n] - ref[:n]).max() <= 4e-7, np.abs(y[:n] - ref[:n]).max()
+    assert np.abs(y[n:m] - ref[n:m]).max() <= 3e-6, np.abs(y[n:m] - ref[n:m]).max()
+    assert np.abs(y[m:] - ref[m:]).max() <= 3e-6, np.abs(y[m:] - ref[m:]).max()
+    assert np.array_equal(y[:n // 2], -y[n // 2:n])
+
+
 @pytest.mark.parametrize("model", ["bicycle", "double_integrator"])
 def test_model_step_matches_oracle(model):
     if model == "bicycle":
