@@ -202,6 +202,19 @@ void release(bssmppi_ctx* h)
 
 void bss::set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
+// SM count of the current device (the lane mapping's occupancy rule); without one, a count so large
+// that the rule keeps one particle per lane.
+static int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1) {
+        (void)cudaGetLastError();
+        return 1 << 20;
+    }
+    return sms;
+}
+
 // The even-polynomial interpolation behind both tyre fits: c_0..c_9 such that f(x) ~ sum_i c_i x^(2i)
 // on |x| <= 1, f even (given as g(x) = f(x) for x in (0, 1]). p(z) interpolates q(z) = f(sqrt z) at
 // the ten Chebyshev points z_k = (1 + cos(pi (k + 1/2) / 10)) / 2 of [0, 1]. The Chebyshev
@@ -284,12 +297,25 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
         why = "Sigma_eps must be symmetric positive definite";
         return BSSMPPI_EINVAL;
     }
-    // Mapping of particles to lanes.
+    // Mapping of particles to lanes: a segment of seg lanes (a power of two) per sample, P particles
+    // per lane (lane l holds particles l, l + seg, ...). From 8 to 32 particles, two per lane in half
+    // as many lanes when the solve still has a warp's worth of samples for about 12 warps per SM (K
+    // above ~2000 warps on 152 SMs): that steps them in packed pairs and halves the per-step merge
+    // and cost work per particle, but fewer warps hide less latency (at 3-7 warps per SM it was
+    // 40 % slower). Otherwise seg is the next power of two >= M up to a warp, and P covers the rest.
     int seg = 1;
-    while (seg < p->M && seg < 32) seg <<= 1;
-    const int ppl = (p->M + seg - 1) / seg;
-    P = 1;
-    while (P < ppl) P <<= 1;
+    int seg2 = 1;
+    while (2 * seg2 < p->M) seg2 <<= 1;
+    const long warps2 = ((long)p->K * seg2 + 31) / 32;  // sample groups of 32 / seg2 samples
+    if (p->M >= 8 && p->M <= 32 && warps2 >= 12L * device_sms()) {
+        seg = seg2;
+        P = 2;
+    } else {
+        while (seg < p->M && seg < 32) seg <<= 1;
+        const int ppl = (p->M + seg - 1) / seg;
+        P = 1;
+        while (P < ppl) P <<= 1;
+    }
     d.K = p->K; d.M = p->M; d.T = p->T; d.nx = nx;
     d.seg = seg; d.spw = 32 / seg;
     d.dist_half = seg * P / 2;  // = 2^ceil(log2 M) / 2 for every M (seg P is the next power of two)

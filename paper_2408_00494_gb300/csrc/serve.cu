@@ -12,7 +12,7 @@
 // A batch is one fixed sequence, captured once per slot as a CUDA graph and replayed:
 //   H2D copy of the batch descriptors (fixed size)
 //   -> three persistent rollout kernels in parallel branches, one per particles-per-lane class
-//      (P = 1, 2, 4 for M <= 32, 64, 128); their warps pull (request, sample-group) items with an
+//      (P = 1, 2, 4 for M < 8, M <= 64, M <= 128); their warps pull (request, sample-group) items with an
 //      atomic counter and run the same per-group body as the single-solve kernel. The constants
 //      the batch's vehicles share (a batch holds controllers of one constants class) are a kernel
 //      parameter, so the body reads them as instruction operands and steps particle pairs with
@@ -72,8 +72,9 @@ struct __align__(16) ServeItem {
     int n_track_mask, pad[3];
 };
 
-// Largest sample count per warp of a particle class: 32 / seg, seg the smallest power of two >= M.
-__host__ __device__ constexpr int serve_spw_max(int cls) { return cls == 0 ? kServeSpwMax : 1; }
+// Largest sample count per warp of a particle class: 32 / seg for its smallest segment (class 0:
+// M = 2 on 2 lanes; class 1: M = 8 on 4 lanes, two particles per lane; class 2: a whole warp).
+__host__ __device__ constexpr int serve_spw_max(int cls) { return cls == 0 ? kServeSpwMax : (cls == 1 ? 8 : 1); }
 
 // Blocks of kServeWarps warps per SM for the register bound: 6, 5 and 4 for 1, 2 and 4 particles
 // per lane (80, 102 and 128 registers), the tightest bounds at which the loop over work items
@@ -327,7 +328,10 @@ size_t request_floats(int K, int T)
     return round((size_t)K * T * 2) + round(K) + round(K);
 }
 
-int class_of(int M) { return M <= 32 ? 0 : (M <= 64 ? 1 : 2); }
+// Particle classes by particles per lane: M < 8 one (segments of the next power of two >= M lanes),
+// 8 <= M <= 64 two (segments of the next power of two >= M / 2 lanes: packed pairs, and half the
+// per-step merge and cost work per particle; a batch has warps enough to hide latency), M > 64 four.
+int class_of(int M) { return M < 8 ? 0 : (M <= 64 ? 1 : 2); }
 
 // Issue one batch on the slot's streams (also used, once, under capture to build the graph).
 cudaError_t issue_batch(bssmppi_server* s, Slot& sl)
@@ -424,11 +428,15 @@ void fill_descriptors(Slot& sl)
         ServeReq& q = reqs[i];
         std::memset(&q, 0, sizeof(q));
         q.ctrl = p.ctrl; q.K = p.K; q.M = p.M; q.T = p.T;
-        int seg = 1;
-        while (seg < p.M && seg < 32) seg <<= 1;
-        const int ppl = (p.M + seg - 1) / seg;
-        int P = 1;
-        while (P < ppl) P <<= 1;
+        int seg = 1, P = 1;
+        if (class_of(p.M) == 1) {
+            while (2 * seg < p.M) seg <<= 1;
+            P = 2;
+        } else {
+            while (seg < p.M && seg < 32) seg <<= 1;
+            const int ppl = (p.M + seg - 1) / seg;
+            while (P < ppl) P <<= 1;
+        }
         q.seg = seg; q.spw = 32 / seg; q.uniform = (p.M == seg * P) ? 1 : 0;
         q.dist_half = seg * P / 2;
         q.cls = class_of(p.M);
