@@ -39,14 +39,14 @@ import workload  # noqa: E402
 METRIC = "particle-steps/s (K*M*T per solve)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one rollout_kernel launch, from one
 # ncu capture of the current kernel on each workload (None where none was taken).
-ROLLOUT_DRAM_BYTES = {"racing_K4096_M64_T40": 125184}
+ROLLOUT_DRAM_BYTES = {"racing_K4096_M64_T40": 127488}
 # Device facts for the nominal ALU peak (GB300: 152 SMs, 128 FP32 lanes per SM, max SM clock); the
 # roofline's denominator is the FP32 peak measured on the device in the same run (bssmppi_fp32_peak).
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # Issue-slot and FMA-pipe activity of the rollout kernel from the committed ncu capture of the
 # current kernel (sm__inst_executed.avg.per_cycle_active / 4 and the FMA pipe's share of its peak).
-ROLLOUT_NCU = {"racing_K4096_M64_T40": {"issue_slots_busy": 2.81 / 4, "fma_pipe_of_peak": 0.404,
-                                        "lane_instructions_per_particle_step": 706,
+ROLLOUT_NCU = {"racing_K4096_M64_T40": {"issue_slots_busy": 2.85 / 4, "fma_pipe_of_peak": 0.401,
+                                        "lane_instructions_per_particle_step": 691,
                                         "source": "profiles/rollout_kernel_racing_K4096_M64_T40.md"}}
 
 
