@@ -20,6 +20,10 @@ __host__ __device__ constexpr int model_s_index(int model) { return model == 0 ?
 // states (the racing cost weights v_x, e_psi and e_y of the bicycle) merges and costs only those
 // belief means; mask 0 stands for a set known at run time only.
 constexpr int kRacingCostMask = (1 << 0) | (1 << 3) | (1 << 4);
+// A general constraint set on the road plane touches e_y and s only; with the racing cost, the
+// full-belief rollout then keeps the means of v_x, e_psi, e_y and s and the covariance of (e_y, s).
+constexpr int kPlaneConMask = (1 << 4) | (1 << 5);
+constexpr int kPlaneMeanMask = kRacingCostMask | kPlaneConMask;
 __host__ __device__ constexpr int mask_count(int m)
 {
     int n = 0;
@@ -889,8 +893,9 @@ struct ConSet {
     float o[kMaxCon][kNxMax];  // disk centre on its two states (0 elsewhere)
 };
 
-// c_q(m) and eta = grad c_q(m).
-template <int NX>
+// c_q(m) and eta = grad c_q(m). CM != 0: the set touches the states of CM only (a and o vanish
+// elsewhere, so the skipped terms are exact zeros), and eta is written on CM only.
+template <int NX, int CM = 0>
 __device__ __forceinline__ float constraint_value(const ConSet& cs, int q, const float (&m)[NX], float (&eta)[NX])
 {
     float v;
@@ -898,6 +903,7 @@ __device__ __forceinline__ float constraint_value(const ConSet& cs, int q, const
         v = -cs.b[q];
 #pragma unroll
         for (int l = 0; l < NX; ++l) {
+            if (CM != 0 && !((CM >> l) & 1)) continue;
             v = fmaf(cs.a[q][l], m[l], v);
             eta[l] = cs.a[q][l];
         }
@@ -905,6 +911,7 @@ __device__ __forceinline__ float constraint_value(const ConSet& cs, int q, const
         v = cs.b[q];
 #pragma unroll
         for (int l = 0; l < NX; ++l) {
+            if (CM != 0 && !((CM >> l) & 1)) continue;
             const float d = cs.a[q][l] * (m[l] - cs.o[q][l]);
             v = fmaf(-d, d, v);
             eta[l] = -2.0f * d;
@@ -915,7 +922,9 @@ __device__ __forceinline__ float constraint_value(const ConSet& cs, int q, const
 
 // Eq. "DCBFchoice0" and Eq. "DCBFchoice": h = min_q -c_q(m) - nu_q sqrt(eta_q^T Sigma eta_q), with the
 // covariance packed (lower triangle by rows).
-template <int NX>
+// CM != 0: the set touches the states of CM only; the covariance is read on CM x CM (the terms of
+// other states carry eta = 0 and would add exact zeros).
+template <int NX, int CM = 0>
 __device__ __forceinline__ float general_barrier(const ConSet& cs, const float (&m)[NX], const float (&C)[NX * (NX + 1) / 2])
 {
     float h = INFINITY;
@@ -923,13 +932,15 @@ __device__ __forceinline__ float general_barrier(const ConSet& cs, const float (
     for (int q = 0; q < kMaxCon; ++q) {
         if (q >= cs.n) break;
         float eta[NX];
-        const float cv = constraint_value<NX>(cs, q, m, eta);
+        const float cv = constraint_value<NX, CM>(cs, q, m, eta);
         float quad = 0.0f;
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
+            if (CM != 0 && !((CM >> i) & 1)) continue;
             float r = 0.5f * C[i * (i + 1) / 2 + i] * eta[i];
 #pragma unroll
-            for (int j = 0; j < i; ++j) r = fmaf(C[i * (i + 1) / 2 + j], eta[j], r);
+            for (int j = 0; j < i; ++j)
+                if (CM == 0 || ((CM >> j) & 1)) r = fmaf(C[i * (i + 1) / 2 + j], eta[j], r);
             quad = fmaf(2.0f * eta[i], r, quad);
         }
         h = fminf(h, -cv - cs.nu[q] * sqrtf(fmaxf(quad, 0.0f)));
@@ -938,7 +949,7 @@ __device__ __forceinline__ float general_barrier(const ConSet& cs, const float (
 }
 
 // The collision indicator of Eq. "CostFunction" for the general set: some c_q(m) > 0.
-template <int NX>
+template <int NX, int CM = 0>
 __device__ __forceinline__ bool any_constraint_broken(const ConSet& cs, const float (&m)[NX])
 {
     bool broken = false;
@@ -946,18 +957,20 @@ __device__ __forceinline__ bool any_constraint_broken(const ConSet& cs, const fl
     for (int q = 0; q < kMaxCon; ++q) {
         if (q >= cs.n) break;
         float eta[NX];
-        broken |= constraint_value<NX>(cs, q, m, eta) > 0.0f;
+        broken |= constraint_value<NX, CM>(cs, q, m, eta) > 0.0f;
     }
     return broken;
 }
 
 // Quadratic part of the running cost, (m - x_g)^T diag(W) (m - x_g).
-template <int NX>
+// MM != 0: W vanishes outside MM (the skipped terms are exact zeros).
+template <int NX, int MM = 0>
 __device__ __forceinline__ float quad_cost(const DevParams& P, const float* W, const float (&m)[NX])
 {
     float c = 0.0f;
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
+        if (MM != 0 && !((MM >> i) & 1)) continue;
         const float d = m[i] - P.xg[i];
         c = fmaf(W[i] * d, d, c);
     }

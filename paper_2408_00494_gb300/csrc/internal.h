@@ -37,7 +37,8 @@ struct TailIO {
 };
 size_t rollout_smem_bytes(const DevParams& dp, int wpb);
 // full: the full-belief kernel variant (re-sampled particles and/or a general constraint set).
-cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L);
+cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L,
+                            const ConSet* cs = nullptr);
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,
                            const float* Sigma0, const float* v, const uint32_t* ctr, float* S, float* eps, float* mean,
                            float* var, const TailIO& tail, const ConSet& cs, cudaStream_t st);

@@ -54,12 +54,12 @@ size_t rollout_smem_bytes(const DevParams& dp, int wpb)
 // Variants: the racing barrier on persistent particles, with compensated or naive reductions; and
 // the full-belief variant (re-sampled particles and/or the general constraint set), always with
 // the compensated sums (the host rejects it with naive reductions).
-cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L)
+cudaError_t rollout_prepare(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L, const ConSet* cs)
 {
     if (full && !comp) return cudaErrorInvalidValue;
-    if (dp.nx == 8) return prepare_model<2>(dp, P, comp, full, L);
-    if (dp.nx == 6) return prepare_model<0>(dp, P, comp, full, L);
-    return prepare_model<1>(dp, P, comp, full, L);
+    if (dp.nx == 8) return prepare_model<2>(dp, P, comp, full, L, cs);
+    if (dp.nx == 6) return prepare_model<0>(dp, P, comp, full, L, cs);
+    return prepare_model<1>(dp, P, comp, full, L, cs);
 }
 
 cudaError_t rollout_launch(const DevParams& dp, int P, bool comp, const RollLaunch& L, const float* x0,

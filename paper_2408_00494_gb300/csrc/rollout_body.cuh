@@ -213,37 +213,78 @@ __device__ __forceinline__ void butterfly_sum(float (&v)[N], int seg)
 // Full belief of one sample for the re-sampling reading of Algorithm 2: every mean and the unbiased
 // covariance (packed lower triangle by rows), in two passes over the segment: the sums give the
 // means, then the centred products are summed. xor-butterfly sums are symmetric in the two partners,
-// so every lane of the segment ends with bit-identical moments.
-template <int NX, int P, typename IT>
+// so every lane of the segment ends with bit-identical moments. MM = kPlaneMeanMask: only the means
+// of MM and the covariance on kPlaneConMask x kPlaneConMask (a constraint set on the road plane, no
+// re-sampling), the same values as the full computation gives for them; other entries untouched.
+template <int NX, int P, int MM = 0, typename IT>
 __device__ __forceinline__ void belief_moments_full(const IT& dp, const float (&x)[P][NX], int ls, int seg,
                                                     float (&mean)[NX], float (&C)[NX * (NX + 1) / 2])
 {
-    float s[NX];
+    if constexpr (MM != 0) {
+        static_assert(MM == kPlaneMeanMask, "the reduced full belief is built for the road plane");
+        constexpr int NM = mask_count(MM), NC = mask_count(kPlaneConMask), NE = NC * (NC + 1) / 2;
+        float s[NM];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) {
-        s[i] = 0.0f;
+        for (int a = 0; a < NM; ++a) {
+            const int i = mask_nth(MM, a);
+            s[a] = 0.0f;
 #pragma unroll
-        for (int p = 0; p < P; ++p) s[i] += (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
-    }
-    butterfly_sum<NX>(s, seg);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) mean[i] = s[i] * dp.invM;
-#pragma unroll
-    for (int i = 0; i < NX; ++i) {
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            float c = 0.0f;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float d = (x[p][i] - mean[i]) * (x[p][j] - mean[j]);
-                c += (dp.uniform || ls + seg * p < dp.M) ? d : 0.0f;
-            }
-            C[i * (i + 1) / 2 + j] = c;
+            for (int p = 0; p < P; ++p) s[a] += (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
         }
-    }
-    butterfly_sum<NX * (NX + 1) / 2>(C, seg);
+        butterfly_sum<NM>(s, seg);
 #pragma unroll
-    for (int e = 0; e < NX * (NX + 1) / 2; ++e) C[e] *= dp.invM1;
+        for (int a = 0; a < NM; ++a) mean[mask_nth(MM, a)] = s[a] * dp.invM;
+        float c[NE];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+#pragma unroll
+            for (int b = 0; b <= a; ++b) {
+                const int i = mask_nth(kPlaneConMask, a), j = mask_nth(kPlaneConMask, b);
+                float acc = 0.0f;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float d = (x[p][i] - mean[i]) * (x[p][j] - mean[j]);
+                    acc += (dp.uniform || ls + seg * p < dp.M) ? d : 0.0f;
+                }
+                c[a * (a + 1) / 2 + b] = acc;
+            }
+        }
+        butterfly_sum<NE>(c, seg);
+#pragma unroll
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b) {
+                const int i = mask_nth(kPlaneConMask, a), j = mask_nth(kPlaneConMask, b);
+                C[i * (i + 1) / 2 + j] = c[a * (a + 1) / 2 + b] * dp.invM1;
+            }
+    } else {
+        float s[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            s[i] = 0.0f;
+#pragma unroll
+            for (int p = 0; p < P; ++p) s[i] += (dp.uniform || ls + seg * p < dp.M) ? x[p][i] : 0.0f;
+        }
+        butterfly_sum<NX>(s, seg);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) mean[i] = s[i] * dp.invM;
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                float c = 0.0f;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float d = (x[p][i] - mean[i]) * (x[p][j] - mean[j]);
+                    c += (dp.uniform || ls + seg * p < dp.M) ? d : 0.0f;
+                }
+                C[i * (i + 1) / 2 + j] = c;
+            }
+        }
+        butterfly_sum<NX * (NX + 1) / 2>(C, seg);
+#pragma unroll
+        for (int e = 0; e < NX * (NX + 1) / 2; ++e) C[e] *= dp.invM1;
+    }
 }
 
 // In-place Cholesky factorisation of a packed (lower, by rows) PSD matrix; a pivot that is not
@@ -328,6 +369,8 @@ __host__ __device__ constexpr int roll_max_threads()
 // batch's vehicles share, stays in kernel parameter space.
 // MM: 0, or the fixed set of states the cost weights (a mask holding e_y; the caller guarantees that
 // Q and Qf vanish outside it and that nothing is recorded): only those means are merged and costed.
+// With FULL, MM = kPlaneMeanMask: a constraint set on e_y and s only, no re-sampling, nothing recorded;
+// the means of MM and the covariance of (e_y, s) are kept.
 template <int MODEL, int P, bool COMP, bool FULL = false, typename Tab = float, bool PACK = true, bool UTRIG = false,
           typename IT = DevParams, bool TYRE_POLY = true, int MM = 0>
 __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it, const RollIO& io,
@@ -338,7 +381,8 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
     constexpr int NX = model_nx(MODEL);
     constexpr int EY = MODEL == 0 ? 4 : (MODEL == 2 ? 6 : 1);
     constexpr int SI = model_s_index(MODEL);  // path coordinate, carried relative to its start (or -1)
-    static_assert(MM == 0 || !FULL, "the full belief merges every mean");
+    static_assert(MM == 0 || !FULL || MM == kPlaneMeanMask, "the full belief merges every mean, or the plane's");
+    constexpr int FCM = (FULL && MM != 0) ? kPlaneConMask : 0;  // the states a constraint set touches
     constexpr bool RECORDS = MM == 0;         // a fixed cost set runs without recording
     const int lane = threadIdx.x & (kWarp - 1);
     const int seg = it.seg;
@@ -416,7 +460,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
             for (int i = 0; i < NX; ++i)
 #pragma unroll
                 for (int j = 0; j <= i; ++j) C0[i * (i + 1) / 2 + j] = io.Sigma0 ? io.Sigma0[i * NX + j] : 0.0f;
-            h_cur = general_barrier<NX>(*cs, mean, C0);
+            h_cur = general_barrier<NX, FCM>(*cs, mean, C0);
         } else {
             h_cur = belief_barrier(dp, mean[EY], var0_ey);
         }
@@ -443,7 +487,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
         const float csafe = dp.Csafe * fmaxf(fmaf(dp.one_m_gamma, h_prev, -h_cur), 0.0f);
         float q;
         if constexpr (FULL) {
-            q = general ? quad_cost<NX>(dp, dp.Q, mean) + (any_constraint_broken<NX>(*cs, mean) ? dp.Cobs : 0.0f)
+            q = general ? quad_cost<NX, MM>(dp, dp.Q, mean) + (any_constraint_broken<NX, FCM>(*cs, mean) ? dp.Cobs : 0.0f)
                         : state_cost<NX, EY>(dp, dp.Q, mean);
         } else {
             q = state_cost<NX, EY, MM>(dp, dp.Q, mean);
@@ -535,17 +579,21 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
         float h_next = 0.0f;
         if constexpr (FULL) {
             float C[NX * (NX + 1) / 2];
-            belief_moments_full<NX, P>(it, x, ls, seg, mean, C);
+            belief_moments_full<NX, P, MM>(it, x, ls, seg, mean, C);
+            if constexpr (MM == 0) {
 #pragma unroll
-            for (int i = 0; i < NX; ++i) var[i] = C[i * (i + 1) / 2 + i];
+                for (int i = 0; i < NX; ++i) var[i] = C[i * (i + 1) / 2 + i];
+            } else {
+                var[EY] = C[EY * (EY + 1) / 2 + EY];
+            }
             if (general) {
                 float ma[NX];
 #pragma unroll
                 for (int i = 0; i < NX; ++i) ma[i] = mean[i];
                 if constexpr (SI >= 0) ma[SI] += s0;
-                h_next = general_barrier<NX>(*cs, ma, C);
+                h_next = general_barrier<NX, FCM>(*cs, ma, C);
             }
-            if (dp.resample && t + 1 < it.T) {  // re-draw x^n_{t+1} ~ N(mean, cov) for the next step (stream 4)
+            if (MM == 0 && dp.resample && t + 1 < it.T) {  // re-draw x^n_{t+1} ~ N(mean, cov) for the next step (stream 4)
                 cholesky_packed_psd<NX>(C);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
@@ -574,7 +622,7 @@ __device__ __forceinline__ float rollout_group(const DevParams& dp, const IT& it
     // Terminal: phi(x_bar_T) + C_safe(z_T).
     float qT;
     if constexpr (FULL) {
-        qT = general ? quad_cost<NX>(dp, dp.Qf, mean) + (any_constraint_broken<NX>(*cs, mean) ? dp.Cobs : 0.0f)
+        qT = general ? quad_cost<NX, MM>(dp, dp.Qf, mean) + (any_constraint_broken<NX, FCM>(*cs, mean) ? dp.Cobs : 0.0f)
                      : state_cost<NX, EY>(dp, dp.Qf, mean);
     } else {
         qT = state_cost<NX, EY, MM>(dp, dp.Qf, mean);

@@ -421,7 +421,7 @@ inline cudaError_t plan_model(const DevParams& dp, int P, RollLaunch& L)
 // Per-model entry points (defined in rollout_model<MODEL>.cu): the launch plan and the launch of
 // the racing-barrier variants (compensated or naive reductions) and the full-belief variant.
 template <int MODEL>
-cudaError_t prepare_model(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L);
+cudaError_t prepare_model(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L, const ConSet* cs);
 template <int MODEL>
 cudaError_t launch_model_variant(const DevParams& dp, const RollIO& io, const TailIO& tail, const ConSet& cs, int P,
                                  bool comp, bool full, const RollLaunch& L, cudaStream_t st);

@@ -4,7 +4,7 @@
 namespace bss {
 
 template <>
-cudaError_t prepare_model<1>(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L)
+cudaError_t prepare_model<1>(const DevParams& dp, int P, bool comp, bool full, RollLaunch& L, const ConSet*)
 {
     if (full) return plan_model<1, true, true>(dp, P, L);
     return comp ? plan_model<1, true, false>(dp, P, L) : plan_model<1, false, false>(dp, P, L);

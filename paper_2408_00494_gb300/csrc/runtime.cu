@@ -709,7 +709,7 @@ int bssmppi_set_constraints(bssmppi_t h, const bssmppi_constraint* cons, int32_t
     bss::RollLaunch L;
     const bool full = h->dp.resample != 0 || n > 0;
     BSS_CUDA(h, cudaStreamSynchronize(h->stream));  // no solve may still read the old set's launch shape
-    BSS_CUDA(h, bss::rollout_prepare(h->dp, h->P, h->prm.compensated != 0, full, L));
+    BSS_CUDA(h, bss::rollout_prepare(h->dp, h->P, h->prm.compensated != 0, full, L, &cs));
     h->roll = L;
     h->cons = cs;
     drop_host_graphs(h);

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workload
-from tests.test_gpu_parity import assert_close, check_solve, gpu_solve
+from tests.test_gpu_parity import assert_close, check_solve, check_unrecorded, gpu_solve
 from tests.test_gpu_resample import redraw_atol
 from tests.test_oracle_solve import CORRELATED_W
 
@@ -50,6 +50,20 @@ def test_constraints_racing_obstacle_ahead(resample):
     x0[4] = 0.2
     p.constraints = _racing_cons(p, x0)
     check_solve(p, x0, v, ctr=11, mean_atol=redraw_atol if resample else None)
+
+
+@pytest.mark.parametrize("M", [20, 64, 128])
+def test_constraints_on_the_road_plane_without_recording(M):
+    """A set on e_y and s only (track edges and an obstacle), with the racing cost and no recording:
+    the build that keeps four means and the (e_y, s) covariance, against the oracle on every sample
+    (costs, weights, v+ isolated and end to end). M = 20 leaves lanes empty; M = 128 puts four
+    particles in a lane."""
+    p = workload.config0()
+    p.K, p.M, p.T = 384, M, 16
+    x0, v = workload.random_state(p, 60 + M), workload.random_nominal(p, 60 + M)
+    x0[4] = 0.2
+    p.constraints = _racing_cons(p, x0)
+    check_unrecorded(p, x0, v, ctr=13 + M)
 
 
 def test_constraints_full_size_sampled_parity():

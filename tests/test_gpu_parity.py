@@ -299,6 +299,19 @@ def test_unrecorded_solve_particle_counts(M, compensated):
     check_unrecorded(p, workload.random_state(p, 300 + M), workload.random_nominal(p, 300 + M), ctr=M + 5)
 
 
+@pytest.mark.parametrize("K,M", [(4096, 32), (4096, 20), (8192, 16), (16384, 8)])
+def test_two_particles_per_lane_mapping(K, M):
+    """From 8 to 32 particles a solve with enough samples for about 12 warps per SM runs two
+    particles per lane in segments of the next power of two >= M / 2 lanes (ragged at M = 20): the
+    recorded solve (every step's means and variances) and the unrecorded one (the racing-cost build)
+    against the oracle."""
+    p = workload.config0()
+    p.K, p.M, p.T = K, M, 10
+    x0, v = workload.random_state(p, 500 + M), workload.random_nominal(p, 500 + M)
+    check_solve(p, x0, v, ctr=M + 1)
+    check_unrecorded(p, x0, v, ctr=M + 2)
+
+
 def test_unrecorded_solve_with_every_state_weighted():
     """A cost that weights every state (the build with the run-time set of merged means)."""
     p = workload.config0()
