@@ -354,13 +354,13 @@ template <> __device__ __forceinline__ float fold<float>(const DevParams& P, int
 }
 template <> __device__ __forceinline__ float2 fold<float2>(const DevParams& P, int i) { return P.fold2[i]; }
 
-// atan t for the bicycle's slip angles, whose arguments (v_y + l_f r) / v_x and (v_y - l_r r) / v_x
+// atan t for the slip angles, whose arguments (v_y + l_f r) / v_x and (v_y - l_r r) / v_x
 // stay small while the tyres grip. For |t| <= 1/2, atan t = t + t z p(z) with z = t^2 and p of degree 4, its
 // coefficients fitted for the least maximum relative error on [0, 1/2] by Lawson's iteratively
 // reweighted least squares (fit_slip_atan.py beside this package): 5.3e-9 in exact arithmetic,
 // 0.72 FP32 ulp by Horner's rule with fused multiply-adds. Beyond, the library's atanf. The choice
-// is made per particle, so a result does not depend on which particles share a warp. (The
-// wheel-speed model keeps atanf for its slip angles: there the branch measured slower.)
+// is made per particle, so a result does not depend on which particles share a warp. Both
+// models take it for their slip angles (slip_atans: pairs of particles in packed instructions).
 __device__ __forceinline__ float slip_atan(float t)
 {
     if (fabsf(t) <= 0.5f) {
@@ -682,9 +682,9 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const TP& trk
     const V vx = X[0], vy = X[1], r = X[2], wf = X[3], wr = X[4];
     const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
     const V yf = vfma(fold<V>(P, kFoldLf), r, vy);                                         // v_y + l_f r
-    const auto sa = [](float a) { return atanf(a); };
-    const V af = vfma(each(vmul(yf, ivx), sa), fold<V>(P, kFoldM1), u.steer);               // alpha_f
-    const V nar = each(vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx), sa);                  // -alpha_r
+    V atf, nar;                                                                            // -alpha_r
+    slip_atans(P, vmul(yf, ivx), vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx), atf, nar);
+    const V af = vfma(atf, fold<V>(P, kFoldM1), u.steer);                                  // alpha_f
     const V vwf = vfma(vx, u.cs, vmul(yf, u.sn));                                          // front wheel's speed
     const auto slip = [&](float num, float vw) { return __fdividef(num, fmaxf(fabsf(vw), P.slip_floor)); };
     const V kf = each(vfma(fold<V>(P, kFoldWRw), wf, vmul(vwf, fold<V>(P, kFoldM1))), vwf, slip);
