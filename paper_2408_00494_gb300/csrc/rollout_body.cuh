@@ -361,8 +361,8 @@ __host__ __device__ constexpr int roll_max_threads()
 // registers of their own. UTRIG: my_u holds (u_0, u_1, sin u_0, cos u_0) per step (T x 4), so the
 // steering angle's sine and cosine are taken once per step by the lanes that draw the controls
 // instead of by every lane in every step; otherwise T x 2.
-// TYRE_POLY: the bicycle's tyre curve from its polynomial where one or two particles share a lane
-// (the library route at four and more, and wherever TYRE_POLY is off, measured faster there).
+// TYRE_POLY: the bicycle's tyre curves from their polynomials where one or two particles share a lane
+// (the library route at four and more, measured faster there, and wherever TYRE_POLY is off).
 // IT: the object holding the per-solve fields (the sizes K, M, T, seg, spw, uniform, dist_half, M's
 // reciprocals, k_off), the Philox round keys and the track's scale and mask. The single-solve kernel
 // passes dp itself; the server passes a per-warp item in shared memory while dp, the constants its

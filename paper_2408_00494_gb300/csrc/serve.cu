@@ -126,10 +126,10 @@ __global__ void __launch_bounds__(kServeWarps * kWarp, serve_min_blocks<P>())
         float* my_u = ubuf + (lane / rq.seg) * 2 * rq.T;
         // a class whose cost weights only v_x, e_psi and e_y merges and costs those means only
         if ((fleet.mean_mask & ~kRacingCostMask) == 0)
-            rollout_group<0, P, true, false, float, true, false, ServeItem, false, kRacingCostMask>(
+            rollout_group<0, P, true, false, float, true, false, ServeItem, true, kRacingCostMask>(
                 fleet, *it, io, cd.kappa, v, my_u, (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
         else
-            rollout_group<0, P, true, false, float, true, false, ServeItem, false>(
+            rollout_group<0, P, true, false, float, true, false, ServeItem, true>(
                 fleet, *it, io, cd.kappa, v, my_u, (int)item - rq.group_begin, ctrl_ctr[rq.ctrl]);
         __syncwarp();
     }
