@@ -163,6 +163,9 @@ size_t bssmppi_params_size(void);
  * (zero-initialised), the device-resident solve counter (0) and the reduction scratch) and copies
  * the curvature table. Synchronous. Returns EINVAL for out-of-range parameters, ENOMEM or ECUDA.
  * On success *out is a new handle; on failure *out is NULL and bssmppi_last_error(NULL) says why.
+ * The particles' placement in lanes depends on K, M and the device's SM count (from 8 to 32
+ * particles, two per lane once the solve fills about 12 warps per SM); the random draws do not, so
+ * two placements give the same solve up to the rounding order of the particle sums.
  */
 int bssmppi_create(const bssmppi_params* params, void* cuda_stream, bssmppi_t* out);
 

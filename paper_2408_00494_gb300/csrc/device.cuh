@@ -377,10 +377,20 @@ __device__ __forceinline__ float slip_atan(float t)
 __device__ __forceinline__ bool beyond(float x, float lim) { return fabsf(x) > lim; }
 __device__ __forceinline__ bool beyond(float2 x, float lim) { return fabsf(x.x) > lim || fabsf(x.y) > lim; }
 
+// slip_atan's polynomial for two particles side by side (each half rounds as slip_atan does).
+__device__ __forceinline__ float2 slip_poly2(const DevParams& P, float2 t)
+{
+    const float2 z = vmul(t, t);
+    float2 p = fold<float2>(P, kFoldSa0);
+#pragma unroll
+    for (int i = kFoldSa0 + 1; i <= kFoldSaLast; ++i) p = vfma(p, z, fold<float2>(P, i));
+    return vfma(vmul(t, z), p, t);
+}
+
 // slip_atan of the front and rear slip arguments of one particle, or of two particles side by side:
-// for pairs, the polynomial for all four with packed instructions (each half rounds as slip_atan
-// does), then the library's atanf for an argument beyond |t| = 1/2, entered by the warp only when
-// one of its particles needs it (one vote for both tyres).
+// for pairs, the polynomial for all four with packed instructions, then the library's atanf for an
+// argument beyond |t| = 1/2, entered by the warp only when one of its particles needs it (one vote
+// for both tyres).
 template <typename V>
 __device__ __forceinline__ void slip_atans(const DevParams& P, V tf, V tr, V& yf, V& yr)
 {
@@ -388,15 +398,8 @@ __device__ __forceinline__ void slip_atans(const DevParams& P, V tf, V tr, V& yf
         yf = slip_atan(tf);
         yr = slip_atan(tr);
     } else {
-        const auto poly = [&](V t) {
-            const V z = vmul(t, t);
-            V p = fold<V>(P, kFoldSa0);
-#pragma unroll
-            for (int i = kFoldSa0 + 1; i <= kFoldSaLast; ++i) p = vfma(p, z, fold<V>(P, i));
-            return vfma(vmul(t, z), p, t);
-        };
-        yf = poly(tf);
-        yr = poly(tr);
+        yf = slip_poly2(P, tf);
+        yr = slip_poly2(P, tr);
         if (__any_sync(__activemask(), beyond(tf, 0.5f) || beyond(tr, 0.5f))) {
             const auto fix = [](float tv, float yv) { return fabsf(tv) <= 0.5f ? yv : atanf(tv); };
             yf = each(tf, yf, fix);
@@ -432,11 +435,7 @@ __device__ __forceinline__ V slip_atan_v(const DevParams& P, V t)
     if constexpr (std::is_same<V, float>::value) {
         return slip_atan(t);
     } else {
-        const V z = vmul(t, t);
-        V p = fold<V>(P, kFoldSa0);
-#pragma unroll
-        for (int i = kFoldSa0 + 1; i <= kFoldSaLast; ++i) p = vfma(p, z, fold<V>(P, i));
-        V y = vfma(vmul(t, z), p, t);
+        V y = slip_poly2(P, t);
         if (__any_sync(__activemask(), beyond(t, 0.5f)))
             y = each(t, y, [](float tv, float yv) { return fabsf(tv) <= 0.5f ? yv : atanf(tv); });
         return y;
@@ -682,7 +681,7 @@ __device__ __forceinline__ void wheels_substep(const DevParams& P, const TP& trk
     const V vx = X[0], vy = X[1], r = X[2], wf = X[3], wr = X[4];
     const V ivx = each(vx, [&](float a) { return __fdividef(1.0f, fmaxf(a, P.vx_floor)); });
     const V yf = vfma(fold<V>(P, kFoldLf), r, vy);                                         // v_y + l_f r
-    V atf, nar;                                                                            // -alpha_r
+    V atf, nar;  // atan of the front slip argument; -alpha_r
     slip_atans(P, vmul(yf, ivx), vmul(vfma(fold<V>(P, kFoldNLr), r, vy), ivx), atf, nar);
     const V af = vfma(atf, fold<V>(P, kFoldM1), u.steer);                                  // alpha_f
     const V vwf = vfma(vx, u.cs, vmul(yf, u.sn));                                          // front wheel's speed

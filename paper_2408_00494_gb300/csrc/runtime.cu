@@ -299,10 +299,10 @@ int bss::derive_params(const bssmppi_params* p, DevParams& d, int& P, std::strin
     }
     // Mapping of particles to lanes: a segment of seg lanes (a power of two) per sample, P particles
     // per lane (lane l holds particles l, l + seg, ...). From 8 to 32 particles, two per lane in half
-    // as many lanes when the solve still has a warp's worth of samples for about 12 warps per SM (K
-    // above ~2000 warps on 152 SMs): that steps them in packed pairs and halves the per-step merge
-    // and cost work per particle, but fewer warps hide less latency (at 3-7 warps per SM it was
-    // 40 % slower). Otherwise seg is the next power of two >= M up to a warp, and P covers the rest.
+    // as many lanes when that still gives about 12 warps per SM (K M / 64 warps: about 1,800 on 152
+    // SMs): the pairs run packed and the per-step merge and cost work is shared by two particles, but
+    // fewer warps hide less latency (at 3-7 warps per SM it was 40 % slower). Otherwise seg is the
+    // next power of two >= M up to a warp, and P covers the rest.
     int seg = 1;
     int seg2 = 1;
     while (2 * seg2 < p->M) seg2 <<= 1;
