@@ -39,7 +39,7 @@ import workload  # noqa: E402
 METRIC = "particle-steps/s (K*M*T per solve)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one rollout_kernel launch, from one
 # ncu capture of the current kernel on each workload (None where none was taken).
-ROLLOUT_DRAM_BYTES = {"racing_K4096_M64_T40": 127488}
+ROLLOUT_DRAM_BYTES = {"racing_K4096_M64_T40": 126976}
 # Device facts for the nominal ALU peak (GB300: 152 SMs, 128 FP32 lanes per SM, max SM clock); the
 # roofline's denominator is the FP32 peak measured on the device in the same run (bssmppi_fp32_peak).
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
@@ -796,7 +796,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS, help="batches the batched server keeps in flight (1-8)")
     ap.add_argument("--serve-repeats", type=int, default=1, help="windows per rate of the sweep (independent streams)")
     ap.add_argument("--serve-rates", type=lambda s: tuple(float(x) for x in s.split(",")),
-                    default=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 5.5, 6.0),
+                    default=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 5.5, 6.0, 6.5, 7.0, 7.5),
                     help="per-controller rates of the sweep (Hz)")
     ap.add_argument("--serve-batch-work", type=float, default=SERVE_BATCH_WORK,
                     help="particle-steps admitted per serving batch (bounds a batch's duration)")
