@@ -277,6 +277,15 @@ struct Control {
     float steer, accel, sin_steer, cos_steer;
 };
 
+// sin x and cos x from the hardware sine and cosine after reducing x into [-pi, pi] (x - 2 pi rint(x /
+// 2 pi)), where their absolute error is at most 2^-21.4: no branch, and a short dependent chain
+// where that matters more than the last bits (the repair's serial forward pass).
+__device__ __forceinline__ void sincos_reduced(float x, float* s, float* c)
+{
+    const float r = fmaf(-6.28318530717958647692f, rintf(x * 0.15915494309189533577f), x);
+    __sincosf(r, s, c);
+}
+
 // sin x and cos x from their Taylor series through x^9 and x^10 (coefficients 1/n!); for |x| <= pi/4
 // the truncation errors are below |x|^11/11! < 2e-9 and |x|^12/12! < 2e-10, under FP32 rounding.
 // Outside that range (a spinning vehicle) the library's sincosf.
@@ -723,7 +732,9 @@ constexpr int kTapeFloats = 7;
 
 // The bicycle model's substep for one particle, with the forces written out unfolded, also writing
 // its tape (the repair's forward pass records it so that the reverse sweep needs no transcendental
-// functions). Its roundings differ from bicycle_substep's folded form by a few FP32 ulps.
+// functions). Its roundings differ from bicycle_substep's folded form by a few FP32 ulps, and its
+// heading's sine and cosine come from sincos_reduced (within 2^-21.4 absolute), which shortens the
+// serial chain of the repair's forward pass.
 __device__ __forceinline__ void bicycle_substep_taped(const DevParams& P, const float* __restrict__ kap, float s0,
                                                       const Control& u, float (&x)[6], float (&tp)[kTapeFloats])
 {
@@ -742,7 +753,7 @@ __device__ __forceinline__ void bicycle_substep_taped(const DevParams& P, const 
     const float k0 = kap[i], k1 = kap[i + 1];
     const float kap_s = fmaf(xs - fl, k1 - k0, k0);
     float sp, cp;
-    sincosf(ep, &sp, &cp);
+    sincos_reduced(ep, &sp, &cp);
     const float sdot = __fdividef(vx * cp - vy * sp, 1.0f - kap_s * ey);
     const float dvx = u.accel - Ff * u.sin_steer * P.inv_m + vy * r;
     const float dvy = (Ff * u.cos_steer + Fr) * P.inv_m - vx * r;

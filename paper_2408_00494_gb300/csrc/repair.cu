@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
             Control c;
             c.steer = v_s[2 * t];
             c.accel = v_s[2 * t + 1];
-            if constexpr (MODEL == 0) sincosf(c.steer, &c.sin_steer, &c.cos_steer);
+            if constexpr (MODEL == 0) sincos_reduced(c.steer, &c.sin_steer, &c.cos_steer);
             if constexpr (MODEL == 0) {
                 for (int j = 0; j < nsub; ++j) {
                     float tp[kTapeFloats];
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kRepairMaxThreads) repair_kernel(const DevPara
                     inject(t + 1, ey_next);
                     c.steer = v_s[2 * t];
                     c.accel = v_s[2 * t + 1];
-                    sincosf(c.steer, &c.sin_steer, &c.cos_steer);
+                    sincos_reduced(c.steer, &c.sin_steer, &c.cos_steer);
                     gs = 0.0f;
                     ga = 0.0f;
                 }

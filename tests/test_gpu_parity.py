@@ -312,6 +312,15 @@ def test_two_particles_per_lane_mapping(K, M):
     check_unrecorded(p, x0, v, ctr=M + 2)
 
 
+@pytest.mark.parametrize("K,M", [(4096, 32), (4096, 20)])
+def test_two_particles_per_lane_mapping_naive_sums(K, M):
+    """The same mapping with the naive (uncompensated) reductions, unrecorded, against the oracle."""
+    p = workload.config0()
+    p.K, p.M, p.T, p.compensated = K, M, 10, 0
+    x0, v = workload.random_state(p, 600 + M), workload.random_nominal(p, 600 + M)
+    check_unrecorded(p, x0, v, ctr=M + 3)
+
+
 def test_unrecorded_solve_with_every_state_weighted():
     """A cost that weights every state (the build with the run-time set of merged means)."""
     p = workload.config0()
